@@ -1,0 +1,125 @@
+"""Pins of the oracle's block solvers (Section 3) against dense LU, the scalar
+BiCGSTAB special case, unitary equivariance and the residual-gap property
+the paper reports for block BiCGGR (Section 4.3, Tables 2-3)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dense, dirac, solvers
+
+
+def _problem(dims, eps, kappa, csw, seed):
+    U = synth.random_su3_field(dims, eps, seed)
+
+    def A(M):
+        return dense.to_columns(dirac.apply_dirac(U, dense.from_columns(M, dims), kappa, csw))
+    return U, A
+
+
+@pytest.fixture(scope="module")
+def lattice_4444():
+    dims = (4, 4, 4, 4)
+    U, A = _problem(dims, 0.3, 0.12, 1.0, 1001)
+    D = dense.dense_matrix(U, 0.12, 1.0)
+    B = dense.to_columns(synth.point_sources(dims))
+    return dims, U, A, D, B
+
+
+@pytest.mark.parametrize("method", [solvers.block_bicgstab, solvers.block_bicggr])
+def test_block_solvers_match_dense_lu_4444(lattice_4444, method):
+    dims, U, A, D, B = lattice_4444
+    Xd = np.linalg.solve(D, B)
+    tol = 1e-12
+    X, info = method(A, B, tol, 500)
+    assert info["converged"]
+    cond = np.linalg.cond(D)
+    dev = np.linalg.norm(X - Xd, axis=0) / np.linalg.norm(Xd, axis=0)
+    # BiCGSTAB's true residual may drift by orders of magnitude (Table 2)
+    assert np.max(dev) <= cond * tol * 1e3
+    assert 5 <= info["iterations"] <= 200
+    assert info["matvecs"] == 2 * info["iterations"] + (1 if method is solvers.block_bicggr else 0)
+
+
+def test_block_solvers_match_dense_lu_extent2():
+    """2^4 lattice: n + mu = n - mu, both hops land on the same site."""
+    dims = (2, 2, 2, 2)
+    U, A = _problem(dims, 0.5, 0.11, 1.0, 7)
+    D = dense.dense_matrix(U, 0.11, 1.0)
+    B = dense.to_columns(synth.gaussian_sources(dims, 4, 8))
+    Xd = np.linalg.solve(D, B)
+    for method in (solvers.block_bicgstab, solvers.block_bicggr):
+        X, info = method(A, B, 1e-13, 400)
+        assert info["converged"]
+        assert np.max(np.linalg.norm(X - Xd, axis=0) / np.linalg.norm(Xd, axis=0)) < 1e-9
+
+
+def test_scalar_bicgstab_matches_dense(lattice_4444):
+    dims, U, A, D, B = lattice_4444
+    b = B[:, 5]
+    x, info = solvers.bicgstab(A, b, 1e-12, 500)
+    assert info["converged"]
+    xd = np.linalg.solve(D, b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
+
+
+def test_block_bicgstab_L1_is_scalar_bicgstab(lattice_4444):
+    """With L = 1 every L x L matrix is a scalar and the block recurrences
+    reduce to BiCGSTAB: same iterates to rounding."""
+    dims, U, A, D, B = lattice_4444
+    b = synth.gaussian_sources(dims, 1, 99)
+    b = dense.to_columns(b)
+    xs, info_s = solvers.bicgstab(A, b[:, 0], 1e-11, 300)
+    xb, info_b = solvers.block_bicgstab(A, b, 1e-11, 300)
+    assert info_s["iterations"] == info_b["iterations"]
+    n = min(len(info_s["history"]), len(info_b["history"]))
+    assert np.allclose(info_s["history"][:n], info_b["history"][:n], rtol=1e-6, atol=1e-14)
+    assert np.linalg.norm(xs - xb[:, 0]) / np.linalg.norm(xs) < 1e-10
+
+
+def test_block_bicggr_L1_relation_to_bicgstab(lattice_4444):
+    """For L = 1 BiCGGR's P/V recursion gives P_{k+1} = R_{k+1} + beta S_k with
+    beta = alpha gamma = (alpha / zeta) (r~, r_{k+1}) / (r~, r_k): check the
+    method still solves the single system to tolerance."""
+    dims, U, A, D, B = lattice_4444
+    b = dense.to_columns(synth.gaussian_sources(dims, 1, 98))
+    x, info = solvers.block_bicggr(A, b, 1e-12, 300)
+    assert info["converged"]
+    xd = np.linalg.solve(D, b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
+
+
+@pytest.mark.parametrize("method", [solvers.block_bicgstab, solvers.block_bicggr])
+def test_unitary_equivariance(lattice_4444, method):
+    """Solving with B M and R~_0 = R_0 M (M unitary) gives X M: the L x L
+    coefficients transform as M^-1 alpha M, zeta is invariant.  Catches
+    transposed or conjugated L x L bookkeeping."""
+    dims, U, A, D, B = lattice_4444
+    Bs = dense.to_columns(synth.gaussian_sources(dims, 4, 17))
+    rng = np.random.default_rng(5)
+    Q, _ = np.linalg.qr(rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4)))
+    X1, i1 = method(A, Bs, 1e-30, 12)
+    X2, i2 = method(A, Bs @ Q, 1e-30, 12)
+    assert i1["iterations"] == i2["iterations"] == 12
+    assert np.linalg.norm(X2 - X1 @ Q) / np.linalg.norm(X1) < 1e-10
+
+
+def test_bicggr_residual_gap_small(lattice_4444):
+    """Block BiCGGR keeps the recursive and the true residual consistent
+    (Section 3, Table 3): true residual close to the tolerance."""
+    dims, U, A, D, B = lattice_4444
+    tol = 1e-12
+    X, info = solvers.block_bicggr(A, B, tol, 500)
+    true_max, _ = solvers.true_residual(A, B, X)
+    assert true_max < 10 * tol
+
+
+def test_breakdown_on_dependent_columns(lattice_4444):
+    """Two identical right-hand sides make R~_0^H V singular."""
+    dims, U, A, D, B = lattice_4444
+    Bd = np.concatenate([B[:, :2], B[:, :1]], axis=1)
+    with np.errstate(all="ignore"):
+        try:
+            X, info = solvers.block_bicggr(A, Bd, 1e-12, 50)
+            assert info["breakdown"] or not info["converged"]
+        except np.linalg.LinAlgError:
+            pass
