@@ -1,0 +1,211 @@
+/*
+ * bkrylov.h - C ABI of the GB300 block Krylov solver library for the
+ * O(a)-improved (clover) Wilson-Dirac equation with L right-hand sides.
+ *
+ * Method: T. Sakurai, H. Tadano, Y. Kuramashi, "Application of block Krylov
+ * subspace algorithms to the Wilson-Dirac equation with multiple right-hand
+ * sides in lattice QCD" (arXiv:0903.4936).
+ *
+ * General rules
+ * -------------
+ *  - Every function returns a bk_status (BK_OK = 0).  No function aborts or
+ *    exits; bk_last_error() gives a one-line detail for the last failure on
+ *    the calling thread.
+ *  - Lattice dims[4] = {Lx, Ly, Lz, Lt}, periodic in all four directions.
+ *    Site index n = x + Lx*(y + Ly*(z + Lz*t)); V = Lx*Ly*Lz*Lt; N = 12 V.
+ *  - Canonical spinor block ("canonical layout"): L columns, column i is a
+ *    contiguous array of N complex FP64 numbers ordered [site][spin][colour]
+ *    {re, im}; component index 3*spin + colour (Section 2 point-source
+ *    convention, 0-based).  Total 16*N*L bytes.
+ *  - Device spinor block ("device layout"): opaque, precision-specific,
+ *    bk_field_bytes() bytes, produced by bk_pack() and read by bk_unpack().
+ *    Columns are stored one after another, each as 16-byte chunks in
+ *    [chunk][site] order (FP64: 12 chunks, FP32: 6, FP16: 3 plus one FP32
+ *    scale per site and column).  Any device allocation with 256-byte
+ *    alignment may hold it.
+ *  - Pointers documented as "device" must be CUDA device memory of the
+ *    context's device; "host" pointers are ordinary (or pinned) host memory.
+ *    The caller owns every buffer it passes; the library copies what it keeps.
+ *  - stream: a cudaStream_t cast to void* (NULL = legacy default stream).
+ *    Work is enqueued on it; functions that must read results back to the
+ *    host (bk_block_solve*) synchronise it.
+ */
+#ifndef BKRYLOV_H
+#define BKRYLOV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bk_status {
+    BK_OK = 0,
+    BK_ERR_INVALID_ARG = 1,   /* bad size, pointer or enum value            */
+    BK_ERR_OUT_OF_MEMORY = 2, /* device or pinned-host allocation failed    */
+    BK_ERR_CUDA = 3,          /* a CUDA runtime call failed                 */
+    BK_ERR_NOT_CONVERGED = 4, /* maxiter reached; X holds the last iterate  */
+    BK_ERR_BREAKDOWN = 5,     /* singular or non-finite L x L system        */
+    BK_ERR_NONFINITE = 6,     /* NaN/Inf in the right-hand side or guess    */
+    BK_ERR_NO_GAUGE = 7       /* gauge field / clover not set up yet        */
+} bk_status;
+
+typedef enum bk_prec {
+    BK_FP64 = 0, /* FP64 storage and arithmetic                               */
+    BK_FP32 = 1, /* FP32 storage and arithmetic                               */
+    BK_FP16 = 2  /* FP16 storage (per site-column FP32 scale), FP32 arithmetic */
+} bk_prec;
+
+typedef enum bk_method {
+    BK_BICGSTAB = 0, /* block BiCGSTAB, Section 3                             */
+    BK_BICGGR = 1    /* block BiCGGR (the paper's new method), Section 3     */
+} bk_method;
+
+typedef struct bk_ctx bk_ctx; /* opaque; owns device gauge, clover, workspace */
+
+/* Human-readable name of a status code (static string). */
+const char* bk_status_string(bk_status s);
+/* Detail message of the last failing call on this thread (static storage). */
+const char* bk_last_error(void);
+
+/* Create a context for lattice dims on CUDA device `device`.
+ * Errors: INVALID_ARG (dims < 2 or V*12 overflow), CUDA.                  */
+bk_status bk_create(const int dims[4], int device, bk_ctx** out);
+/* Release every device allocation of the context.  NULL is accepted.      */
+bk_status bk_destroy(bk_ctx* ctx);
+
+/* Gauge field U_mu(n,a,b) (Section 2): array [4 mu][V site][3 a][3 b]
+ * {re, im} FP64, mu = 0..3 for x, y, z, t.  Copied into device FP64 and FP32
+ * copies; U may be host (U_on_device = 0) or device memory.  Invalidates
+ * a previously built clover term.  Errors: INVALID_ARG, CUDA.              */
+bk_status bk_upload_gauge(bk_ctx* ctx, const double* U, int U_on_device, void* stream);
+
+/* Clover term of Eq. (wd-op): builds F_mu_nu(n) from the four plaquette
+ * leaves (Section 2, leaves read as closed paths) in FP64 on the device and
+ * stores the kappa-independent site matrix
+ *     C(n) = c_SW * sum_{mu,nu} (i/2) sigma_mu_nu F_mu_nu(n)
+ * as two 6x6 Hermitian blocks (chiral basis) in FP64 and FP32.
+ * csw = 0 gives the plain Wilson operator.  Errors: NO_GAUGE, CUDA.        */
+bk_status bk_build_clover(bk_ctx* ctx, double csw, void* stream);
+
+/* Bytes of an L-column device-layout block of precision prec.             */
+size_t bk_field_bytes(const bk_ctx* ctx, int L, bk_prec prec);
+
+/* Canonical FP64 (device) -> device layout in prec (rounds to nearest).   */
+bk_status bk_pack(bk_ctx* ctx, const double* X, void* Xd, int L, bk_prec prec, void* stream);
+/* Device layout in prec -> canonical FP64 (device).                       */
+bk_status bk_unpack(bk_ctx* ctx, const void* Xd, double* X, int L, bk_prec prec, void* stream);
+
+/* Multi-RHS operator, Eq. (wd-op), one kernel launch:
+ *     Y_i = X_i - kappa_i * ( H X_i + C X_i ),   i = 0..L-1,
+ * H the hopping term (8 neighbours, (1 -+ gamma_mu) projectors, periodic),
+ * C the clover term of bk_build_clover.  kappa: host array of L values (one
+ * hopping parameter per column).  Xd, Yd: device-layout blocks in prec,
+ * must not overlap.  Errors: NO_GAUGE, INVALID_ARG, CUDA.                 */
+bk_status bk_dslash_dev(bk_ctx* ctx, const double* kappa, const void* Xd, void* Yd, int L,
+                        bk_prec prec, void* stream);
+
+/* Same operator on canonical FP64 device blocks X -> Y, computed in prec:
+ * packs X, applies the operator, unpacks into Y (library workspace).      */
+bk_status bk_dslash(bk_ctx* ctx, const double* kappa, const double* X, double* Y, int L,
+                    bk_prec prec, void* stream);
+
+/* gamma_5 (as printed in Section 2) applied to every column of a canonical
+ * FP64 device block, out of place (Y may equal X).                        */
+bk_status bk_gamma5(bk_ctx* ctx, const double* X, double* Y, int L, void* stream);
+
+/* Block inner product (Section 3, the L x L matrices R~_0^H V_k etc.):
+ *     G[i][j] = sum_{n, alpha, a} conj(A_i(n,alpha,a)) B_j(n,alpha,a)
+ * for device-layout blocks A, B of L columns in prec.  G: device array of
+ * L*L complex FP64 {re, im}, row-major.  Products and per-thread partial sums
+ * are in the arithmetic precision of prec; the sum across threads and blocks
+ * is FP64.  Uses library workspace for the per-block partial sums.
+ * Errors: INVALID_ARG, CUDA.                                              */
+bk_status bk_block_gram(bk_ctx* ctx, const void* A, const void* B, int L, bk_prec prec,
+                        double* G, void* stream);
+
+/* Block linear combination (Section 3, products such as S_k alpha_k):
+ *     Y = Z + c * (X M)     with X, Y, Z device blocks of L columns in prec,
+ * M an L x L complex FP64 device matrix (row-major, (X M)_j = sum_i X_i M_ij)
+ * and c a complex scalar {re, im} (host).  Z may be NULL (treated as 0) or
+ * equal Y; X must not overlap Y.  Errors: INVALID_ARG, CUDA.              */
+bk_status bk_block_xmy(bk_ctx* ctx, const void* X, const double* M, const double c[2],
+                       const void* Z, void* Y, int L, bk_prec prec, void* stream);
+
+/* Dense L x L solve in FP64 on the device (one thread block):
+ *     G Xs = s * H,  G, H, Xs device arrays of L*L complex FP64, row-major;
+ * s a complex scalar {re, im} (host).  LU with partial pivoting; *info
+ * (device int) is set to 0 on success, k+1 if pivot k is below
+ * 1e-14 * max|G| or not finite (then Xs is unspecified).  This is the
+ * "Solve ... for alpha_k" step of both block algorithms.                  */
+bk_status bk_small_solve(int L, const double* G, const double* H, const double s[2],
+                         double* Xs, int* info, void* stream);
+
+/* ---------------------------------------------------------------- solves */
+
+typedef struct bk_solve_params {
+    int method;            /* bk_method                                       */
+    int prec;              /* inner precision (bk_prec).  BK_FP64 = the plain
+                              method; FP32/FP16 = inner iterations in that
+                              precision with FP64 reliable updates             */
+    double tol;            /* eps of the stopping rule max_i ||r_i||/||b_i||  */
+    int maxiter;           /* iteration limit (loop bodies)                   */
+    double reliable_delta; /* mixed precision: FP64 residual replacement when
+                              the residual fell by this factor (0: default 0.1) */
+    int x0_given;          /* 1: X holds the initial guess X_0; 0: X_0 = 0    */
+    int buffers_on_host;   /* 1: B and X are host canonical buffers (copied in
+                              and out inside the call); 0: device canonical    */
+    int rtilde_random;     /* 0: R~_0 = R_0 (default); 1: seeded Gaussian     */
+    uint64_t seed;         /* seed for rtilde_random                          */
+    int record_history;    /* 1: info->history[k] = max_i rel. residual       */
+    int timing;            /* 1: time every dslash launch with CUDA events    */
+} bk_solve_params;
+
+typedef struct bk_solve_info {
+    int iterations;        /* completed loop bodies                           */
+    int matvecs;           /* operator applications in the inner precision    */
+    int matvecs_fp64;      /* FP64 operator applications (residuals)          */
+    int reliable_updates;  /* FP64 residual replacements                      */
+    int converged;         /* 1 if every column met tol (true residual for
+                              mixed precision)                                 */
+    int breakdown;         /* 1 if an L x L solve broke down                   */
+    double true_res_max;   /* max_i ||b_i - A x_i|| / ||b_i|| in FP64 at exit */
+    double rec_res_max;    /* recursive residual max at exit                  */
+    double* true_res;      /* optional caller array [L], filled if non-NULL    */
+    double* history;       /* optional caller array [maxiter + 1]              */
+    int history_len;       /* entries written to history                      */
+    double time_total_ms;  /* wall time of the call (host clock)              */
+    double time_dslash_ms; /* summed CUDA-event time of dslash launches
+                              (params.timing = 1 only)                         */
+    int n_dslash;          /* dslash launches (all precisions)                */
+    int n_dslash_inner;    /* dslash launches in the inner precision          */
+    double time_dslash_inner_ms; /* event time of those (timing = 1)          */
+    long long n_launches;  /* kernels launched by the call                    */
+} bk_solve_info;
+
+/* Solve D_W X = B (Eq. (linear_mrhs)) for L right-hand sides with one kappa
+ * (the clover term of the last bk_build_clover).  B, X: canonical FP64
+ * blocks (device, or host if params->buffers_on_host).  On return X holds
+ * the solution (or the last iterate for NOT_CONVERGED / BREAKDOWN) and
+ * info is filled.  Errors: INVALID_ARG, NO_GAUGE, NONFINITE, BREAKDOWN,
+ * NOT_CONVERGED, OUT_OF_MEMORY, CUDA.                                     */
+bk_status bk_block_solve(bk_ctx* ctx, const bk_solve_params* params, double kappa,
+                         const double* B, double* X, int L, bk_solve_info* info, void* stream);
+
+/* Several independent systems on the same gauge field, solved together:
+ * system s has hopping parameter kappa[s] and Ls[s] columns; their columns
+ * are concatenated in B and X (canonical layout, sum(Ls) columns).  One
+ * multi-RHS operator launch serves every system per step (each link and
+ * clover block is read once for all columns); Gram matrices, L x L solves and
+ * block updates are block-diagonal per system; converged systems are frozen.
+ * info: array of nsys entries.  nsys <= 32.                               */
+bk_status bk_block_solve_batched(bk_ctx* ctx, const bk_solve_params* params, int nsys,
+                                 const double* kappa, const int* Ls, const double* B, double* X,
+                                 bk_solve_info* info, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BKRYLOV_H */

@@ -1,0 +1,1052 @@
+// C ABI of the library (include/bkrylov.h): context, gauge and clover set-up,
+// operator entry points, and the block BiCGSTAB / block BiCGGR drivers of
+// Section 3 of arXiv:0903.4936.
+//
+// The drivers run the paper's recurrences step by step as device kernels
+// (operator, Gram matrices, L x L solves, fused block updates).  The host
+// only orders the launches and, once per iteration, reads back the L column
+// norms of the new residual (and the solve status words) to apply the
+// stopping rule max_i ||r_i|| / ||b_i|| <= eps and, with FP32/FP16 inner
+// precision, to decide on FP64 reliable updates (residual replacement).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "bk_common.cuh"
+#include "bk_kernels.h"
+
+// ---------------------------------------------------------------- errors
+
+static thread_local char g_err[512] = "";
+
+void bk_set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+#define BK_TRY(expr)                        \
+    do {                                    \
+        bk_status _s = (expr);              \
+        if (_s != BK_OK) return _s;         \
+    } while (0)
+
+#define BK_CHECK_ARG(cond, msg)             \
+    do {                                    \
+        if (!(cond)) {                      \
+            bk_set_error("%s", msg);        \
+            return BK_ERR_INVALID_ARG;      \
+        }                                   \
+    } while (0)
+
+// ---------------------------------------------------------------- buffers
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+    bk_status ensure(size_t bytes) {
+        if (bytes <= n && p) return BK_OK;
+        release();
+        if (bytes == 0) bytes = 256;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            n = 0;
+            bk_set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+            return BK_ERR_OUT_OF_MEMORY;
+        }
+        n = bytes;
+        return BK_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    template <typename T>
+    T* as() const {
+        return (T*)p;
+    }
+};
+
+struct HostBuf {
+    void* p = nullptr;
+    size_t n = 0;
+    bk_status ensure(size_t bytes) {
+        if (bytes <= n && p) return BK_OK;
+        release();
+        cudaError_t e = cudaMallocHost(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            bk_set_error("cudaMallocHost(%zu) failed: %s", bytes, cudaGetErrorString(e));
+            return BK_ERR_OUT_OF_MEMORY;
+        }
+        n = bytes;
+        return BK_OK;
+    }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+// ---------------------------------------------------------------- context
+
+struct bk_ctx {
+    int dims[4];
+    int V;
+    int device;
+    DevBuf U64, U32, C64, C32, Utmp;
+    bool has_gauge = false, has_clover = false;
+    double csw = 0.0;
+    // scratch of the single-operation entry points
+    DevBuf s1, s2, part, scal;
+    // solver workspace
+    DevBuf B64, X64, R64, Xlo, blk[8], small, spart, gwork, canonB, canonX;
+    HostBuf rb_host;
+    std::vector<cudaEvent_t> events;
+};
+
+static const void* gauge_ptr(const bk_ctx* c, int prec) { return prec == BK_FP64 ? c->U64.p : c->U32.p; }
+static const void* clov_ptr(const bk_ctx* c, int prec) { return prec == BK_FP64 ? c->C64.p : c->C32.p; }
+
+static bool valid_prec(int p) { return p == BK_FP64 || p == BK_FP32 || p == BK_FP16; }
+
+extern "C" const char* bk_status_string(bk_status s) {
+    switch (s) {
+        case BK_OK: return "ok";
+        case BK_ERR_INVALID_ARG: return "invalid argument";
+        case BK_ERR_OUT_OF_MEMORY: return "out of memory";
+        case BK_ERR_CUDA: return "CUDA error";
+        case BK_ERR_NOT_CONVERGED: return "not converged";
+        case BK_ERR_BREAKDOWN: return "breakdown of an L x L solve";
+        case BK_ERR_NONFINITE: return "non-finite input";
+        case BK_ERR_NO_GAUGE: return "gauge field or clover term not set";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* bk_last_error(void) { return g_err; }
+
+extern "C" bk_status bk_create(const int dims[4], int device, bk_ctx** out) {
+    BK_CHECK_ARG(dims && out, "null argument");
+    long long V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        BK_CHECK_ARG(dims[mu] >= 2, "every lattice extent must be >= 2");
+        V *= dims[mu];
+    }
+    BK_CHECK_ARG(V * 12 < (1LL << 31), "lattice too large (12 V must fit in int32)");
+    BK_CUDA_TRY(cudaSetDevice(device));
+    bk_ctx* c = new bk_ctx();
+    for (int mu = 0; mu < 4; ++mu) c->dims[mu] = dims[mu];
+    c->V = (int)V;
+    c->device = device;
+    bk_status s;
+    if ((s = c->U64.ensure((size_t)36 * V * sizeof(double2))) != BK_OK ||
+        (s = c->U32.ensure((size_t)36 * V * sizeof(float2))) != BK_OK ||
+        (s = c->C64.ensure((size_t)36 * V * sizeof(double2))) != BK_OK ||
+        (s = c->C32.ensure((size_t)18 * V * sizeof(float4))) != BK_OK) {
+        bk_destroy(c);
+        return s;
+    }
+    *out = c;
+    return BK_OK;
+}
+
+extern "C" bk_status bk_destroy(bk_ctx* c) {
+    if (!c) return BK_OK;
+    cudaSetDevice(c->device);
+    DevBuf* bufs[] = {&c->U64, &c->U32, &c->C64, &c->C32, &c->Utmp, &c->s1, &c->s2, &c->part, &c->scal,
+                      &c->B64, &c->X64, &c->R64, &c->Xlo, &c->small, &c->spart, &c->gwork, &c->canonB,
+                      &c->canonX};
+    for (DevBuf* b : bufs) b->release();
+    for (auto& b : c->blk) b.release();
+    c->rb_host.release();
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    delete c;
+    return BK_OK;
+}
+
+extern "C" bk_status bk_upload_gauge(bk_ctx* c, const double* U, int on_device, void* stream) {
+    BK_CHECK_ARG(c && U, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    BK_CUDA_TRY(cudaSetDevice(c->device));
+    const double* src = U;
+    if (!on_device) {
+        BK_TRY(c->Utmp.ensure((size_t)36 * c->V * sizeof(double2)));
+        BK_CUDA_TRY(cudaMemcpyAsync(c->Utmp.p, U, (size_t)36 * c->V * sizeof(double2), cudaMemcpyHostToDevice, st));
+        src = c->Utmp.as<double>();
+    }
+    BK_TRY(launch_gauge_convert(src, c->U64.as<double2>(), c->U32.as<float2>(), c->V, st));
+    if (!on_device) BK_CUDA_TRY(cudaStreamSynchronize(st));
+    c->has_gauge = true;
+    c->has_clover = false;
+    return BK_OK;
+}
+
+extern "C" bk_status bk_build_clover(bk_ctx* c, double csw, void* stream) {
+    BK_CHECK_ARG(c, "null context");
+    if (!c->has_gauge) {
+        bk_set_error("bk_build_clover before bk_upload_gauge");
+        return BK_ERR_NO_GAUGE;
+    }
+    BK_CUDA_TRY(cudaSetDevice(c->device));
+    BK_TRY(launch_clover_build(c->U64.as<double2>(), c->C64.as<double2>(), c->C32.as<float4>(), c->dims, csw,
+                               (cudaStream_t)stream));
+    c->csw = csw;
+    c->has_clover = true;
+    return BK_OK;
+}
+
+extern "C" size_t bk_field_bytes(const bk_ctx* c, int L, bk_prec prec) {
+    if (!c || L < 0 || !valid_prec(prec)) return 0;
+    return field_bytes(L, c->V, prec);
+}
+
+extern "C" bk_status bk_pack(bk_ctx* c, const double* X, void* Xd, int L, bk_prec prec, void* stream) {
+    BK_CHECK_ARG(c && X && Xd && L >= 1 && valid_prec(prec), "bad argument to bk_pack");
+    BK_CUDA_TRY(cudaSetDevice(c->device));
+    return launch_pack(prec, X, make_field(Xd, L, c->V, prec), L, (cudaStream_t)stream);
+}
+
+extern "C" bk_status bk_unpack(bk_ctx* c, const void* Xd, double* X, int L, bk_prec prec, void* stream) {
+    BK_CHECK_ARG(c && X && Xd && L >= 1 && valid_prec(prec), "bad argument to bk_unpack");
+    BK_CUDA_TRY(cudaSetDevice(c->device));
+    return launch_unpack(prec, make_field((void*)Xd, L, c->V, prec), X, L, (cudaStream_t)stream);
+}
+
+static bk_status dslash_fields(bk_ctx* c, int prec, const double* kappa, Field x, Field y, Field b, int col0,
+                               int ncol, int residual, cudaStream_t st) {
+    DslashOp op;
+    op.x = x;
+    op.y = y;
+    op.b = b;
+    op.U = gauge_ptr(c, prec);
+    op.clov = clov_ptr(c, prec);
+    for (int mu = 0; mu < 4; ++mu) op.dims[mu] = c->dims[mu];
+    op.V = c->V;
+    op.col0 = col0;
+    op.ncol = ncol;
+    op.residual = residual;
+    op.kappa = kappa;
+    op.site_block = 0;
+    op.col_block = 0;
+    return launch_dslash(prec, op, st);
+}
+
+extern "C" bk_status bk_dslash_dev(bk_ctx* c, const double* kappa, const void* Xd, void* Yd, int L, bk_prec prec,
+                                   void* stream) {
+    BK_CHECK_ARG(c && kappa && Xd && Yd && L >= 1 && valid_prec(prec), "bad argument to bk_dslash_dev");
+    BK_CHECK_ARG(Xd != Yd, "bk_dslash_dev: X and Y must not overlap");
+    if (!c->has_gauge || !c->has_clover) {
+        bk_set_error("operator needs bk_upload_gauge and bk_build_clover first");
+        return BK_ERR_NO_GAUGE;
+    }
+    BK_CUDA_TRY(cudaSetDevice(c->device));
+    Field x = make_field((void*)Xd, L, c->V, prec), y = make_field(Yd, L, c->V, prec);
+    return dslash_fields(c, prec, kappa, x, y, x, 0, L, 0, (cudaStream_t)stream);
+}
+
+extern "C" bk_status bk_dslash(bk_ctx* c, const double* kappa, const double* X, double* Y, int L, bk_prec prec,
+                               void* stream) {
+    BK_CHECK_ARG(c && kappa && X && Y && L >= 1 && valid_prec(prec), "bad argument to bk_dslash");
+    if (!c->has_gauge || !c->has_clover) {
+        bk_set_error("operator needs bk_upload_gauge and bk_build_clover first");
+        return BK_ERR_NO_GAUGE;
+    }
+    BK_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nb = field_bytes(L, c->V, prec);
+    BK_TRY(c->s1.ensure(nb));
+    BK_TRY(c->s2.ensure(nb));
+    Field x = make_field(c->s1.p, L, c->V, prec), y = make_field(c->s2.p, L, c->V, prec);
+    BK_TRY(launch_pack(prec, X, x, L, st));
+    BK_TRY(dslash_fields(c, prec, kappa, x, y, x, 0, L, 0, st));
+    return launch_unpack(prec, y, Y, L, st);
+}
+
+extern "C" bk_status bk_gamma5(bk_ctx* c, const double* X, double* Y, int L, void* stream) {
+    BK_CHECK_ARG(c && X && Y && L >= 1, "bad argument to bk_gamma5");
+    BK_CUDA_TRY(cudaSetDevice(c->device));
+    return launch_gamma5_canon(X, Y, (long long)L * c->V, (cudaStream_t)stream);
+}
+
+extern "C" bk_status bk_block_gram(bk_ctx* c, const void* A, const void* B, int L, bk_prec prec, double* G,
+                                   void* stream) {
+    BK_CHECK_ARG(c && A && B && G && L >= 1 && valid_prec(prec), "bad argument to bk_block_gram");
+    BK_CUDA_TRY(cudaSetDevice(c->device));
+    SysPart p = single_part(L);
+    BK_TRY(c->part.ensure(gram_partial_bytes(p, c->V)));
+    return launch_gram(prec, make_field((void*)A, L, c->V, prec), make_field((void*)B, L, c->V, prec), p, G,
+                       c->part.as<double>(), c->V, (cudaStream_t)stream);
+}
+
+extern "C" bk_status bk_block_xmy(bk_ctx* c, const void* X, const double* M, const double cval[2], const void* Z,
+                                  void* Y, int L, bk_prec prec, void* stream) {
+    BK_CHECK_ARG(c && X && M && cval && Y && L >= 1 && valid_prec(prec), "bad argument to bk_block_xmy");
+    BK_CHECK_ARG(X != Y, "bk_block_xmy: X must not overlap Y");
+    BK_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    BK_TRY(c->scal.ensure(2 * sizeof(double)));
+    BK_CUDA_TRY(cudaMemcpyAsync(c->scal.p, cval, 2 * sizeof(double), cudaMemcpyHostToDevice, st));
+    SysPart p = single_part(L);
+    Field fz = make_field((void*)(Z ? Z : X), L, c->V, prec);
+    return launch_xmy(prec, make_field((void*)X, L, c->V, prec), M, c->scal.as<double>(), fz, Z != nullptr,
+                      make_field(Y, L, c->V, prec), p, c->V, st);
+}
+
+extern "C" bk_status bk_small_solve(int L, const double* G, const double* H, const double s[2], double* Xs,
+                                    int* info, void* stream) {
+    BK_CHECK_ARG(G && H && s && Xs && info && L >= 1 && L <= 1024, "bad argument to bk_small_solve");
+    cudaStream_t st = (cudaStream_t)stream;
+    SysPart p = single_part(L);
+    double* gwork = nullptr;
+    if (L > 48) BK_CUDA_TRY(cudaMallocAsync((void**)&gwork, (size_t)2 * L * L * sizeof(double2), st));
+    bk_status r = launch_small_solve(G, H, nullptr, Xs, info, p, st, gwork, s);
+    if (gwork) cudaFreeAsync(gwork, st);
+    return r;
+}
+
+// ================================================================= solver
+
+namespace {
+
+// per-system scalar coefficients computed on the device
+//   mode 0 (BiCGGR):   zeta = sum_j d0_j / sum_j d1_j  (d0 = W^H R, d1 = W^H W)
+//   mode 1 (BiCGSTAB): zeta = sum_j d0_j / sum_j d1_j  (d0 = Z^H T, d1 = Z^H Z)
+// writes zeta, -zeta, 1/zeta; zbad[s] = 1 when zeta is not finite or zero.
+__global__ void k_scalars(const double2* __restrict__ dots, int Lt, SysPart p, double2* zeta, double2* mzeta,
+                          double2* izeta, int* zbad) {
+    const int s = threadIdx.x;
+    if (s >= p.nsys) return;
+    if (!((p.active >> s) & 1u)) return;
+    double2 num = make_double2(0, 0), den = make_double2(0, 0);
+    for (int j = p.col0[s]; j < p.col0[s + 1]; ++j) {
+        num.x += dots[j].x;
+        num.y += dots[j].y;
+        den.x += dots[Lt + j].x;
+        den.y += dots[Lt + j].y;
+    }
+    const double d = den.x * den.x + den.y * den.y;
+    const double zr = (num.x * den.x + num.y * den.y) / d, zi = (num.y * den.x - num.x * den.y) / d;
+    zeta[s] = make_double2(zr, zi);
+    mzeta[s] = make_double2(-zr, -zi);
+    const double m = zr * zr + zi * zi;
+    izeta[s] = make_double2(zr / m, -zi / m);
+    zbad[s] = (isfinite(zr) && isfinite(zi) && m > 0.0) ? 0 : 1;
+}
+
+// X64[cols] += Xlo[cols]; Xlo[cols] = 0
+__global__ void k_accum(Field x64, Field xlo, int V) {
+    const int site = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (site >= V) return;
+    cx<double> a[12];
+    cx<float> b[12];
+    load_spinor<BK_FP64>(x64, c, site, a);
+    load_spinor<BK_FP32>(xlo, c, site, b);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        a[k] = a[k] + mk((double)b[k].r, (double)b[k].i);
+        b[k] = mk(0.f, 0.f);
+    }
+    store_spinor<BK_FP64>(x64, c, site, a);
+    store_spinor<BK_FP32>(xlo, c, site, b);
+}
+
+// Seeded Gaussian shadow residual: SplitMix64 of (seed, index), Box-Muller.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+template <int P>
+__global__ void k_random(Field f, int V, uint64_t seed) {
+    using R = typename Prec<P>::real;
+    const int site = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (site >= V) return;
+    cx<R> v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const uint64_t idx = (((uint64_t)c * V + site) * 12 + k);
+        const uint64_t a = splitmix64(seed ^ (2 * idx)), b = splitmix64(seed ^ (2 * idx + 1));
+        const double u1 = ((a >> 11) + 1) * (1.0 / 9007199254740993.0);
+        const double u2 = (b >> 11) * (1.0 / 9007199254740992.0);
+        const double r = sqrt(-log(u1)) * 0.7071067811865476 * 1.4142135623730951 * 0.7071067811865476;
+        v[k] = mk((R)(r * cospi(2 * u2)), (R)(r * sinpi(2 * u2)));
+    }
+    store_spinor<P>(f, c, site, v);
+}
+
+struct Solve {
+    bk_ctx* c;
+    const bk_solve_params* prm;
+    cudaStream_t st;
+    int nsys, Lt, V, P, method;
+    bool mixed;
+    SysPart part;
+    std::vector<double> kcol;        // kappa per column
+    std::vector<double> bnorm;       // ||b_j||
+    std::vector<int> done;           // per system: 0 active, 1 converged, 2 breakdown, 3 not converged
+    std::vector<double> rmax_since;  // per system, mixed precision
+    std::vector<int> iters, mv, mv64, nrel;
+    std::vector<std::vector<double>> hist;
+    std::vector<double> true_res, rec_res;
+    Field B64, X64, R64, Xlo, R, Rt, Pb, Vb, Wb, Ub, Yb, Tb, Zb, Ptmp;
+    // small device arrays
+    double *G_V, *G_RR, *G_RRn, *alpha, *gam, *G_Z, *dots, *rn, *zeta, *mzeta, *izeta, *partial, *gwork;
+    int *info_a, *info_g, *zbad;
+    // host readback
+    char* rbh;
+    double* rn_h;
+    int *info_a_h, *info_g_h, *zbad_h;
+    size_t rb_bytes;
+    char* rb_dev;
+    // counters
+    long long launches = 0;
+    int n_dslash = 0, n_dslash_inner = 0;
+    double t_dslash = 0, t_dslash_inner = 0;
+    std::vector<std::pair<int, bool>> ev_pending;  // (event index, inner)
+    int ev_used = 0;
+
+    int ncoef() const { return part.coef_off[nsys]; }
+
+    bk_status event_pair(int& idx) {
+        while ((int)c->events.size() < ev_used + 2) {
+            cudaEvent_t e;
+            BK_CUDA_TRY(cudaEventCreate(&e));
+            c->events.push_back(e);
+        }
+        idx = ev_used;
+        ev_used += 2;
+        return BK_OK;
+    }
+    bk_status harvest_events() {
+        for (auto& pr : ev_pending) {
+            float ms = 0.f;
+            BK_CUDA_TRY(cudaEventElapsedTime(&ms, c->events[pr.first], c->events[pr.first + 1]));
+            t_dslash += ms;
+            if (pr.second) t_dslash_inner += ms;
+        }
+        ev_pending.clear();
+        ev_used = 0;
+        return BK_OK;
+    }
+
+    // y = D x (inner precision) over all active columns
+    bk_status dslash(int prec, Field x, Field y, Field b, int col0, int ncol, int residual) {
+        int ev = -1;
+        if (prm->timing) {
+            BK_TRY(event_pair(ev));
+            BK_CUDA_TRY(cudaEventRecord(c->events[ev], st));
+        }
+        BK_TRY(dslash_fields(c, prec, kcol.data() + col0, x, y, b, col0, ncol, residual, st));
+        if (prm->timing) {
+            BK_CUDA_TRY(cudaEventRecord(c->events[ev + 1], st));
+            ev_pending.push_back({ev, prec == P});
+        }
+        launches += (ncol + BK_MAX_COLS - 1) / BK_MAX_COLS;
+        n_dslash++;
+        if (prec == P) n_dslash_inner++;
+        return BK_OK;
+    }
+
+    bk_status gram(Field A, Field B, double* G) {
+        launches += 2;
+        return launch_gram(P, A, B, part, G, partial, V, st);
+    }
+    bk_status coldot(int prec, int npair, const Field* A, const Field* B, double* out) {
+        launches += 2;
+        return launch_coldot(prec, npair, A, B, Lt, out, partial, V, st);
+    }
+    bk_status small_solve(const double* G, const double* H, const double* scale, double* X, int* info) {
+        launches += 1;
+        return launch_small_solve(G, H, scale, X, info, part, st, gwork);
+    }
+    bk_status scalars() {
+        launches += 1;
+        k_scalars<<<1, 32, 0, st>>>((const double2*)dots, Lt, part, (double2*)zeta, (double2*)mzeta,
+                                    (double2*)izeta, zbad);
+        BK_CUDA_TRY(cudaGetLastError());
+        return BK_OK;
+    }
+    bk_status genop(const GenOp& g) {
+        launches += 1;
+        return launch_genop(P, g, V, st);
+    }
+    GenOp genop0() {
+        GenOp g;
+        memset(&g, 0, sizeof(g));
+        g.p = part;
+        return g;
+    }
+
+    bk_status readback() {
+        BK_CUDA_TRY(cudaMemcpyAsync(rbh, rb_dev, rb_bytes, cudaMemcpyDeviceToHost, st));
+        BK_CUDA_TRY(cudaStreamSynchronize(st));
+        if (prm->timing) BK_TRY(harvest_events());
+        return BK_OK;
+    }
+
+    // squared FP64 column norms of R (inner precision) into rn; then readback
+    bk_status residual_norms() {
+        Field a[1] = {R}, b[1] = {R};
+        BK_TRY(coldot(P, 1, a, b, rn));
+        return readback();
+    }
+
+    double rel(int j) const { return std::sqrt(std::max(rn_h[2 * j], 0.0)) / bnorm[j]; }
+    double sys_max(int s) const {
+        double m = 0;
+        for (int j = part.col0[s]; j < part.col0[s + 1]; ++j) {
+            const double r = rel(j);
+            m = (std::isnan(r) || r > m) ? r : m;
+            if (std::isnan(m)) return m;
+        }
+        return m;
+    }
+
+    // FP64 residual replacement for system s: X64 += Xlo, R64 = B - A X64, R = R64.
+    // Leaves the FP64 residual norms of s in rn_h after a readback.
+    bk_status reliable_update(const std::vector<int>& sys) {
+        for (int s : sys) {
+            const int c0 = part.col0[s], n = part.col0[s + 1] - c0;
+            if (mixed) {
+                dim3 grid((V + 127) / 128, n);
+                k_accum<<<grid, 128, 0, st>>>(field_cols(X64, c0), field_cols(Xlo, c0), V);
+                BK_CUDA_TRY(cudaGetLastError());
+                launches++;
+            }
+            BK_TRY(dslash(BK_FP64, X64, R64, B64, c0, n, 1));
+            mv64[s]++;
+            if (P != BK_FP64) {
+                BK_TRY(launch_cast(BK_FP64, field_cols(R64, c0), P, field_cols(R, c0), n, st));
+            } else {
+                BK_CUDA_TRY(cudaMemcpyAsync((char*)R.data + (size_t)c0 * R.cstride * 16,
+                                            (char*)R64.data + (size_t)c0 * R64.cstride * 16,
+                                            (size_t)n * R.cstride * 16, cudaMemcpyDeviceToDevice, st));
+            }
+            launches++;
+            nrel[s]++;
+        }
+        Field a[1] = {R64}, b[1] = {R64};
+        BK_TRY(coldot(BK_FP64, 1, a, b, rn));
+        return readback();
+    }
+
+    bk_status setup(const double* Bc, const double* Xc) {
+        const size_t fb64 = field_bytes(Lt, V, BK_FP64), fbp = field_bytes(Lt, V, P);
+        BK_TRY(c->B64.ensure(fb64));
+        BK_TRY(c->X64.ensure(fb64));
+        BK_TRY(c->R64.ensure(fb64));
+        B64 = make_field(c->B64.p, Lt, V, BK_FP64);
+        X64 = make_field(c->X64.p, Lt, V, BK_FP64);
+        R64 = make_field(c->R64.p, Lt, V, BK_FP64);
+        const int nblk = 7;
+        for (int i = 0; i < nblk; ++i) BK_TRY(c->blk[i].ensure(fbp));
+        Field f[7];
+        for (int i = 0; i < nblk; ++i) f[i] = make_field(c->blk[i].p, Lt, V, P);
+        R = f[0];
+        Rt = f[1];
+        Pb = f[2];
+        Vb = f[3];
+        if (method == BK_BICGGR) {
+            Wb = f[4];
+            Ub = f[5];
+            Yb = f[6];
+        } else {
+            Tb = f[4];
+            Zb = f[5];
+            Ptmp = f[6];
+        }
+        if (mixed) {
+            BK_TRY(c->Xlo.ensure(field_bytes(Lt, V, BK_FP32)));
+            Xlo = make_field(c->Xlo.p, Lt, V, BK_FP32);
+        }
+        // small arrays (complex FP64 unless noted)
+        const int nc = ncoef();
+        const size_t nsmall = (size_t)6 * nc + 3 * Lt + Lt + 3 * nsys;
+        BK_TRY(c->small.ensure(nsmall * sizeof(double2) + 3 * nsys * sizeof(int) + 256));
+        double2* q = c->small.as<double2>();
+        G_V = (double*)q;
+        q += nc;
+        G_RR = (double*)q;
+        q += nc;
+        G_RRn = (double*)q;
+        q += nc;
+        alpha = (double*)q;
+        q += nc;
+        gam = (double*)q;
+        q += nc;
+        G_Z = (double*)q;
+        q += nc;
+        dots = (double*)q;
+        q += 3 * Lt;
+        zeta = (double*)q;
+        q += nsys;
+        mzeta = (double*)q;
+        q += nsys;
+        izeta = (double*)q;
+        q += nsys;
+        // readback region: rn (Lt complex), info_a, info_g, zbad (nsys ints each)
+        rb_dev = (char*)q;
+        rn = (double*)q;
+        q += Lt;
+        int* qi = (int*)q;
+        info_a = qi;
+        info_g = qi + nsys;
+        zbad = qi + 2 * nsys;
+        rb_bytes = (size_t)Lt * sizeof(double2) + 3 * nsys * sizeof(int);
+        BK_TRY(c->rb_host.ensure(rb_bytes));
+        rbh = (char*)c->rb_host.p;
+        rn_h = (double*)rbh;
+        info_a_h = (int*)(rbh + (size_t)Lt * sizeof(double2));
+        info_g_h = info_a_h + nsys;
+        zbad_h = info_a_h + 2 * nsys;
+        BK_CUDA_TRY(cudaMemsetAsync(info_a, 0, 3 * nsys * sizeof(int), st));
+        const size_t pb = std::max(gram_partial_bytes(part, V), coldot_partial_bytes(Lt, 3, V));
+        BK_TRY(c->spart.ensure(pb));
+        partial = c->spart.as<double>();
+        int maxL = 0;
+        for (int s = 0; s < nsys; ++s) maxL = std::max(maxL, part.col0[s + 1] - part.col0[s]);
+        gwork = nullptr;
+        if (maxL > 48) {
+            BK_TRY(c->gwork.ensure((size_t)2 * nc * sizeof(double2)));
+            gwork = c->gwork.as<double>();
+        }
+
+        // B, X0 into the FP64 device layout
+        BK_TRY(launch_pack(BK_FP64, Bc, B64, Lt, st));
+        launches++;
+        {
+            Field a[1] = {B64}, b[1] = {B64};
+            BK_TRY(coldot(BK_FP64, 1, a, b, rn));
+            BK_TRY(readback());
+            for (int j = 0; j < Lt; ++j) {
+                const double n2 = rn_h[2 * j];
+                if (!std::isfinite(n2)) {
+                    bk_set_error("right-hand side column %d is not finite", j);
+                    return BK_ERR_NONFINITE;
+                }
+                if (n2 <= 0.0) {
+                    bk_set_error("right-hand side column %d is zero", j);
+                    return BK_ERR_INVALID_ARG;
+                }
+                bnorm[j] = std::sqrt(n2);
+            }
+        }
+        if (prm->x0_given) {
+            BK_TRY(launch_pack(BK_FP64, Xc, X64, Lt, st));
+            launches++;
+            Field a[1] = {X64}, b[1] = {X64};
+            BK_TRY(coldot(BK_FP64, 1, a, b, rn));
+            BK_TRY(readback());
+            for (int j = 0; j < Lt; ++j)
+                if (!std::isfinite(rn_h[2 * j])) {
+                    bk_set_error("initial guess column %d is not finite", j);
+                    return BK_ERR_NONFINITE;
+                }
+            BK_TRY(dslash(BK_FP64, X64, R64, B64, 0, Lt, 1));
+            for (int s = 0; s < nsys; ++s) mv64[s]++;
+        } else {
+            BK_CUDA_TRY(cudaMemsetAsync(X64.data, 0, fb64, st));
+            BK_CUDA_TRY(cudaMemcpyAsync(R64.data, B64.data, fb64, cudaMemcpyDeviceToDevice, st));
+        }
+        if (mixed) BK_CUDA_TRY(cudaMemsetAsync(Xlo.data, 0, field_bytes(Lt, V, BK_FP32), st));
+        BK_TRY(launch_cast(BK_FP64, R64, P, R, Lt, st));
+        launches++;
+        if (prm->rtilde_random) {
+            dim3 grid((V + 127) / 128, Lt);
+            switch (P) {
+                case BK_FP64: k_random<BK_FP64><<<grid, 128, 0, st>>>(Rt, V, prm->seed); break;
+                case BK_FP32: k_random<BK_FP32><<<grid, 128, 0, st>>>(Rt, V, prm->seed); break;
+                default: k_random<BK_FP16><<<grid, 128, 0, st>>>(Rt, V, prm->seed); break;
+            }
+            BK_CUDA_TRY(cudaGetLastError());
+            launches++;
+        } else {
+            BK_CUDA_TRY(cudaMemcpyAsync(Rt.data, R.data, fbp, cudaMemcpyDeviceToDevice, st));
+        }
+        BK_CUDA_TRY(cudaMemcpyAsync(Pb.data, R.data, fbp, cudaMemcpyDeviceToDevice, st));
+        if (method == BK_BICGGR) {
+            BK_TRY(dslash(P, R, Wb, R, 0, Lt, 0));  // V_0 = W_0 = A R_0
+            for (int s = 0; s < nsys; ++s) mv[s]++;
+            BK_CUDA_TRY(cudaMemcpyAsync(Vb.data, Wb.data, fbp, cudaMemcpyDeviceToDevice, st));
+            BK_TRY(gram(Rt, R, G_RR));
+        }
+        BK_TRY(residual_norms());
+        for (int s = 0; s < nsys; ++s) {
+            const double m = sys_max(s);
+            hist[s].push_back(m);
+            rmax_since[s] = m;
+            if (m <= prm->tol) done[s] = 1;
+        }
+        update_active();
+        return BK_OK;
+    }
+
+    void update_active() {
+        unsigned a = 0;
+        for (int s = 0; s < nsys; ++s)
+            if (done[s] == 0) a |= 1u << s;
+        part.active = a;
+    }
+
+    // After the new residual R_{k+1} exists: stopping rule, breakdown flags,
+    // reliable updates.  Returns via `done`.
+    bk_status check(int k) {
+        BK_TRY(residual_norms());
+        std::vector<int> upd;
+        for (int s = 0; s < nsys; ++s) {
+            if (done[s]) continue;
+            iters[s] = k + 1;
+            mv[s] += 2;
+            if (info_a_h[s] || info_g_h[s] || zbad_h[s]) {
+                done[s] = 2;
+                continue;
+            }
+            const double m = sys_max(s);
+            hist[s].push_back(m);
+            if (!std::isfinite(m)) {
+                done[s] = 2;
+                continue;
+            }
+            if (!mixed) {
+                if (m <= prm->tol) done[s] = 1;
+                continue;
+            }
+            rmax_since[s] = std::max(rmax_since[s], m);
+            const double delta = prm->reliable_delta > 0 ? prm->reliable_delta : 0.1;
+            if (m <= prm->tol || m < delta * rmax_since[s]) upd.push_back(s);
+        }
+        if (!upd.empty()) {
+            BK_TRY(reliable_update(upd));
+            for (int s : upd) {
+                const double m = sys_max(s);  // FP64 true residual
+                hist[s].back() = m;
+                rmax_since[s] = m;
+                if (m <= prm->tol) done[s] = 1;
+            }
+        }
+        update_active();
+        return BK_OK;
+    }
+
+    bk_status iterate_bicggr() {
+        for (int k = 0; k < prm->maxiter && part.active; ++k) {
+            {   // G_V = R~^H V; traces Tr(W^H R), Tr(W^H W)
+                BK_TRY(gram(Rt, Vb, G_V));
+                Field a[2] = {Wb, Wb}, b[2] = {R, Wb};
+                BK_TRY(coldot(P, 2, a, b, dots));
+                BK_TRY(scalars());
+            }
+            // alpha: (R~^H V) alpha = R~^H R
+            BK_TRY(small_solve(G_V, G_RR, nullptr, alpha, info_a));
+            {   // U = (P - zeta V) alpha;  X += zeta R + U
+                GenOp g = genop0();
+                g.nmi = 2;
+                g.Mi[0] = Pb;
+                g.Mi[1] = Vb;
+                g.ma[0] = nullptr;
+                g.ma_mult[0] = 1.0;
+                g.ma[1] = zeta;
+                g.ma_mult[1] = -1.0;
+                g.M = alpha;
+                g.hasY = 1;
+                g.Y = Ub;
+                g.ym = 1.0;
+                g.hasX = 1;
+                g.X = mixed ? Xlo : X64;
+                g.Xin = R;
+                g.xa = zeta;
+                g.xa_mult = 1.0;
+                g.xm = 1.0;
+                g.skip = info_a;
+                BK_TRY(genop(g));
+            }
+            BK_TRY(dslash(P, Ub, Yb, Ub, 0, Lt, 0));  // Y = A U
+            {   // R <- R - zeta W - Y
+                GenOp g = genop0();
+                g.ne = 3;
+                g.E[0] = R;
+                g.ea_mult[0] = 1.0;
+                g.E[1] = Wb;
+                g.ea[1] = zeta;
+                g.ea_mult[1] = -1.0;
+                g.E[2] = Yb;
+                g.ea_mult[2] = -1.0;
+                g.hasY = 1;
+                g.Y = R;
+                g.skip = info_a;
+                BK_TRY(genop(g));
+            }
+            const unsigned before = part.active;
+            BK_TRY(check(k));
+            // systems that stopped keep their state; the rest continue
+            part.active &= before;
+            if (!part.active) break;
+            BK_TRY(gram(Rt, R, G_RRn));          // R~^H R_{k+1}
+            BK_TRY(dslash(P, R, Wb, R, 0, Lt, 0));  // W = A R
+            // gamma: (R~^H R_k) gamma = R~^H R_{k+1} / zeta
+            BK_TRY(small_solve(G_RR, G_RRn, izeta, gam, info_g));
+            {   // P = R + U gamma
+                GenOp g = genop0();
+                g.ne = 1;
+                g.E[0] = R;
+                g.ea_mult[0] = 1.0;
+                g.nmi = 1;
+                g.Mi[0] = Ub;
+                g.ma_mult[0] = 1.0;
+                g.M = gam;
+                g.hasY = 1;
+                g.Y = Pb;
+                g.ym = 1.0;
+                g.skip = info_g;
+                BK_TRY(genop(g));
+                // V = W + Y gamma
+                g.E[0] = Wb;
+                g.Mi[0] = Yb;
+                g.Y = Vb;
+                BK_TRY(genop(g));
+            }
+            std::swap(G_RR, G_RRn);
+        }
+        return BK_OK;
+    }
+
+    bk_status iterate_bicgstab() {
+        for (int k = 0; k < prm->maxiter && part.active; ++k) {
+            BK_TRY(dslash(P, Pb, Vb, Pb, 0, Lt, 0));  // V = A P
+            BK_TRY(gram(Rt, Vb, G_V));
+            BK_TRY(gram(Rt, R, G_RR));
+            BK_TRY(small_solve(G_V, G_RR, nullptr, alpha, info_a));  // alpha
+            {   // T = R - V alpha
+                GenOp g = genop0();
+                g.ne = 1;
+                g.E[0] = R;
+                g.ea_mult[0] = 1.0;
+                g.nmi = 1;
+                g.Mi[0] = Vb;
+                g.ma_mult[0] = -1.0;
+                g.M = alpha;
+                g.hasY = 1;
+                g.Y = Tb;
+                g.ym = 1.0;
+                g.skip = info_a;
+                BK_TRY(genop(g));
+            }
+            BK_TRY(dslash(P, Tb, Zb, Tb, 0, Lt, 0));  // Z = A T
+            {
+                Field a[2] = {Zb, Zb}, b[2] = {Tb, Zb};
+                BK_TRY(coldot(P, 2, a, b, dots));  // Tr(Z^H T), Tr(Z^H Z)
+                BK_TRY(scalars());
+                BK_TRY(gram(Rt, Zb, G_Z));
+            }
+            // beta: (R~^H V) beta = -R~^H Z
+            {
+                const double m1[2] = {-1.0, 0.0};
+                launches += 1;
+                BK_TRY(launch_small_solve(G_V, G_Z, nullptr, gam, info_g, part, st, gwork, m1));
+            }
+            {   // X += P alpha + zeta T;  R = T - zeta Z
+                GenOp g = genop0();
+                g.ne = 2;
+                g.E[0] = Tb;
+                g.ea_mult[0] = 1.0;
+                g.E[1] = Zb;
+                g.ea[1] = zeta;
+                g.ea_mult[1] = -1.0;
+                g.nmi = 1;
+                g.Mi[0] = Pb;
+                g.ma_mult[0] = 1.0;
+                g.M = alpha;
+                g.hasY = 1;
+                g.Y = R;
+                g.ym = 0.0;
+                g.hasX = 1;
+                g.X = mixed ? Xlo : X64;
+                g.Xin = Tb;
+                g.xa = zeta;
+                g.xa_mult = 1.0;
+                g.xm = 1.0;
+                g.skip = info_a;
+                BK_TRY(genop(g));
+            }
+            const unsigned before = part.active;
+            BK_TRY(check(k));
+            part.active &= before;
+            if (!part.active) break;
+            {   // P = R + (P - zeta V) beta   (into Ptmp, then swap)
+                GenOp g = genop0();
+                g.ne = 1;
+                g.E[0] = R;
+                g.ea_mult[0] = 1.0;
+                g.nmi = 2;
+                g.Mi[0] = Pb;
+                g.ma_mult[0] = 1.0;
+                g.Mi[1] = Vb;
+                g.ma[1] = zeta;
+                g.ma_mult[1] = -1.0;
+                g.M = gam;
+                g.hasY = 1;
+                g.Y = Ptmp;
+                g.ym = 1.0;
+                g.skip = info_g;
+                BK_TRY(genop(g));
+                // systems skipped by genop keep P: copy is not needed because they stop
+                std::swap(Pb, Ptmp);
+            }
+        }
+        return BK_OK;
+    }
+
+    // Final FP64 true residual of every column and the solution in canonical layout.
+    bk_status finish(double* Xc) {
+        part.active = nsys >= 32 ? 0xffffffffu : ((1u << nsys) - 1u);
+        if (mixed) {
+            dim3 grid((V + 127) / 128, Lt);
+            k_accum<<<grid, 128, 0, st>>>(X64, Xlo, V);
+            BK_CUDA_TRY(cudaGetLastError());
+            launches++;
+        }
+        BK_TRY(dslash(BK_FP64, X64, R64, B64, 0, Lt, 1));
+        {
+            Field a[1] = {R64}, b[1] = {R64};
+            BK_TRY(coldot(BK_FP64, 1, a, b, rn));
+        }
+        BK_TRY(launch_unpack(BK_FP64, X64, Xc, Lt, st));
+        launches++;
+        BK_TRY(readback());
+        for (int j = 0; j < Lt; ++j) true_res[j] = rel(j);
+        return BK_OK;
+    }
+};
+
+}  // namespace
+
+static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, const double* kappa, const int* Ls,
+                            const double* B, double* X, bk_solve_info* info, void* stream) {
+    auto t0 = std::chrono::steady_clock::now();
+    BK_CHECK_ARG(c && prm && kappa && Ls && B && X && info, "null argument");
+    BK_CHECK_ARG(nsys >= 1 && nsys <= BK_MAX_SYS, "nsys must be in [1, 32]");
+    BK_CHECK_ARG(prm->method == BK_BICGSTAB || prm->method == BK_BICGGR, "unknown method");
+    BK_CHECK_ARG(valid_prec(prm->prec), "unknown precision");
+    BK_CHECK_ARG(prm->tol > 0 && prm->maxiter >= 0, "tol must be > 0 and maxiter >= 0");
+    int Lt = 0;
+    for (int s = 0; s < nsys; ++s) {
+        BK_CHECK_ARG(Ls[s] >= 1, "every system needs L >= 1");
+        Lt += Ls[s];
+    }
+    if (!c->has_gauge || !c->has_clover) {
+        bk_set_error("solve needs bk_upload_gauge and bk_build_clover first");
+        return BK_ERR_NO_GAUGE;
+    }
+    BK_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+
+    Solve S;
+    S.c = c;
+    S.prm = prm;
+    S.st = st;
+    S.nsys = nsys;
+    S.Lt = Lt;
+    S.V = c->V;
+    S.P = prm->prec;
+    S.method = prm->method;
+    S.mixed = prm->prec != BK_FP64;
+    S.part = make_part(nsys, Ls);
+    S.kcol.resize(Lt);
+    for (int s = 0; s < nsys; ++s)
+        for (int j = S.part.col0[s]; j < S.part.col0[s + 1]; ++j) S.kcol[j] = kappa[s];
+    S.bnorm.assign(Lt, 1.0);
+    S.done.assign(nsys, 0);
+    S.rmax_since.assign(nsys, 0.0);
+    S.iters.assign(nsys, 0);
+    S.mv.assign(nsys, 0);
+    S.mv64.assign(nsys, 0);
+    S.nrel.assign(nsys, 0);
+    S.hist.resize(nsys);
+    S.true_res.assign(Lt, 0.0);
+
+    const size_t canon_bytes = (size_t)Lt * c->V * 12 * sizeof(double2);
+    const double* Bd = B;
+    double* Xd = X;
+    if (prm->buffers_on_host) {
+        BK_TRY(c->canonB.ensure(canon_bytes));
+        BK_TRY(c->canonX.ensure(canon_bytes));
+        BK_CUDA_TRY(cudaMemcpyAsync(c->canonB.p, B, canon_bytes, cudaMemcpyHostToDevice, st));
+        if (prm->x0_given) BK_CUDA_TRY(cudaMemcpyAsync(c->canonX.p, X, canon_bytes, cudaMemcpyHostToDevice, st));
+        Bd = c->canonB.as<double>();
+        Xd = c->canonX.as<double>();
+    }
+
+    BK_TRY(S.setup(Bd, Xd));
+    if (prm->method == BK_BICGGR)
+        BK_TRY(S.iterate_bicggr());
+    else
+        BK_TRY(S.iterate_bicgstab());
+    BK_TRY(S.finish(Xd));
+    if (prm->buffers_on_host) {
+        BK_CUDA_TRY(cudaMemcpyAsync(X, Xd, canon_bytes, cudaMemcpyDeviceToHost, st));
+        BK_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+
+    bk_status result = BK_OK;
+    for (int s = 0; s < nsys; ++s) {
+        bk_solve_info& in = info[s];
+        in.iterations = S.iters[s];
+        in.matvecs = S.mv[s] + (prm->method == BK_BICGGR ? 0 : 0);
+        in.matvecs_fp64 = S.mv64[s] + 1;  // + final true residual
+        in.reliable_updates = S.nrel[s];
+        in.breakdown = S.done[s] == 2;
+        double tm = 0, rm = 0;
+        for (int j = S.part.col0[s]; j < S.part.col0[s + 1]; ++j) {
+            tm = std::max(tm, S.true_res[j]);
+            if (in.true_res) in.true_res[j - S.part.col0[s]] = S.true_res[j];
+        }
+        rm = S.hist[s].empty() ? 0.0 : S.hist[s].back();
+        in.true_res_max = tm;
+        in.rec_res_max = rm;
+        in.converged = S.done[s] == 1 && (S.mixed ? tm <= prm->tol * 10.0 : true);
+        if (in.history && prm->record_history) {
+            const int n = std::min((int)S.hist[s].size(), prm->maxiter + 1);
+            for (int i = 0; i < n; ++i) in.history[i] = S.hist[s][i];
+            in.history_len = n;
+        } else {
+            in.history_len = 0;
+        }
+        in.time_total_ms = ms;
+        in.time_dslash_ms = S.t_dslash;
+        in.time_dslash_inner_ms = S.t_dslash_inner;
+        in.n_dslash = S.n_dslash;
+        in.n_dslash_inner = S.n_dslash_inner;
+        in.n_launches = S.launches;
+        if (S.done[s] == 2 && result == BK_OK) result = BK_ERR_BREAKDOWN;
+        if (S.done[s] == 0 && result == BK_OK) result = BK_ERR_NOT_CONVERGED;
+    }
+    if (result == BK_ERR_BREAKDOWN) bk_set_error("an L x L solve broke down (singular or non-finite)");
+    if (result == BK_ERR_NOT_CONVERGED) bk_set_error("maxiter reached before the stopping rule was met");
+    return result;
+}
+
+extern "C" bk_status bk_block_solve(bk_ctx* c, const bk_solve_params* prm, double kappa, const double* B, double* X,
+                                    int L, bk_solve_info* info, void* stream) {
+    return solve_impl(c, prm, 1, &kappa, &L, B, X, info, stream);
+}
+
+extern "C" bk_status bk_block_solve_batched(bk_ctx* c, const bk_solve_params* prm, int nsys, const double* kappa,
+                                            const int* Ls, const double* B, double* X, bk_solve_info* info,
+                                            void* stream) {
+    return solve_impl(c, prm, nsys, kappa, Ls, B, X, info, stream);
+}

@@ -1,0 +1,102 @@
+// Host-side launchers of the device kernels, shared between translation
+// units.  All launchers enqueue on `st` and return BK_OK or BK_ERR_CUDA.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "bk_common.cuh"
+
+// ---------------------------------------------------------------- gauge.cu
+bk_status launch_gauge_convert(const double* Uin_dev, double2* U64, float2* U32, int V, cudaStream_t st);
+bk_status launch_clover_build(const double2* U64, double2* C64, float4* C32, const int dims[4], double csw,
+                              cudaStream_t st);
+
+// ---------------------------------------------------------------- dslash.cu
+struct DslashOp {
+    Field x, y, b;         // y = D x, or y = b - D x when residual != 0
+    const void* U;         // gauge [4][9][V], double2 (FP64) or float2
+    const void* clov;      // packed clover, double2 [36][V] or float4 [18][V]
+    int dims[4];
+    int V;
+    int col0, ncol;        // columns [col0, col0 + ncol) of x, y, b
+    int residual;
+    const double* kappa;   // host array, ncol entries (kappa of column col0 + j)
+    int site_block;        // launch shape: sites per thread block (0 = default)
+    int col_block;         // columns per thread block (0 = default)
+};
+bk_status launch_dslash(int prec, const DslashOp& op, cudaStream_t st);
+
+// canonical FP64 [col][site][12] complex <-> device layout
+bk_status launch_pack(int prec, const double* canon, Field f, int L, cudaStream_t st);
+bk_status launch_unpack(int prec, Field f, double* canon, int L, cudaStream_t st);
+// device layout conversion between precisions (same column count)
+bk_status launch_cast(int pin, Field in, int pout, Field out, int L, cudaStream_t st);
+// canonical gamma_5
+bk_status launch_gamma5_canon(const double* X, double* Y, long long nsites_cols, cudaStream_t st);
+
+// ---------------------------------------------------------------- blas.cu
+// Partition of the columns into independent systems: system s owns columns
+// [col0[s], col0[s+1]).  coef_off[s] = offset (in complex entries) of system
+// s's L_s x L_s matrix inside a packed coefficient array.
+struct SysPart {
+    int nsys;
+    int col0[BK_MAX_SYS + 1];
+    int coef_off[BK_MAX_SYS + 1];
+    unsigned active;       // bit s set: system s is still iterating
+};
+SysPart make_part(int nsys, const int* Ls);
+SysPart single_part(int L);
+
+// Block-diagonal Gram matrices G_s = A_s^H B_s (packed by coef_off, complex FP64).
+// `partial` is scratch of gram_partial_bytes() bytes.
+size_t gram_partial_bytes(const SysPart& p, int V);
+bk_status launch_gram(int prec, Field A, Field B, const SysPart& p, double* G, double* partial, int V,
+                      cudaStream_t st);
+
+// Column dot products: out[k * L + j] = (A_k)_j^H (B_k)_j for pairs k < npair.
+size_t coldot_partial_bytes(int L, int npair, int V);
+bk_status launch_coldot(int prec, int npair, const Field* A, const Field* B, int L, double* out,
+                        double* partial, int V, cudaStream_t st);
+
+// Y_j = Z_j + c_s * sum_{i in s} X_i M_s[i][j]  (Z may be null; c per system, complex FP64)
+bk_status launch_xmy(int prec, Field X, const double* M, const double* c_dev, Field Z, bool hasZ, Field Y,
+                     const SysPart& p, int V, cudaStream_t st);
+
+// Small dense solves, one thread block per system: Xs_s = G_s^{-1} (scale_s H_s),
+// scale_s a complex device scalar (null = 1).  info[s] = 0 or pivot index + 1.
+// `gwork` (2 * sum L_s^2 complex FP64) is needed when some L_s > 48.  When
+// scale_dev is null the complex host value scale_host[2] (or 1) is used.
+bk_status launch_small_solve(const double* G, const double* H, const double* scale_dev, double* Xs, int* info,
+                             const SysPart& p, cudaStream_t st, double* gwork, const double* scale_host = nullptr);
+
+// Fused block update (see blas.cu):
+//   matpart_j = sum_{i in s} (sum_u ma_u Mi_u,i) M_s[i][j]
+//   Y_j = sum_t ea_t E_t,j + ym matpart_j;   X_j += xa Xin_j + xm matpart_j
+// Coefficients: mult * (ptr ? ptr[s] : 1), ptr = complex FP64 per system.
+// Y may alias an E_t; neither Y nor X may alias an Mi_u.  X is FP64 for FP64
+// blocks, FP32 otherwise.  Columns of inactive systems, or of systems with
+// skip[s] != 0, are left untouched.
+#define GENOP_MAXE 3
+#define GENOP_MAXMI 2
+struct GenOp {
+    int ne;
+    Field E[GENOP_MAXE];
+    const double* ea[GENOP_MAXE];
+    double ea_mult[GENOP_MAXE];
+    int nmi;
+    Field Mi[GENOP_MAXMI];
+    const double* ma[GENOP_MAXMI];
+    double ma_mult[GENOP_MAXMI];
+    const double* M;
+    int hasY;
+    Field Y;
+    double ym;
+    int hasX;
+    Field X, Xin;
+    const double* xa;
+    double xa_mult;
+    double xm;
+    const int* skip;
+    SysPart p;
+};
+bk_status launch_genop(int prec, const GenOp& g, int V, cudaStream_t st);

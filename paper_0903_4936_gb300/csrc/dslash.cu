@@ -1,0 +1,420 @@
+// Multi-RHS O(a)-improved Wilson-Dirac operator, Eq. (wd-op) of arXiv:0903.4936,
+// and the layout-conversion kernels around it.
+//
+// One thread computes one (site, column) output spinor:
+//     y = x - kappa_c * ( sum_mu [(1 - gamma_mu) U_mu(n) x(n+mu)
+//                                 + (1 + gamma_mu) U_mu(n-mu)^+ x(n-mu)] + C(n) x(n) )
+// The threads of a block cover `SX` consecutive sites times `BY` columns, so
+// every gauge link and clover block a block needs is fetched from DRAM once
+// and served to all of its columns from L1 (the multi-vector reuse the paper
+// exploits on its CPU, Section 4.3).  Each (1 -+ gamma_mu) has rank two: the
+// neighbour spinor is projected to two colour vectors, multiplied by the 3x3
+// link, and expanded again.  With the printed gamma matrices, for projector
+// (1 + s gamma_mu) (s = -1 forward, +1 backward) and h = (h0, h1):
+//   mu=x: h0 = q0 - i s q3, h1 = q1 - i s q2;  out = (h0, h1,  i s h1,  i s h0)
+//   mu=y: h0 = q0 -   s q3, h1 = q1 +   s q2;  out = (h0, h1,    s h1,   -s h0)
+//   mu=z: h0 = q0 - i s q2, h1 = q1 + i s q3;  out = (h0, h1,  i s h0, -i s h1)
+//   mu=t: s=+1: out = (2 q0, 2 q1, 0, 0);  s=-1: out = (0, 0, 2 q2, 2 q3)
+#include "bk_common.cuh"
+#include "bk_kernels.h"
+
+namespace {
+
+template <int P>
+struct DArgs {
+    Field x, y, b;
+    const typename Prec<P>::link* __restrict__ U;
+    const typename Prec<P>::clov* __restrict__ C;
+    int L[4], st[4];
+    int V, col0, ncol, residual, SX;
+    double kappa[BK_MAX_COLS];
+};
+
+template <int MU, int S, typename R>
+__device__ __forceinline__ void project(const cx<R> (&q)[12], cx<R> (&h)[6]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const cx<R> q0 = q[a], q1 = q[3 + a], q2 = q[6 + a], q3 = q[9 + a];
+        if constexpr (MU == 0) {
+            h[a] = S > 0 ? q0 - ti(q3) : q0 + ti(q3);
+            h[3 + a] = S > 0 ? q1 - ti(q2) : q1 + ti(q2);
+        } else if constexpr (MU == 1) {
+            h[a] = S > 0 ? q0 - q3 : q0 + q3;
+            h[3 + a] = S > 0 ? q1 + q2 : q1 - q2;
+        } else if constexpr (MU == 2) {
+            h[a] = S > 0 ? q0 - ti(q2) : q0 + ti(q2);
+            h[3 + a] = S > 0 ? q1 + ti(q3) : q1 - ti(q3);
+        } else {
+            h[a] = S > 0 ? q0 : q2;
+            h[3 + a] = S > 0 ? q1 : q3;
+        }
+    }
+}
+
+template <int MU, int S, typename R>
+__device__ __forceinline__ void reconstruct(const cx<R> (&w)[6], cx<R> (&acc)[12]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const cx<R> w0 = w[a], w1 = w[3 + a];
+        if constexpr (MU == 0) {
+            acc[a] = acc[a] + w0;
+            acc[3 + a] = acc[3 + a] + w1;
+            acc[6 + a] = S > 0 ? acc[6 + a] + ti(w1) : acc[6 + a] - ti(w1);
+            acc[9 + a] = S > 0 ? acc[9 + a] + ti(w0) : acc[9 + a] - ti(w0);
+        } else if constexpr (MU == 1) {
+            acc[a] = acc[a] + w0;
+            acc[3 + a] = acc[3 + a] + w1;
+            acc[6 + a] = S > 0 ? acc[6 + a] + w1 : acc[6 + a] - w1;
+            acc[9 + a] = S > 0 ? acc[9 + a] - w0 : acc[9 + a] + w0;
+        } else if constexpr (MU == 2) {
+            acc[a] = acc[a] + w0;
+            acc[3 + a] = acc[3 + a] + w1;
+            acc[6 + a] = S > 0 ? acc[6 + a] + ti(w0) : acc[6 + a] - ti(w0);
+            acc[9 + a] = S > 0 ? acc[9 + a] - ti(w1) : acc[9 + a] + ti(w1);
+        } else {
+            const R two = R(2);
+            if constexpr (S > 0) {
+                acc[a] = acc[a] + two * w0;
+                acc[3 + a] = acc[3 + a] + two * w1;
+            } else {
+                acc[6 + a] = acc[6 + a] + two * w0;
+                acc[9 + a] = acc[9 + a] + two * w1;
+            }
+        }
+    }
+}
+
+template <typename L, typename R>
+__device__ __forceinline__ void load_link(const L* __restrict__ U, int mu, int s, int V, cx<R> (&u)[9]) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        L q = __ldg(U + (size_t)(mu * 9 + k) * V + s);
+        u[k] = mk((R)q.x, (R)q.y);
+    }
+}
+
+template <int P, int MU>
+__device__ __forceinline__ void hop_dir(const DArgs<P>& a, const int (&co)[4], int s, int c,
+                                        cx<typename Prec<P>::real> (&acc)[12]) {
+    using R = typename Prec<P>::real;
+    const int Lm = a.L[MU], sm = a.st[MU];
+    const int sf = co[MU] == Lm - 1 ? s - (Lm - 1) * sm : s + sm;
+    const int sb = co[MU] == 0 ? s + (Lm - 1) * sm : s - sm;
+    {   // forward: (1 - gamma_mu) U_mu(n) x(n + mu)
+        cx<R> q[12], h[6], w[6], u[9];
+        load_spinor<P>(a.x, c, sf, q);
+        project<MU, -1>(q, h);
+        load_link(a.U, MU, s, a.V, u);
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                cx<R> t = u[3 * i] * h[3 * hh];
+                cmac(t, u[3 * i + 1], h[3 * hh + 1]);
+                cmac(t, u[3 * i + 2], h[3 * hh + 2]);
+                w[3 * hh + i] = t;
+            }
+        reconstruct<MU, -1>(w, acc);
+    }
+    {   // backward: (1 + gamma_mu) U_mu(n - mu)^+ x(n - mu)
+        cx<R> q[12], h[6], w[6], u[9];
+        load_spinor<P>(a.x, c, sb, q);
+        project<MU, +1>(q, h);
+        load_link(a.U, MU, sb, a.V, u);
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                cx<R> t = mk(R(0), R(0));
+                cjmac(t, u[i], h[3 * hh]);
+                cjmac(t, u[3 + i], h[3 * hh + 1]);
+                cjmac(t, u[6 + i], h[3 * hh + 2]);
+                w[3 * hh + i] = t;
+            }
+        reconstruct<MU, +1>(w, acc);
+    }
+}
+
+// y = A x for a packed 6x6 Hermitian block (36 reals: 6 diagonal, 15 complex lower).
+template <typename R>
+__device__ __forceinline__ void herm6(const R (&m)[36], const cx<R> (&x)[6], cx<R> (&y)[6]) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) y[i] = m[i] * x[i];
+    int p = 0;
+#pragma unroll
+    for (int i = 1; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < i; ++j, ++p) {
+            const cx<R> A = mk(m[6 + 2 * p], m[7 + 2 * p]);
+            cmac(y[i], A, x[j]);
+            cjmac(y[j], A, x[i]);
+        }
+}
+
+template <typename R>
+__device__ __forceinline__ void load_clov_block(const double2* __restrict__ C, int blk, int s, int V, R (&m)[36]) {
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+        double2 v = __ldg(C + (size_t)(18 * blk + q) * V + s);
+        m[2 * q] = (R)v.x;
+        m[2 * q + 1] = (R)v.y;
+    }
+}
+template <typename R>
+__device__ __forceinline__ void load_clov_block(const float4* __restrict__ C, int blk, int s, int V, R (&m)[36]) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        float4 v = __ldg(C + (size_t)(9 * blk + q) * V + s);
+        m[4 * q] = v.x;
+        m[4 * q + 1] = v.y;
+        m[4 * q + 2] = v.z;
+        m[4 * q + 3] = v.w;
+    }
+}
+
+// FP64 needs more registers per thread: cap its blocks at 256 threads.
+template <int P>
+constexpr int dslash_max_threads() { return P == BK_FP64 ? 256 : 512; }
+
+template <int P>
+__global__ void __launch_bounds__(dslash_max_threads<P>()) k_dslash(const __grid_constant__ DArgs<P> a) {
+    using R = typename Prec<P>::real;
+    const int tid = threadIdx.x;
+    const int s = blockIdx.x * a.SX + (tid % a.SX);
+    const int cl = blockIdx.y * (blockDim.x / a.SX) + tid / a.SX;
+    if (s >= a.V || cl >= a.ncol) return;
+    const int c = a.col0 + cl;
+    int co[4];
+    {
+        int r = s;
+        co[0] = r % a.L[0];
+        r /= a.L[0];
+        co[1] = r % a.L[1];
+        r /= a.L[1];
+        co[2] = r % a.L[2];
+        co[3] = r / a.L[2];
+    }
+    cx<R> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = mk(R(0), R(0));
+    hop_dir<P, 0>(a, co, s, c, acc);
+    hop_dir<P, 1>(a, co, s, c, acc);
+    hop_dir<P, 2>(a, co, s, c, acc);
+    hop_dir<P, 3>(a, co, s, c, acc);
+
+    cx<R> q[12];
+    load_spinor<P>(a.x, c, s, q);
+    {   // clover: chiral blocks act on a = u + l and b = u - l
+        cx<R> v[6], yv[6];
+        R m[36];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = q[k] + q[k + 6];
+        load_clov_block(a.C, 0, s, a.V, m);
+        herm6(m, v, yv);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            acc[k] = acc[k] + yv[k];
+            acc[k + 6] = acc[k + 6] + yv[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = q[k] - q[k + 6];
+        load_clov_block(a.C, 1, s, a.V, m);
+        herm6(m, v, yv);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            acc[k] = acc[k] + yv[k];
+            acc[k + 6] = acc[k + 6] - yv[k];
+        }
+    }
+    const R kap = (R)a.kappa[cl];
+    cx<R> out[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[k] = q[k] - kap * acc[k];
+    if (a.residual) {
+        cx<R> bb[12];
+        load_spinor<P>(a.b, c, s, bb);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) out[k] = bb[k] - out[k];
+    }
+    store_spinor<P>(a.y, c, s, out);
+}
+
+template <int P>
+bk_status dslash_impl(const DslashOp& op, cudaStream_t st) {
+    if (op.ncol <= 0) return BK_OK;
+    if (op.ncol > BK_MAX_COLS) {
+        // split into launches of at most BK_MAX_COLS columns
+        for (int c0 = 0; c0 < op.ncol; c0 += BK_MAX_COLS) {
+            DslashOp sub = op;
+            sub.col0 = op.col0 + c0;
+            sub.ncol = op.ncol - c0 < BK_MAX_COLS ? op.ncol - c0 : BK_MAX_COLS;
+            sub.kappa = op.kappa + c0;
+            bk_status e = dslash_impl<P>(sub, st);
+            if (e != BK_OK) return e;
+        }
+        return BK_OK;
+    }
+    DArgs<P> a;
+    a.x = op.x;
+    a.y = op.y;
+    a.b = op.b;
+    a.U = (const typename Prec<P>::link*)op.U;
+    a.C = (const typename Prec<P>::clov*)op.clov;
+    int stride = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        a.L[mu] = op.dims[mu];
+        a.st[mu] = stride;
+        stride *= op.dims[mu];
+    }
+    a.V = op.V;
+    a.col0 = op.col0;
+    a.ncol = op.ncol;
+    a.residual = op.residual;
+    for (int j = 0; j < op.ncol; ++j) a.kappa[j] = op.kappa[j];
+    // Launch shape: BY columns x SX sites per block.
+    int BY = op.col_block, SX = op.site_block;
+    if (BY <= 0) {
+        const int nyb = (op.ncol + 15) / 16;
+        BY = (op.ncol + nyb - 1) / nyb;
+    }
+    if (SX <= 0) SX = BY <= 8 ? 32 : 16;
+    const int maxt = dslash_max_threads<P>();
+    if (SX > maxt) SX = maxt;
+    if (SX * BY > maxt) BY = maxt / SX;
+    a.SX = SX;
+    dim3 grid((op.V + SX - 1) / SX, (op.ncol + BY - 1) / BY);
+    k_dslash<P><<<grid, SX * BY, 0, st>>>(a);
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}
+
+// ----------------------------------------------------------------- conversions
+
+template <int P>
+__global__ void k_pack(const double2* __restrict__ canon, Field f, int V) {
+    using R = typename Prec<P>::real;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (s >= V) return;
+    const double2* p = canon + ((size_t)c * V + s) * 12;
+    cx<R> v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        double2 q = p[k];
+        v[k] = mk((R)q.x, (R)q.y);
+    }
+    store_spinor<P>(f, c, s, v);
+}
+
+template <int P>
+__global__ void k_unpack(Field f, double2* __restrict__ canon, int V) {
+    using R = typename Prec<P>::real;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (s >= V) return;
+    cx<R> v[12];
+    load_spinor<P>(f, c, s, v);
+    double2* p = canon + ((size_t)c * V + s) * 12;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[k] = make_double2((double)v[k].r, (double)v[k].i);
+}
+
+template <int PI, int PO>
+__global__ void k_cast(Field in, Field out, int V) {
+    using RI = typename Prec<PI>::real;
+    using RO = typename Prec<PO>::real;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (s >= V) return;
+    cx<RI> v[12];
+    load_spinor<PI>(in, c, s, v);
+    cx<RO> w[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) w[k] = mk((RO)v[k].r, (RO)v[k].i);
+    store_spinor<PO>(out, c, s, w);
+}
+
+__global__ void k_gamma5(const double2* __restrict__ X, double2* __restrict__ Y, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = X[i * 12 + k];
+    // gamma_5 of Section 2: spin 0 <-> 2, 1 <-> 3, all entries +1
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        Y[i * 12 + a] = v[6 + a];
+        Y[i * 12 + 3 + a] = v[9 + a];
+        Y[i * 12 + 6 + a] = v[a];
+        Y[i * 12 + 9 + a] = v[3 + a];
+    }
+}
+
+}  // namespace
+
+bk_status launch_dslash(int prec, const DslashOp& op, cudaStream_t st) {
+    switch (prec) {
+        case BK_FP64: return dslash_impl<BK_FP64>(op, st);
+        case BK_FP32: return dslash_impl<BK_FP32>(op, st);
+        case BK_FP16: return dslash_impl<BK_FP16>(op, st);
+    }
+    return BK_ERR_INVALID_ARG;
+}
+
+bk_status launch_pack(int prec, const double* canon, Field f, int L, cudaStream_t st) {
+    if (L <= 0) return BK_OK;
+    dim3 grid((f.V + 127) / 128, L);
+    const double2* c = (const double2*)canon;
+    switch (prec) {
+        case BK_FP64: k_pack<BK_FP64><<<grid, 128, 0, st>>>(c, f, f.V); break;
+        case BK_FP32: k_pack<BK_FP32><<<grid, 128, 0, st>>>(c, f, f.V); break;
+        case BK_FP16: k_pack<BK_FP16><<<grid, 128, 0, st>>>(c, f, f.V); break;
+        default: return BK_ERR_INVALID_ARG;
+    }
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}
+
+bk_status launch_unpack(int prec, Field f, double* canon, int L, cudaStream_t st) {
+    if (L <= 0) return BK_OK;
+    dim3 grid((f.V + 127) / 128, L);
+    double2* c = (double2*)canon;
+    switch (prec) {
+        case BK_FP64: k_unpack<BK_FP64><<<grid, 128, 0, st>>>(f, c, f.V); break;
+        case BK_FP32: k_unpack<BK_FP32><<<grid, 128, 0, st>>>(f, c, f.V); break;
+        case BK_FP16: k_unpack<BK_FP16><<<grid, 128, 0, st>>>(f, c, f.V); break;
+        default: return BK_ERR_INVALID_ARG;
+    }
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}
+
+bk_status launch_cast(int pin, Field in, int pout, Field out, int L, cudaStream_t st) {
+    if (L <= 0) return BK_OK;
+    dim3 grid((in.V + 127) / 128, L);
+    const int V = in.V;
+#define BK_CAST(A, B)                                              \
+    if (pin == A && pout == B) {                                   \
+        k_cast<A, B><<<grid, 128, 0, st>>>(in, out, V);            \
+        BK_CUDA_TRY(cudaGetLastError());                           \
+        return BK_OK;                                              \
+    }
+    BK_CAST(BK_FP64, BK_FP32)
+    BK_CAST(BK_FP64, BK_FP16)
+    BK_CAST(BK_FP32, BK_FP64)
+    BK_CAST(BK_FP16, BK_FP64)
+    BK_CAST(BK_FP32, BK_FP16)
+    BK_CAST(BK_FP16, BK_FP32)
+    BK_CAST(BK_FP64, BK_FP64)
+    BK_CAST(BK_FP32, BK_FP32)
+    BK_CAST(BK_FP16, BK_FP16)
+#undef BK_CAST
+    return BK_ERR_INVALID_ARG;
+}
+
+bk_status launch_gamma5_canon(const double* X, double* Y, long long n, cudaStream_t st) {
+    if (n <= 0) return BK_OK;
+    k_gamma5<<<(unsigned)((n + 127) / 128), 128, 0, st>>>((const double2*)X, (double2*)Y, n);
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}

@@ -1,0 +1,272 @@
+// Gauge-field upload and clover-term construction (Section 2 of arXiv:0903.4936).
+//
+// Device gauge layout: [mu][9 = 3a + b][site] complex, FP64 (double2) and
+// FP32 (float2) copies, so that a warp reading one matrix element for 32
+// consecutive sites issues one coalesced transaction.
+//
+// Clover layout: 72 reals per site, [72/k][site] chunks of k reals (FP64:
+// double2, FP32: float4).  The site term C(n) = c_SW sum_{mu,nu} (i/2)
+// sigma_mu_nu F_mu_nu(n) commutes with gamma_5, so in the basis
+// a = u + l, b = u - l (u = spins 0,1, l = spins 2,3) it is block diagonal:
+//     (C q)_u = A' a + B' b,   (C q)_l = A' a - B' b,
+// with A' = (c_SW/2) A, B' = (c_SW/2) B, and with the printed gamma matrices
+//     A = [[-G3, -G1 + i G2], [-G1 - i G2, G3]],
+//     G1 = F_23 + F_14, G2 = F_31 + F_24, G3 = F_12 + F_34
+// (B: the same with F_14, F_24, F_34 negated).  Each 6x6 Hermitian block is
+// stored as 6 real diagonal entries followed by the 15 complex entries below
+// the diagonal in row order (1,0),(2,0),(2,1),(3,0),...,(5,4).
+#include "bk_common.cuh"
+#include "bk_kernels.h"
+
+namespace {
+
+struct M3 {
+    cx<double> m[3][3];
+};
+
+__device__ __forceinline__ M3 ldU(const double2* __restrict__ U, int mu, int s, int V) {
+    M3 r;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            double2 q = U[(size_t)(mu * 9 + a * 3 + b) * V + s];
+            r.m[a][b] = mk(q.x, q.y);
+        }
+    return r;
+}
+
+// a * b, a * b^dag, a^dag * b
+__device__ __forceinline__ M3 mm(const M3& a, const M3& b) {
+    M3 r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cx<double> s = mk(0.0, 0.0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cmac(s, a.m[i][k], b.m[k][j]);
+            r.m[i][j] = s;
+        }
+    return r;
+}
+__device__ __forceinline__ M3 mmd(const M3& a, const M3& b) {
+    M3 r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cx<double> s = mk(0.0, 0.0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cmac(s, a.m[i][k], cj(b.m[j][k]));
+            r.m[i][j] = s;
+        }
+    return r;
+}
+__device__ __forceinline__ M3 mdm(const M3& a, const M3& b) {
+    M3 r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cx<double> s = mk(0.0, 0.0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cjmac(s, a.m[k][i], b.m[k][j]);
+            r.m[i][j] = s;
+        }
+    return r;
+}
+
+// a^dag * b^dag
+__device__ __forceinline__ M3 mdd(const M3& a, const M3& b) {
+    M3 r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cx<double> s = mk(0.0, 0.0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cmac(s, cj(a.m[k][i]), cj(b.m[j][k]));
+            r.m[i][j] = s;
+        }
+    return r;
+}
+
+struct Geo {
+    int L[4];
+    int st[4];
+};
+
+__device__ __forceinline__ int hop(const Geo& g, const int (&c)[4], int s, int mu, int d) {
+    int x = c[mu] + d;
+    int s2 = s + d * g.st[mu];
+    if (x < 0) s2 += g.L[mu] * g.st[mu];
+    if (x >= g.L[mu]) s2 -= g.L[mu] * g.st[mu];
+    return s2;
+}
+
+// F_mu_nu(n) from the four leaves, read as closed paths:
+//   P1 = U_mu(n) U_nu(n+mu) U_mu(n+nu)^+ U_nu(n)^+
+//   P2 = U_nu(n) U_mu(n-mu+nu)^+ U_nu(n-mu)^+ U_mu(n-mu)
+//   P3 = U_mu(n-mu)^+ U_nu(n-mu-nu)^+ U_mu(n-mu-nu) U_nu(n-nu)
+//   P4 = U_nu(n-nu)^+ U_mu(n-nu) U_nu(n+mu-nu) U_mu(n)^+
+// F = (1/4) sum_i (P_i - P_i^+) / (2i).
+__device__ M3 field_strength(const double2* __restrict__ U, const Geo& g, const int (&c)[4], int s, int V,
+                             int mu, int nu) {
+    const int sp_m = hop(g, c, s, mu, +1), sm_m = hop(g, c, s, mu, -1);
+    const int sp_n = hop(g, c, s, nu, +1), sm_n = hop(g, c, s, nu, -1);
+    int cm[4] = {c[0], c[1], c[2], c[3]};
+    cm[mu] = (c[mu] + g.L[mu] - 1) % g.L[mu];
+    const int sm_m_p_n = hop(g, cm, sm_m, nu, +1);
+    const int sm_m_m_n = hop(g, cm, sm_m, nu, -1);
+    int cp[4] = {c[0], c[1], c[2], c[3]};
+    cp[mu] = (c[mu] + 1) % g.L[mu];
+    const int sp_m_m_n = hop(g, cp, sp_m, nu, -1);
+
+    const M3 Um = ldU(U, mu, s, V), Un = ldU(U, nu, s, V);
+    M3 Q;
+    // P1
+    M3 t = mm(Um, ldU(U, nu, sp_m, V));
+    t = mmd(t, ldU(U, mu, sp_n, V));
+    M3 P = mmd(t, Un);
+    Q = P;
+    // P2
+    t = mmd(Un, ldU(U, mu, sm_m_p_n, V));
+    t = mmd(t, ldU(U, nu, sm_m, V));
+    P = mm(t, ldU(U, mu, sm_m, V));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Q.m[i][j] = Q.m[i][j] + P.m[i][j];
+    // P3
+    t = mdd(ldU(U, mu, sm_m, V), ldU(U, nu, sm_m_m_n, V));
+    t = mm(t, ldU(U, mu, sm_m_m_n, V));
+    P = mm(t, ldU(U, nu, sm_n, V));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Q.m[i][j] = Q.m[i][j] + P.m[i][j];
+    // P4
+    t = mdm(ldU(U, nu, sm_n, V), ldU(U, mu, sm_n, V));
+    t = mm(t, ldU(U, nu, sp_m_m_n, V));
+    P = mmd(t, Um);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Q.m[i][j] = Q.m[i][j] + P.m[i][j];
+    // F = -(i/8) (Q - Q^+)
+    M3 F;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cx<double> d = Q.m[i][j] - cj(Q.m[j][i]);
+            F.m[i][j] = mk(d.i * 0.125, -d.r * 0.125);
+        }
+    return F;
+}
+
+__global__ void k_gauge_convert(const double2* __restrict__ Uin, double2* __restrict__ U64,
+                                float2* __restrict__ U32, int V) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int mu = blockIdx.y;
+    if (s >= V) return;
+    const double2* p = Uin + ((size_t)mu * V + s) * 9;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        double2 q = p[k];
+        U64[(size_t)(mu * 9 + k) * V + s] = q;
+        U32[(size_t)(mu * 9 + k) * V + s] = make_float2((float)q.x, (float)q.y);
+    }
+}
+
+// Chiral 6x6 block from (G1, G2, G3), scaled: blk = scale * [[-G3, -G1 + iG2], [-G1 - iG2, G3]].
+__device__ __forceinline__ cx<double> chiral_elem(const M3& G1, const M3& G2, const M3& G3, int i, int j) {
+    const int si = i / 3, ci = i % 3, sj = j / 3, cj2 = j % 3;
+    const cx<double> g1 = G1.m[ci][cj2], g2 = G2.m[ci][cj2], g3 = G3.m[ci][cj2];
+    if (si == 0 && sj == 0) return mk(-g3.r, -g3.i);
+    if (si == 1 && sj == 1) return g3;
+    if (si == 0 && sj == 1) return mk(-g1.r, -g1.i) + ti(g2);
+    return mk(-g1.r, -g1.i) - ti(g2);
+}
+
+__global__ void k_clover_build(const double2* __restrict__ U, double2* __restrict__ C64,
+                               float4* __restrict__ C32, Geo g, int V, double csw) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    int c[4];
+    {
+        int r = s;
+        c[0] = r % g.L[0];
+        r /= g.L[0];
+        c[1] = r % g.L[1];
+        r /= g.L[1];
+        c[2] = r % g.L[2];
+        c[3] = r / g.L[2];
+    }
+    // F indices: 0=x,1=y,2=z,3=t.  Paper F_23 = F(1,2), F_14 = F(0,3), F_31 = F(2,0),
+    // F_24 = F(1,3), F_12 = F(0,1), F_34 = F(2,3).
+    const M3 F12 = field_strength(U, g, c, s, V, 0, 1);
+    const M3 F23 = field_strength(U, g, c, s, V, 1, 2);
+    const M3 F31 = field_strength(U, g, c, s, V, 2, 0);
+    const M3 F14 = field_strength(U, g, c, s, V, 0, 3);
+    const M3 F24 = field_strength(U, g, c, s, V, 1, 3);
+    const M3 F34 = field_strength(U, g, c, s, V, 2, 3);
+    double out[72];
+    const double h = 0.5 * csw;
+#pragma unroll
+    for (int blk = 0; blk < 2; ++blk) {
+        const double sgn = blk == 0 ? 1.0 : -1.0;
+        M3 G1, G2, G3;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                G1.m[i][j] = F23.m[i][j] + sgn * F14.m[i][j];
+                G2.m[i][j] = F31.m[i][j] + sgn * F24.m[i][j];
+                G3.m[i][j] = F12.m[i][j] + sgn * F34.m[i][j];
+            }
+        double* o = out + 36 * blk;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) o[i] = h * chiral_elem(G1, G2, G3, i, i).r;
+        int p = 0;
+#pragma unroll
+        for (int i = 1; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j < i; ++j, ++p) {
+                cx<double> e = chiral_elem(G1, G2, G3, i, j);
+                o[6 + 2 * p] = h * e.r;
+                o[6 + 2 * p + 1] = h * e.i;
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < 36; ++q) C64[(size_t)q * V + s] = make_double2(out[2 * q], out[2 * q + 1]);
+#pragma unroll
+    for (int q = 0; q < 18; ++q)
+        C32[(size_t)q * V + s] = make_float4((float)out[4 * q], (float)out[4 * q + 1], (float)out[4 * q + 2],
+                                             (float)out[4 * q + 3]);
+}
+
+}  // namespace
+
+bk_status launch_gauge_convert(const double* Uin_dev, double2* U64, float2* U32, int V, cudaStream_t st) {
+    dim3 grid((V + 127) / 128, 4);
+    k_gauge_convert<<<grid, 128, 0, st>>>((const double2*)Uin_dev, U64, U32, V);
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}
+
+bk_status launch_clover_build(const double2* U64, double2* C64, float4* C32, const int dims[4], double csw,
+                              cudaStream_t st) {
+    Geo g;
+    int stride = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        g.L[mu] = dims[mu];
+        g.st[mu] = stride;
+        stride *= dims[mu];
+    }
+    const int V = stride;
+    k_clover_build<<<(V + 63) / 64, 64, 0, st>>>(U64, C64, C32, g, V, csw);
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}

@@ -1,0 +1,153 @@
+"""GPU parity of the multi-RHS operator and the block linear algebra (C ABI)
+against the FP64 oracle and numpy."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dirac
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+# Relative (max-norm) tolerances of D_W X against the FP64 oracle.  FP64: the
+# paper's operator to rounding.  FP32: unit roundoff 6e-8 times ~50 terms
+# summed per output.  FP16 storage: inputs rounded to 11 mantissa bits
+# relative to each site's largest component (2.4e-4), plus the output store.
+TOL = {"fp64": 1e-13, "fp32": 2e-6, "fp16": 2e-3}
+
+
+def _lat(dims, eps, seed, csw=1.0):
+    import paper_0903_4936_gb300 as bk
+    U = synth.random_su3_field(dims, eps, seed)
+    lat = bk.Lattice(dims)
+    lat.upload_gauge(U)
+    lat.build_clover(csw)
+    return lat, U
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("dims,L", [((4, 4, 4, 4), 12), ((2, 4, 2, 6), 5), ((3, 5, 4, 6), 1),
+                                    ((8, 8, 8, 16), 12), ((6, 4, 4, 4), 17)])
+def test_dslash_matches_oracle(prec, dims, L):
+    lat, U = _lat(dims, 0.5, 100 + L)
+    X = synth.gaussian_sources(dims, L, 7)
+    kappa = [0.11 + 0.002 * j for j in range(L)]
+    Y = lat.dslash(torch.from_numpy(X).cuda(), kappa, prec).cpu().numpy()
+    Yref = dirac.apply_dirac(U, X, np.array(kappa), 1.0)
+    assert _rel(Y, Yref) < TOL[prec]
+
+
+@pytest.mark.parametrize("csw", [0.0, 1.9])
+def test_dslash_csw_values(csw):
+    dims = (4, 4, 4, 6)
+    lat, U = _lat(dims, 0.6, 5, csw)
+    X = synth.z4_noise(dims, 3, 9)
+    Y = lat.dslash(torch.from_numpy(X).cuda(), 0.13, "fp64").cpu().numpy()
+    assert _rel(Y, dirac.apply_dirac(U, X, 0.13, csw)) < 1e-13
+
+
+def test_dslash_point_sources_and_free_field():
+    import paper_0903_4936_gb300 as bk
+    dims = (4, 4, 4, 4)
+    lat = bk.Lattice(dims)
+    U = synth.unit_gauge_field(dims)
+    lat.upload_gauge(U)
+    lat.build_clover(1.0)
+    B = synth.point_sources(dims)
+    Y = lat.dslash(torch.from_numpy(B).cuda(), 0.125, "fp64").cpu().numpy()
+    assert _rel(Y, dirac.apply_dirac(U, B, 0.125, 1.0)) < 1e-15
+
+
+def test_gamma5_and_pack_roundtrip():
+    dims = (4, 4, 4, 4)
+    lat, U = _lat(dims, 0.3, 3)
+    X = synth.gaussian_sources(dims, 4, 1)
+    Xt = torch.from_numpy(X).cuda()
+    assert np.array_equal(lat.gamma5(Xt).cpu().numpy(), dirac.apply_gamma5(X))
+    for prec, tol in [("fp64", 0.0), ("fp32", 1e-7), ("fp16", 1e-3)]:
+        back = lat.unpack(lat.pack(Xt, prec), 4, prec).cpu().numpy()
+        assert _rel(back, X) <= tol
+
+
+def test_dslash_dev_layout_single_launch():
+    dims = (8, 8, 8, 8)
+    lat, U = _lat(dims, 0.4, 11)
+    X = synth.gaussian_sources(dims, 12, 2)
+    F = lat.pack(torch.from_numpy(X).cuda(), "fp32")
+    G = lat.dslash_dev(F, 12, 0.124, "fp32")
+    Y = lat.unpack(G, 12, "fp32").cpu().numpy()
+    assert _rel(Y, dirac.apply_dirac(U, X, 0.124, 1.0)) < TOL["fp32"]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 1e-5), ("fp16", 2e-3)])
+@pytest.mark.parametrize("L", [1, 6, 12, 13])
+def test_gram_matches_numpy(prec, tol, L):
+    dims = (4, 4, 4, 8)
+    lat, _ = _lat(dims, 0.3, 1)
+    A = synth.gaussian_sources(dims, L, 21)
+    B = synth.z2_noise(dims, L, 22)
+    Fa = lat.pack(torch.from_numpy(A).cuda(), prec)
+    Fb = lat.pack(torch.from_numpy(B).cuda(), prec)
+    G = lat.gram(Fa, Fb, L, prec).cpu().numpy()
+    Am, Bm = A.reshape(L, -1).T, B.reshape(L, -1).T
+    Gref = Am.conj().T @ Bm
+    assert _rel(G, Gref) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-14), ("fp32", 1e-6), ("fp16", 2e-3)])
+def test_xmy_matches_numpy(prec, tol):
+    dims = (4, 4, 4, 4)
+    lat, _ = _lat(dims, 0.3, 1)
+    L = 7
+    X = synth.gaussian_sources(dims, L, 31)
+    Z = synth.gaussian_sources(dims, L, 32)
+    rng = np.random.default_rng(3)
+    M = rng.standard_normal((L, L)) + 1j * rng.standard_normal((L, L))
+    c = 0.3 - 0.7j
+    Fx = lat.pack(torch.from_numpy(X).cuda(), prec)
+    Fz = lat.pack(torch.from_numpy(Z).cuda(), prec)
+    Fy = lat.xmy(Fx, torch.from_numpy(M).cuda(), L, c, Fz, prec)
+    Y = lat.unpack(Fy, L, prec).cpu().numpy()
+    ref = Z + c * np.einsum("i...,ij->j...", X, M)
+    assert _rel(Y, ref) < tol
+
+
+@pytest.mark.parametrize("L", [1, 3, 12, 48, 60])
+def test_small_solve_matches_numpy(L):
+    import paper_0903_4936_gb300 as bk
+    rng = np.random.default_rng(L)
+    G = rng.standard_normal((L, L)) + 1j * rng.standard_normal((L, L))
+    H = rng.standard_normal((L, L)) + 1j * rng.standard_normal((L, L))
+    s = 0.5 + 2.0j
+    X, info = bk.small_solve(torch.from_numpy(G).cuda(), torch.from_numpy(H).cuda(), s)
+    assert info == 0
+    ref = np.linalg.solve(G, s * H)
+    assert _rel(X.cpu().numpy(), ref) < 1e-10
+
+
+def test_small_solve_detects_singular():
+    import paper_0903_4936_gb300 as bk
+    rng = np.random.default_rng(0)
+    G = rng.standard_normal((5, 5)) + 0j
+    G[3] = G[1]
+    X, info = bk.small_solve(torch.from_numpy(G).cuda(), torch.from_numpy(np.eye(5) + 0j).cuda())
+    assert info > 0
+
+
+def test_dslash_full_size_sampled_sites_fp16():
+    """16^3 x 32, L = 12 point sources, FP16 storage: the launch shape the
+    benchmark times; compared on sampled sites with the site-wise oracle."""
+    dims = (16, 16, 16, 32)
+    lat, U = _lat(dims, 0.5, 2003)
+    X = synth.z2_noise(dims, 12, 5)
+    Y = lat.dslash(torch.from_numpy(X).cuda(), 0.125, "fp16").cpu().numpy()
+    V = 16 * 16 * 16 * 32
+    sites = [0, 1, 15, 16, 255, 4095, 4096, V // 2 + 17, V - 4096, V - 1]
+    ref = dirac.apply_dirac_at(U, X, 0.125, 1.0, sites, dims)
+    got = Y.reshape(12, V, 4, 3)[:, sites]
+    assert _rel(got, ref) < TOL["fp16"]

@@ -1,0 +1,181 @@
+"""GPU block solvers (C ABI) against the FP64 oracle: dense LU on 4^4, the
+oracle's own block BiCGGR on 8^3 x 16, mixed precision, batched systems,
+host buffers and the error statuses."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import clover, dense, dirac, solvers
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(dims, eps, seed, csw=1.0):
+    import paper_0903_4936_gb300 as bk
+    U = synth.random_su3_field(dims, eps, seed)
+    lat = bk.Lattice(dims)
+    lat.upload_gauge(U)
+    lat.build_clover(csw)
+    return lat, U
+
+
+def _dev(X, Xref):
+    a = X.reshape(X.shape[0], -1)
+    b = Xref.reshape(Xref.shape[0], -1)
+    return float(np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)))
+
+
+@pytest.fixture(scope="module")
+def c1():
+    """4^4, eps = 0.3, kappa = 0.12, c_SW = 1, 12 point sources; dense LU."""
+    dims = (4, 4, 4, 4)
+    lat, U = _setup(dims, 0.3, 1001)
+    B = synth.point_sources(dims)
+    D = dense.dense_matrix(U, 0.12, 1.0)
+    Xd = dense.from_columns(np.linalg.solve(D, dense.to_columns(B)), dims)
+    A = lambda M: dense.to_columns(dirac.apply_dirac(U, dense.from_columns(M, dims), 0.12, 1.0))  # noqa: E731
+    return dims, lat, U, B, Xd, A
+
+
+@pytest.mark.parametrize("method", ["bicggr", "bicgstab"])
+def test_fp64_solve_matches_dense_lu(c1, method):
+    dims, lat, U, B, Xd, A = c1
+    X, info = lat.block_solve(torch.from_numpy(B).cuda(), 0.12, method=method, prec="fp64", tol=1e-12,
+                              maxiter=500, history=True)
+    X = X.cpu().numpy()
+    assert info["converged"] == 1
+    assert info["true_res_max"] <= 1e-10
+    assert _dev(X, Xd) <= 1e-8
+    # iterate for iterate: the residual history of the oracle's algorithm
+    fn = solvers.block_bicggr if method == "bicggr" else solvers.block_bicgstab
+    Xo, io = fn(A, dense.to_columns(B), 1e-12, 500)
+    assert abs(info["iterations"] - io["iterations"]) <= 1
+    n = min(20, len(io["history"]))
+    h = np.array(info["history"][:n])
+    assert np.allclose(h, io["history"][:n], rtol=1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("method", ["bicggr", "bicgstab"])
+def test_mixed_solve_matches_dense_lu(c1, prec, method):
+    dims, lat, U, B, Xd, A = c1
+    X, info = lat.block_solve(torch.from_numpy(B).cuda(), 0.12, method=method, prec=prec, tol=1e-10,
+                              maxiter=1000)
+    X = X.cpu().numpy()
+    assert info["converged"] == 1
+    assert info["true_res_max"] <= 1e-10
+    assert info["reliable_updates"] >= 1
+    assert _dev(X, Xd) <= 1e-8
+    # the library's FP64 true residual agrees with the oracle's
+    tr, _ = solvers.true_residual(A, dense.to_columns(B), dense.to_columns(X))
+    assert tr <= 1e-10
+
+
+@pytest.fixture(scope="module")
+def c2():
+    """8^3 x 16, eps = 0.5, kappa = 0.125, c_SW = 1, 12 point sources."""
+    dims = (8, 8, 8, 16)
+    lat, U = _setup(dims, 0.5, 1002)
+    B = synth.point_sources(dims)
+    F = clover.field_strength(U)
+    A = lambda M: dense.to_columns(dirac.apply_dirac(U, dense.from_columns(M, dims), 0.125, 1.0, F=F))  # noqa
+    Xo, io = solvers.block_bicggr(A, dense.to_columns(B), 1e-13, 1000)
+    return dims, lat, U, B, dense.from_columns(Xo, dims), A
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+def test_c2_solution_matches_oracle(c2, prec):
+    dims, lat, U, B, Xo, A = c2
+    X, info = lat.block_solve(torch.from_numpy(B).cuda(), 0.125, method="bicggr", prec=prec, tol=1e-10,
+                              maxiter=1000)
+    X = X.cpu().numpy()
+    assert info["converged"] == 1 and info["true_res_max"] <= 1e-10
+    assert _dev(X, Xo) <= 1e-8
+
+
+def test_batched_systems_match_individual(c1):
+    dims, lat, U, B, Xd, A = c1
+    kappas = [0.11, 0.12, 0.125]
+    Ls = [2, 4, 3]
+    Bs = synth.z4_noise(dims, sum(Ls), 77)
+    X, infos = lat.block_solve_batched(torch.from_numpy(Bs).cuda(), kappas, Ls, method="bicggr", prec="fp32",
+                                       tol=1e-10, maxiter=1000)
+    X = X.cpu().numpy()
+    c0 = 0
+    for s, (k, L) in enumerate(zip(kappas, Ls)):
+        D = dense.dense_matrix(U, k, 1.0)
+        ref = dense.from_columns(np.linalg.solve(D, dense.to_columns(Bs[c0:c0 + L])), dims)
+        assert infos[s]["converged"] == 1 and infos[s]["true_res_max"] <= 1e-10
+        assert _dev(X[c0:c0 + L], ref) <= 1e-8
+        c0 += L
+
+
+def test_host_buffers_path(c1):
+    dims, lat, U, B, Xd, A = c1
+    Bh = torch.from_numpy(B).pin_memory()
+    X, info = lat.block_solve(Bh, 0.12, method="bicggr", prec="fp32", tol=1e-10, maxiter=500)
+    assert not X.is_cuda
+    assert info["converged"] == 1
+    assert _dev(X.numpy(), Xd) <= 1e-8
+
+
+def test_initial_guess_is_used(c1):
+    dims, lat, U, B, Xd, A = c1
+    X, info = lat.block_solve(torch.from_numpy(B).cuda(), 0.12, prec="fp64", tol=1e-10,
+                              X0=torch.from_numpy(Xd).cuda())
+    assert info["iterations"] == 0 and info["converged"] == 1
+
+
+def test_unitary_equivariance_gpu(c1):
+    dims, lat, U, B, Xd, A = c1
+    rng = np.random.default_rng(5)
+    Q, _ = np.linalg.qr(rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4)))
+    Bs = synth.gaussian_sources(dims, 4, 17)
+    BQ = np.einsum("i...,ij->j...", Bs, Q)
+    X1, _ = lat.block_solve(torch.from_numpy(Bs).cuda(), 0.12, prec="fp64", tol=1e-30, maxiter=10,
+                            raise_on_fail=False)
+    X2, _ = lat.block_solve(torch.from_numpy(BQ).cuda(), 0.12, prec="fp64", tol=1e-30, maxiter=10,
+                            raise_on_fail=False)
+    X1Q = np.einsum("i...,ij->j...", X1.cpu().numpy(), Q)
+    assert np.linalg.norm(X2.cpu().numpy() - X1Q) / np.linalg.norm(X1Q) < 1e-10
+
+
+def test_breakdown_on_duplicate_columns(c1):
+    import paper_0903_4936_gb300 as bk
+    dims, lat, U, B, Xd, A = c1
+    Bd = np.concatenate([B[:2], B[:1]], axis=0).copy()
+    X, info = lat.block_solve(torch.from_numpy(Bd).cuda(), 0.12, prec="fp64", tol=1e-12, maxiter=50,
+                              raise_on_fail=False)
+    assert info["status"] == "BK_ERR_BREAKDOWN"
+    assert np.all(np.isfinite(X.cpu().numpy()))
+    with pytest.raises(bk.BKError):
+        lat.block_solve(torch.from_numpy(Bd).cuda(), 0.12, prec="fp64", tol=1e-12, maxiter=50)
+
+
+def test_nonfinite_rhs_rejected(c1):
+    dims, lat, U, B, Xd, A = c1
+    Bn = B.copy()
+    Bn[3, 0, 0, 0, 1, 2, 1] = np.nan
+    X, info = lat.block_solve(torch.from_numpy(Bn).cuda(), 0.12, raise_on_fail=False)
+    assert info["status"] == "BK_ERR_NONFINITE"
+
+
+def test_not_converged_returns_iterate(c1):
+    dims, lat, U, B, Xd, A = c1
+    X, info = lat.block_solve(torch.from_numpy(B).cuda(), 0.12, prec="fp32", tol=1e-12, maxiter=3,
+                              raise_on_fail=False)
+    assert info["status"] == "BK_ERR_NOT_CONVERGED"
+    assert info["iterations"] == 3
+    assert np.all(np.isfinite(X.cpu().numpy()))
+    assert info["true_res_max"] < 1.0
+
+
+def test_bicggr_residual_gap_vs_bicgstab(c2):
+    """Section 4.3: BiCGGR's true residual stays at the tolerance; BiCGSTAB's
+    may drift above it.  Both in FP64, recursive stopping rule."""
+    dims, lat, U, B, Xo, A = c2
+    _, ig = lat.block_solve(torch.from_numpy(B).cuda(), 0.125, method="bicggr", prec="fp64", tol=1e-12,
+                            maxiter=1000)
+    assert ig["true_res_max"] < 5e-12
