@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Benchmark: right-hand sides solved per second to true relative residual 1e-10
+with the mixed-precision block BiCGGR solver, on a synthetic 16^3 x 32 clover
+Wilson-Dirac problem, plus the multi-RHS operator's HBM roofline.
+
+One step = every case of the workload solved once through the C ABI (block
+BiCGGR, FP16-stored / FP32-arithmetic inner iterations, FP64 reliable updates
+and FP64 true residual).  Each solve must reach a FP64 true residual <= 1e-10,
+else the run fails.  Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload c3|c3-12|c2] [--no-fp64] [--no-cpu-baseline]
+
+--impl reference times the FP64 CPU oracle (test infrastructure, written from
+the paper) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RHS solved/s to rel resid 1e-10 (mixed vs FP64); multi-RHS dslash HBM GB/s"
+
+# Workloads: (Lx, Ly, Lz, Lt), link spread eps, c_SW, cases (kappa, L, source kind).
+WORKLOADS = {
+    "c3": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp16",
+               cases=[(k, L, src) for k in (0.120, 0.125, 0.130) for (L, src) in ((12, "point"), (48, "z2"))],
+               desc="16^3x32 clover Wilson-Dirac, random SU(3) links eps=0.5, c_SW=1.0, kappa in "
+                    "{0.120,0.125,0.130} x (L=12 point sources, L=48 complex-Z2 noise); block BiCGGR, "
+                    "FP16-stored/FP32 inner, FP64 reliable updates and true residual, tol 1e-10"),
+    "c3-12": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp16",
+                  cases=[(0.125, 12, "point")],
+                  desc="16^3x32, eps=0.5, c_SW=1.0, kappa=0.125, L=12 point sources; block BiCGGR, "
+                       "FP16-stored/FP32 inner, FP64 reliable updates, tol 1e-10"),
+    "c2": dict(dims=(8, 8, 8, 16), eps=0.5, csw=1.0, gauge_seed=1002, prec="fp32",
+               cases=[(0.125, 12, "point")],
+               desc="8^3x16, eps=0.5, c_SW=1.0, kappa=0.125, L=12 point sources; block BiCGGR FP32 inner + "
+                    "FP64 reliable updates, tol 1e-10"),
+}
+TOL = 1e-10
+MAXITER = 5000
+
+
+def spinor_bytes(prec):
+    # per site and column: read 24 reals, write 24 reals (+ one FP32 scale each way for FP16)
+    return {"fp64": 2 * 24 * 8, "fp32": 2 * 24 * 4, "fp16": 2 * (24 * 2 + 4)}[prec]
+
+
+def dslash_bytes(V, L, prec):
+    """Algorithmic bytes of one multi-RHS operator launch: 4 links and the
+    72-real clover per site once, every spinor column read once and written once."""
+    s = 8 if prec == "fp64" else 4
+    return V * (4 * 18 * s + 72 * s) + V * L * spinor_bytes(prec)
+
+
+def sources(dims, L, kind, seed):
+    import synth
+    if kind == "point":
+        B = synth.point_sources(dims)
+        return B[:L].copy() if L <= 12 else None
+    if kind == "z2":
+        return synth.z2_noise(dims, L, seed)
+    if kind == "z4":
+        return synth.z4_noise(dims, L, seed)
+    return synth.gaussian_sources(dims, L, seed)
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_0903_4936_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per inner-operator launch from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "dslash_fp16_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != source_hash():
+        return None
+    return d.get("per_launch_bytes", {}).get(workload)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        mhz = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": mhz[len(mhz) // 2] if mhz else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ oracle baseline
+
+ORACLE_SNIPPET = r"""
+import os, sys, time, json
+sys.path.insert(0, {root!r})
+import numpy as np, synth
+from oracle import clover, dense, dirac, solvers
+dims = {dims!r}; kappa = {kappa!r}; L = {L}; kind = {kind!r}
+U = synth.random_su3_field(dims, {eps!r}, {gseed!r})
+B = synth.point_sources(dims)[:L].copy() if kind == "point" else synth.z2_noise(dims, L, {sseed!r})
+t0 = time.perf_counter()
+F = clover.field_strength(U)
+A = lambda M: dense.to_columns(dirac.apply_dirac(U, dense.from_columns(M, dims), kappa, {csw!r}, F=F))
+Bc = dense.to_columns(B)
+t1 = time.perf_counter()
+A(Bc)  # one operator application: the set-up product W_0 = A R_0 of the solve below
+t2 = time.perf_counter()
+X, info = solvers.block_bicggr(A, Bc, 1e-300, {iters})
+t3 = time.perf_counter()
+it = max(1, info["iterations"])
+print(json.dumps(dict(setup_s=t1 - t0, apply_s=t2 - t1, iter_s=((t3 - t2) - (t2 - t1)) / it, iterations=it)))
+"""
+
+
+def run_oracle_sample(wl, case, iters=1):
+    """Time `iters` iterations of the oracle's block BiCGGR (plus the initial
+    operator application) on one case, single-threaded, in a fresh process."""
+    kappa, L, kind = case
+    code = ORACLE_SNIPPET.format(root=ROOT, dims=wl["dims"], kappa=kappa, L=L, kind=kind, eps=wl["eps"],
+                                 gseed=wl["gauge_seed"], sseed=2000 + L, csw=wl["csw"], iters=iters)
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def gb300_arm(args, wl, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_0903_4936_gb300 as bk
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dims = wl["dims"]
+    U = synth.random_su3_field(dims, wl["eps"], wl["gauge_seed"])
+    lat = bk.Lattice(dims, local_rank)
+    lat.upload_gauge(U)
+    lat.build_clover(wl["csw"])
+    V = lat.V
+    cases = []
+    for (kappa, L, kind) in wl["cases"]:
+        B = sources(dims, L, kind, 2000 + L + 7919 * rank)
+        cases.append(dict(kappa=kappa, L=L, kind=kind, B=torch.from_numpy(B).to(dev),
+                          Bh=torch.from_numpy(B).pin_memory()))
+    del U
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step(record, host=False):
+        tot = dict(rhs=0, launches=0, t_inner=0.0, n_inner=0, bytes_inner=0.0)
+        for c in cases:
+            B = c["Bh"] if host else c["B"]
+            X, info = lat.block_solve(B, c["kappa"], method="bicggr", prec=wl["prec"], tol=TOL, maxiter=MAXITER,
+                                      timing=record)
+            if not (info["converged"] and info["true_res_max"] <= TOL):
+                raise RuntimeError(f"solve did not reach {TOL}: {info}")
+            tot["rhs"] += c["L"]
+            tot["launches"] += info["n_launches"]
+            tot["t_inner"] += info["time_dslash_inner_ms"]
+            tot["n_inner"] += info["n_dslash_inner"]
+            tot["bytes_inner"] += info["n_dslash_inner"] * dslash_bytes(V, c["L"], wl["prec"])
+            c["last_info"] = info
+        return tot
+
+    for _ in range(args.warmup):
+        step(False)
+        flush.fill_(1)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local_rank)
+    if rank == 0:
+        clocks.start()
+    per_step_ms = []
+    agg = dict(rhs=0, launches=0, t_inner=0.0, n_inner=0, bytes_inner=0.0)
+    stream = torch.cuda.current_stream(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t = step(True)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        per_step_ms.append(ms)
+        total_ms += ms
+        for k in agg:
+            agg[k] += t[k]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if rank == 0 else None
+
+    # e2e: the same metric through the public API with host (pinned) buffers:
+    # B copied in and X copied out inside every call.
+    e2e_ms = 0.0
+    h2d = d2h = 0
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t = step(False, host=True)
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    n_e2e = max(1, min(args.steps, 3))
+    for c in cases:
+        h2d += c["B"].numel() * 16
+        d2h += c["B"].numel() * 16
+
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        # plain FP64 block BiCGGR on the L = 12 cases at the same accuracy (outside the timed loop)
+        rhs = 0
+        ms = 0.0
+        mixed_ms = 0.0
+        for c in cases:
+            if c["L"] != 12:
+                continue
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            X, info = lat.block_solve(c["B"], c["kappa"], method="bicggr", prec="fp64", tol=TOL, maxiter=MAXITER)
+            e1.record()
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            rhs += c["L"]
+            e0.record()
+            X, info2 = lat.block_solve(c["B"], c["kappa"], method="bicggr", prec=wl["prec"], tol=TOL,
+                                       maxiter=MAXITER)
+            e1.record()
+            e1.synchronize()
+            mixed_ms += e0.elapsed_time(e1)
+            if info["true_res_max"] > TOL:
+                raise RuntimeError(f"FP64 solve did not reach {TOL}: {info}")
+        if rhs:
+            fp64 = dict(fp64_rhs_per_s=rhs / (ms / 1e3), mixed_rhs_per_s=rhs / (mixed_ms / 1e3),
+                        cases="L=12 cases only", speedup=ms / mixed_ms)
+
+    return dict(total_ms=total_ms, per_step_ms=per_step_ms, agg=agg, clocks=clk, e2e_ms=e2e_ms / n_e2e,
+                h2d=h2d, d2h=d2h, fp64=fp64, V=V,
+                iters={f"k{c['kappa']}_L{c['L']}": c["last_info"]["iterations"] for c in cases},
+                rel_updates={f"k{c['kappa']}_L{c['L']}": c["last_info"]["reliable_updates"] for c in cases})
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    total_rhs_per_step = sum(L for (_, L, _) in wl["cases"])
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # Reference arm: the CPU oracle as it stands, one process, one thread.
+        first = wl["cases"][0]
+        samples = []
+        for _ in range(args.warmup + args.steps):
+            samples.append(run_oracle_sample(wl, first, iters=1))
+        timed = samples[args.warmup:]
+        iter_s = sum(s["iter_s"] for s in timed) / len(timed)
+        n_it = GPU_ITERS_HINT.get(args.workload, 100)
+        value = first[1] / (iter_s * n_it)
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": iter_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "parallelism": "none (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": 1, "kind": "oracle",
+                             "sample": f"one block BiCGGR iteration of the FP64 numpy oracle per step on the case "
+                                       f"kappa={first[0]}, L={first[1]} {first[2]}; RHS/s = L / (seconds per "
+                                       f"iteration x {n_it} iterations, the GPU solver's count for this case)"},
+            "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    # The oracle baseline runs in a spawned process before any GPU work.
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu_case = wl["cases"][0]
+        cpu = run_oracle_sample(wl, cpu_case, iters=1)
+
+    r = gb300_arm(args, wl, rank, world, local_rank)
+
+    total_ms = r["total_ms"]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * total_rhs_per_step * args.steps / (total_ms / 1e3)
+    agg = r["agg"]
+    hbm, peak_kind = measured_peaks()
+    achieved = (agg["bytes_inner"] / agg["n_inner"]) / ((agg["t_inner"] / agg["n_inner"]) / 1e3) / 1e9 \
+        if agg["n_inner"] else None
+    traffic = ncu_traffic(args.workload)
+    line = {
+        "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": wl["prec"], "data": "synthetic",
+        "config": {"workload": wl["desc"], "lattice": "x".join(map(str, wl["dims"])),
+                   "rhs_per_step": total_rhs_per_step, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "l2": "inputs larger than L2 and a 256 MB L2 flush before every timed step"},
+        "roofline": {"bound": "hbm", "kernel": "k_dslash<FP16>", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": (achieved / hbm) if achieved else None, "peak_kind": peak_kind,
+                     "traffic": traffic, "launches": agg["n_inner"],
+                     "avg_launch_us": agg["t_inner"] / agg["n_inner"] * 1e3 if agg["n_inner"] else None},
+        "e2e": {"value": world * total_rhs_per_step / (r["e2e_ms"] / 1e3), "unit": "RHS/s",
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+        "gpu_launches": int(agg["launches"]),
+        "clocks": r["clocks"],
+        "iterations": r["iters"], "reliable_updates": r["rel_updates"],
+    }
+    if r["fp64"]:
+        line["fp64_comparison"] = r["fp64"]
+    if cpu is not None:
+        its = r["iters"].get(f"k{wl['cases'][0][0]}_L{wl['cases'][0][1]}", 100)
+        cv = wl["cases"][0][1] / (cpu["iter_s"] * its)
+        line["cpu_baseline"] = {"value": cv, "unit": "RHS/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one FP64 numpy-oracle block BiCGGR iteration ({cpu['iter_s']:.1f} s) on "
+                                          f"kappa={wl['cases'][0][0]}, L={wl['cases'][0][1]}; RHS/s = L / (s/iter x "
+                                          f"{its} iterations, the GPU solver's count for that case)"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# Iteration counts of the GPU solver per workload's first case, used to turn the
+# oracle's seconds per iteration into RHS/s on the reference arm.
+GPU_ITERS_HINT = {"c3": 100, "c3-12": 100, "c2": 60}
+
+if __name__ == "__main__":
+    main()

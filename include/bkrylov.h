@@ -156,8 +156,14 @@ typedef struct bk_solve_params {
     int x0_given;          /* 1: X holds the initial guess X_0; 0: X_0 = 0    */
     int buffers_on_host;   /* 1: B and X are host canonical buffers (copied in
                               and out inside the call); 0: device canonical    */
-    int rtilde_random;     /* 0: R~_0 = R_0 (default); 1: seeded Gaussian     */
-    uint64_t seed;         /* seed for rtilde_random                          */
+    int rtilde_mode;       /* shadow residual R~_0 ("Choose", Section 3):
+                              0: seeded complex Gaussian (default; SplitMix64
+                                 counter hash + Box-Muller on the device),
+                              1: R~_0 = R_0,
+                              2: the caller's block `rtilde` (canonical FP64,
+                                 L columns, same location as B)            */
+    uint64_t seed;         /* seed of rtilde_mode 0                           */
+    const double* rtilde;  /* rtilde_mode 2 only                              */
     int record_history;    /* 1: info->history[k] = max_i rel. residual       */
     int timing;            /* 1: time every dslash launch with CUDA events    */
 } bk_solve_params;

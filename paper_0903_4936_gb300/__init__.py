@@ -166,11 +166,19 @@ class Lattice:
         return Y
 
     # ------------------------------------------------------------ solves
-    def _params(self, method, prec, tol, maxiter, delta, x0_given, on_host, rtilde_random, seed, history,
-                timing):
+    def _params(self, method, prec, tol, maxiter, delta, x0_given, on_host, rtilde, seed, history, timing):
+        """rtilde: None -> seeded Gaussian R~_0 (library default), "r0" -> R~_0 = R_0,
+        tensor -> the caller's block (canonical layout, where B lives)."""
+        mode, ptr = 0, None
+        if isinstance(rtilde, str):
+            if rtilde != "r0":
+                raise ValueError("rtilde must be None, 'r0' or a block")
+            mode = 1
+        elif rtilde is not None:
+            mode, ptr = 2, C.c_void_p(rtilde.data_ptr())
         return SolveParams(METHOD[method] if isinstance(method, str) else int(method), _prec(prec), float(tol),
-                           int(maxiter), float(delta), int(x0_given), int(on_host), int(rtilde_random),
-                           int(seed), int(history), int(timing))
+                           int(maxiter), float(delta), int(x0_given), int(on_host), mode, int(seed), ptr,
+                           int(history), int(timing))
 
     @staticmethod
     def _info_dict(info: SolveInfo, hist_buf, res_buf):
@@ -180,7 +188,7 @@ class Lattice:
         return d
 
     def block_solve(self, B: torch.Tensor, kappa: float, method="bicggr", prec="fp64", tol=1e-10, maxiter=2000,
-                    X0: torch.Tensor | None = None, delta=0.0, rtilde_random=False, seed=0, history=False,
+                    X0: torch.Tensor | None = None, delta=0.0, rtilde=None, seed=0, history=False,
                     timing=False, out: torch.Tensor | None = None, raise_on_fail=True):
         """Solve D_W X = B (Eq. (linear_mrhs)).  B on the GPU, or on the host
         (then pinned memory is best): X is returned where B lives."""
@@ -190,8 +198,12 @@ class Lattice:
         X = (torch.empty_like(B, pin_memory=on_host) if on_host else torch.empty_like(B)) if out is None else out
         if X0 is not None:
             X.copy_(X0)
-        prm = self._params(method, prec, tol, maxiter, delta, X0 is not None, on_host, rtilde_random, seed,
-                           history, timing)
+        if rtilde is not None and not isinstance(rtilde, str):
+            self._check_block(rtilde, "rtilde")
+            if rtilde.shape != B.shape or rtilde.is_cuda != B.is_cuda:
+                raise ValueError("rtilde must have B's shape and location")
+        prm = self._params(method, prec, tol, maxiter, delta, X0 is not None, on_host, rtilde, seed, history,
+                           timing)
         info = SolveInfo()
         res_buf = (C.c_double * L)()
         info.true_res = C.cast(res_buf, C.POINTER(C.c_double))
@@ -207,8 +219,8 @@ class Lattice:
         return X, d
 
     def block_solve_batched(self, B: torch.Tensor, kappas: Sequence[float], Ls: Sequence[int], method="bicggr",
-                            prec="fp64", tol=1e-10, maxiter=2000, delta=0.0, history=False, timing=False,
-                            raise_on_fail=True):
+                            prec="fp64", tol=1e-10, maxiter=2000, delta=0.0, rtilde=None, seed=0, history=False,
+                            timing=False, raise_on_fail=True):
         """Several systems (kappa_s, L_s columns each, concatenated in B)."""
         self._check_block(B, "B")
         nsys = len(Ls)
@@ -216,7 +228,7 @@ class Lattice:
             raise ValueError("B must hold sum(Ls) columns and one kappa per system")
         on_host = not B.is_cuda
         X = torch.empty_like(B, pin_memory=on_host) if on_host else torch.empty_like(B)
-        prm = self._params(method, prec, tol, maxiter, delta, False, on_host, False, 0, history, timing)
+        prm = self._params(method, prec, tol, maxiter, delta, False, on_host, rtilde, seed, history, timing)
         infos = (SolveInfo * nsys)()
         res_bufs, hist_bufs = [], []
         for s in range(nsys):

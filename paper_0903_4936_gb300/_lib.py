@@ -32,7 +32,7 @@ class SolveParams(C.Structure):
     _fields_ = [
         ("method", C.c_int), ("prec", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int),
         ("reliable_delta", C.c_double), ("x0_given", C.c_int), ("buffers_on_host", C.c_int),
-        ("rtilde_random", C.c_int), ("seed", C.c_uint64), ("record_history", C.c_int),
+        ("rtilde_mode", C.c_int), ("seed", C.c_uint64), ("rtilde", C.c_void_p), ("record_history", C.c_int),
         ("timing", C.c_int),
     ]
 

@@ -110,7 +110,7 @@ struct bk_ctx {
     // scratch of the single-operation entry points
     DevBuf s1, s2, part, scal;
     // solver workspace
-    DevBuf B64, X64, R64, Xlo, blk[8], small, spart, gwork, canonB, canonX;
+    DevBuf B64, X64, R64, Xlo, blk[8], small, spart, gwork, canonB, canonX, canonRt;
     HostBuf rb_host;
     std::vector<cudaEvent_t> events;
 };
@@ -166,7 +166,7 @@ extern "C" bk_status bk_destroy(bk_ctx* c) {
     cudaSetDevice(c->device);
     DevBuf* bufs[] = {&c->U64, &c->U32, &c->C64, &c->C32, &c->Utmp, &c->s1, &c->s2, &c->part, &c->scal,
                       &c->B64, &c->X64, &c->R64, &c->Xlo, &c->small, &c->spart, &c->gwork, &c->canonB,
-                      &c->canonX};
+                      &c->canonX, &c->canonRt};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : c->blk) b.release();
     c->rb_host.release();
@@ -382,7 +382,7 @@ __global__ void k_random(Field f, int V, uint64_t seed) {
         const uint64_t a = splitmix64(seed ^ (2 * idx)), b = splitmix64(seed ^ (2 * idx + 1));
         const double u1 = ((a >> 11) + 1) * (1.0 / 9007199254740993.0);
         const double u2 = (b >> 11) * (1.0 / 9007199254740992.0);
-        const double r = sqrt(-log(u1)) * 0.7071067811865476 * 1.4142135623730951 * 0.7071067811865476;
+        const double r = sqrt(-log(u1));  // |z| of a complex Gaussian with E|z|^2 = 1
         v[k] = mk((R)(r * cospi(2 * u2)), (R)(r * sinpi(2 * u2)));
     }
     store_spinor<P>(f, c, site, v);
@@ -645,6 +645,32 @@ struct Solve {
                 bnorm[j] = std::sqrt(n2);
             }
         }
+        if (prm->rtilde_mode == 2) {
+            const double* rt = prm->rtilde;
+            if (prm->buffers_on_host) {
+                BK_TRY(c->canonRt.ensure((size_t)Lt * V * 12 * sizeof(double2)));
+                BK_CUDA_TRY(cudaMemcpyAsync(c->canonRt.p, rt, (size_t)Lt * V * 12 * sizeof(double2),
+                                            cudaMemcpyHostToDevice, st));
+                rt = c->canonRt.as<double>();
+            }
+            if (P == BK_FP64) {
+                BK_TRY(launch_pack(BK_FP64, rt, Rt, Lt, st));
+            } else {
+                BK_TRY(launch_pack(BK_FP64, rt, R64, Lt, st));  // R64 is rebuilt below
+                BK_TRY(launch_cast(BK_FP64, R64, P, Rt, Lt, st));
+                launches++;
+            }
+            launches++;
+        } else if (prm->rtilde_mode == 0) {
+            dim3 grid((V + 127) / 128, Lt);
+            switch (P) {
+                case BK_FP64: k_random<BK_FP64><<<grid, 128, 0, st>>>(Rt, V, prm->seed); break;
+                case BK_FP32: k_random<BK_FP32><<<grid, 128, 0, st>>>(Rt, V, prm->seed); break;
+                default: k_random<BK_FP16><<<grid, 128, 0, st>>>(Rt, V, prm->seed); break;
+            }
+            BK_CUDA_TRY(cudaGetLastError());
+            launches++;
+        }
         if (prm->x0_given) {
             BK_TRY(launch_pack(BK_FP64, Xc, X64, Lt, st));
             launches++;
@@ -662,21 +688,12 @@ struct Solve {
             BK_CUDA_TRY(cudaMemsetAsync(X64.data, 0, fb64, st));
             BK_CUDA_TRY(cudaMemcpyAsync(R64.data, B64.data, fb64, cudaMemcpyDeviceToDevice, st));
         }
+
         if (mixed) BK_CUDA_TRY(cudaMemsetAsync(Xlo.data, 0, field_bytes(Lt, V, BK_FP32), st));
         BK_TRY(launch_cast(BK_FP64, R64, P, R, Lt, st));
         launches++;
-        if (prm->rtilde_random) {
-            dim3 grid((V + 127) / 128, Lt);
-            switch (P) {
-                case BK_FP64: k_random<BK_FP64><<<grid, 128, 0, st>>>(Rt, V, prm->seed); break;
-                case BK_FP32: k_random<BK_FP32><<<grid, 128, 0, st>>>(Rt, V, prm->seed); break;
-                default: k_random<BK_FP16><<<grid, 128, 0, st>>>(Rt, V, prm->seed); break;
-            }
-            BK_CUDA_TRY(cudaGetLastError());
-            launches++;
-        } else {
+        if (prm->rtilde_mode == 1)
             BK_CUDA_TRY(cudaMemcpyAsync(Rt.data, R.data, fbp, cudaMemcpyDeviceToDevice, st));
-        }
         BK_CUDA_TRY(cudaMemcpyAsync(Pb.data, R.data, fbp, cudaMemcpyDeviceToDevice, st));
         if (method == BK_BICGGR) {
             BK_TRY(dslash(P, R, Wb, R, 0, Lt, 0));  // V_0 = W_0 = A R_0
@@ -942,6 +959,8 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
     BK_CHECK_ARG(prm->method == BK_BICGSTAB || prm->method == BK_BICGGR, "unknown method");
     BK_CHECK_ARG(valid_prec(prm->prec), "unknown precision");
     BK_CHECK_ARG(prm->tol > 0 && prm->maxiter >= 0, "tol must be > 0 and maxiter >= 0");
+    BK_CHECK_ARG(prm->rtilde_mode >= 0 && prm->rtilde_mode <= 2, "rtilde_mode must be 0, 1 or 2");
+    BK_CHECK_ARG(prm->rtilde_mode != 2 || prm->rtilde, "rtilde_mode 2 needs the rtilde block");
     int Lt = 0;
     for (int s = 0; s < nsys; ++s) {
         BK_CHECK_ARG(Ls[s] >= 1, "every system needs L >= 1");
