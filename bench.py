@@ -32,15 +32,15 @@ METRIC = "RHS solved/s to rel resid 1e-10 (mixed vs FP64); multi-RHS dslash HBM 
 
 # Workloads: (Lx, Ly, Lz, Lt), link spread eps, c_SW, cases (kappa, L, source kind).
 WORKLOADS = {
-    "c3": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp16",
+    "c3": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp32",
                cases=[(k, L, src) for k in (0.120, 0.125, 0.130) for (L, src) in ((12, "point"), (48, "z2"))],
                desc="16^3x32 clover Wilson-Dirac, random SU(3) links eps=0.5, c_SW=1.0, kappa in "
                     "{0.120,0.125,0.130} x (L=12 point sources, L=48 complex-Z2 noise); block BiCGGR, "
-                    "FP16-stored/FP32 inner, FP64 reliable updates and true residual, tol 1e-10"),
-    "c3-12": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp16",
+                    "FP32 inner iterations, FP64 reliable updates and true residual, tol 1e-10"),
+    "c3-12": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp32",
                   cases=[(0.125, 12, "point")],
                   desc="16^3x32, eps=0.5, c_SW=1.0, kappa=0.125, L=12 point sources; block BiCGGR, "
-                       "FP16-stored/FP32 inner, FP64 reliable updates, tol 1e-10"),
+                       "FP32 inner iterations, FP64 reliable updates, tol 1e-10"),
     "c2": dict(dims=(8, 8, 8, 16), eps=0.5, csw=1.0, gauge_seed=1002, prec="fp32",
                cases=[(0.125, 12, "point")],
                desc="8^3x16, eps=0.5, c_SW=1.0, kappa=0.125, L=12 point sources; block BiCGGR FP32 inner + "
@@ -94,7 +94,7 @@ def measured_peaks():
 def ncu_traffic(workload):
     """DRAM bytes per inner-operator launch from the committed ncu summary, if it
     was taken on the current kernel sources; else None."""
-    p = os.path.join(ROOT, "profiles", "dslash_fp16_traffic.json")
+    p = os.path.join(ROOT, "profiles", "dslash_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
@@ -388,10 +388,11 @@ def main():
         "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": wl["prec"], "data": "synthetic",
+        "mixed_precision": "inner iterations in FP32, FP64 residual replacement and true residual",
         "config": {"workload": wl["desc"], "lattice": "x".join(map(str, wl["dims"])),
                    "rhs_per_step": total_rhs_per_step, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 and a 256 MB L2 flush before every timed step"},
-        "roofline": {"bound": "hbm", "kernel": "k_dslash<FP16>", "achieved": achieved, "peak": hbm,
+        "roofline": {"bound": "hbm", "kernel": f"k_dslash<{wl['prec'].upper()}>", "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": (achieved / hbm) if achieved else None, "peak_kind": peak_kind,
                      "traffic": traffic, "launches": agg["n_inner"],
                      "avg_launch_us": agg["t_inner"] / agg["n_inner"] * 1e3 if agg["n_inner"] else None},

@@ -173,6 +173,9 @@ typedef struct bk_solve_info {
     int matvecs;           /* operator applications in the inner precision    */
     int matvecs_fp64;      /* FP64 operator applications (residuals)          */
     int reliable_updates;  /* FP64 residual replacements                      */
+    int restarts;          /* mixed precision: low-precision cycles discarded
+                              and restarted from the last FP64 residual
+                              (breakdown, non-finite or runaway residual)     */
     int converged;         /* 1 if every column met tol (true residual for
                               mixed precision)                                 */
     int breakdown;         /* 1 if an L x L solve broke down                   */

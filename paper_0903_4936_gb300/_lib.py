@@ -40,7 +40,7 @@ class SolveParams(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [
         ("iterations", C.c_int), ("matvecs", C.c_int), ("matvecs_fp64", C.c_int),
-        ("reliable_updates", C.c_int), ("converged", C.c_int), ("breakdown", C.c_int),
+        ("reliable_updates", C.c_int), ("restarts", C.c_int), ("converged", C.c_int), ("breakdown", C.c_int),
         ("true_res_max", C.c_double), ("rec_res_max", C.c_double),
         ("true_res", C.POINTER(C.c_double)), ("history", C.POINTER(C.c_double)),
         ("history_len", C.c_int), ("time_total_ms", C.c_double), ("time_dslash_ms", C.c_double),

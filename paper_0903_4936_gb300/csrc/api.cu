@@ -13,7 +13,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "bk_common.cuh"
@@ -113,6 +115,12 @@ struct bk_ctx {
     DevBuf B64, X64, R64, Xlo, blk[8], small, spart, gwork, canonB, canonX, canonRt;
     HostBuf rb_host;
     std::vector<cudaEvent_t> events;
+    // operator launch shapes chosen by the autotuner, keyed by (prec, residual, ncol)
+    struct Shape {
+        int rpt, sx, by;
+    };
+    std::map<long long, Shape> shapes;
+    bool autotune = true;
 };
 
 static const void* gauge_ptr(const bk_ctx* c, int prec) { return prec == BK_FP64 ? c->U64.p : c->U32.p; }
@@ -148,6 +156,10 @@ extern "C" bk_status bk_create(const int dims[4], int device, bk_ctx** out) {
     bk_ctx* c = new bk_ctx();
     for (int mu = 0; mu < 4; ++mu) c->dims[mu] = dims[mu];
     c->V = (int)V;
+    {
+        const char* e = getenv("BK_AUTOTUNE");
+        c->autotune = !(e && e[0] == '0');
+    }
     c->device = device;
     bk_status s;
     if ((s = c->U64.ensure((size_t)36 * V * sizeof(double2))) != BK_OK ||
@@ -223,6 +235,52 @@ extern "C" bk_status bk_unpack(bk_ctx* c, const void* Xd, double* X, int L, bk_p
     return launch_unpack(prec, make_field((void*)Xd, L, c->V, prec), X, L, (cudaStream_t)stream);
 }
 
+// Pick the operator's launch shape (columns per thread, sites and column
+// groups per block) for this context: on first use of a (precision, mode,
+// column count) every candidate runs on the caller's data and the fastest
+// (CUDA events, 2 timed launches after 1 warm-up) is kept.  Every candidate
+// computes the same result.
+static bk_status tune_shape(bk_ctx* c, int prec, DslashOp op, cudaStream_t st, bk_ctx::Shape& best) {
+    std::vector<bk_ctx::Shape> cands;
+    const int rpts[3] = {1, 2, 4};
+    for (int ri = 0; ri < (prec == BK_FP64 ? 1 : 3); ++ri) {
+        const int rpt = rpts[ri];
+        if (rpt > 1 && rpt > op.ncol) continue;
+        const int ngroups = (op.ncol + rpt - 1) / rpt;
+        for (int sx : {16, 32})
+            for (int threads : {128, 256}) {
+                int by = std::min(threads / sx, ngroups);
+                if (by < 1) by = 1;
+                cands.push_back({rpt, sx, by});
+            }
+    }
+    cudaEvent_t e0, e1;
+    BK_CUDA_TRY(cudaEventCreate(&e0));
+    BK_CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    best = cands[0];
+    for (const auto& cd : cands) {
+        op.rpt = cd.rpt;
+        op.site_block = cd.sx;
+        op.col_block = cd.by;
+        BK_TRY(launch_dslash(prec, op, st));
+        BK_CUDA_TRY(cudaEventRecord(e0, st));
+        BK_TRY(launch_dslash(prec, op, st));
+        BK_TRY(launch_dslash(prec, op, st));
+        BK_CUDA_TRY(cudaEventRecord(e1, st));
+        BK_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BK_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cd;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return BK_OK;
+}
+
 static bk_status dslash_fields(bk_ctx* c, int prec, const double* kappa, Field x, Field y, Field b, int col0,
                                int ncol, int residual, cudaStream_t st) {
     DslashOp op;
@@ -239,6 +297,19 @@ static bk_status dslash_fields(bk_ctx* c, int prec, const double* kappa, Field x
     op.kappa = kappa;
     op.site_block = 0;
     op.col_block = 0;
+    op.rpt = 0;
+    if (c->autotune && ncol <= BK_MAX_COLS) {
+        const long long key = ((long long)prec << 40) | ((long long)(residual != 0) << 36) | ncol;
+        auto it = c->shapes.find(key);
+        if (it == c->shapes.end()) {
+            bk_ctx::Shape sh;
+            BK_TRY(tune_shape(c, prec, op, st, sh));
+            it = c->shapes.emplace(key, sh).first;
+        }
+        op.rpt = it->second.rpt;
+        op.site_block = it->second.sx;
+        op.col_block = it->second.by;
+    }
     return launch_dslash(prec, op, st);
 }
 
@@ -400,6 +471,10 @@ struct Solve {
     std::vector<int> done;           // per system: 0 active, 1 converged, 2 breakdown, 3 not converged
     std::vector<double> rmax_since;  // per system, mixed precision
     std::vector<int> iters, mv, mv64, nrel;
+    // mixed precision: iterations since the last FP64 update, true residual at
+    // that update, restarts, and systems whose recurrences restart this iteration
+    std::vector<int> since, nrestart, restart_now;
+    std::vector<double> m_upd;
     std::vector<std::vector<double>> hist;
     std::vector<double> true_res, rec_res;
     Field B64, X64, R64, Xlo, R, Rt, Pb, Vb, Wb, Ub, Yb, Tb, Zb, Ptmp;
@@ -719,32 +794,80 @@ struct Solve {
         part.active = a;
     }
 
-    // After the new residual R_{k+1} exists: stopping rule, breakdown flags,
-    // reliable updates.  Returns via `done`.
+    // Copy columns [c0, c0 + n) of src into dst (same precision and layout).
+    bk_status copy_cols(Field dst, Field src, int c0, int n, int prec) {
+        const size_t bytes = (size_t)n * src.cstride * 16;
+        BK_CUDA_TRY(cudaMemcpyAsync((char*)dst.data + (size_t)c0 * src.cstride * 16,
+                                    (char*)src.data + (size_t)c0 * src.cstride * 16, bytes,
+                                    cudaMemcpyDeviceToDevice, st));
+        if (prec == BK_FP16)
+            BK_CUDA_TRY(cudaMemcpyAsync(dst.norm + (size_t)c0 * V, src.norm + (size_t)c0 * V,
+                                        (size_t)n * V * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        return BK_OK;
+    }
+
+    // Mixed precision guard: the low-precision cycle of system s went wrong
+    // (breakdown, non-finite or runaway residual).  Its correction since the
+    // last FP64 update is discarded and the recurrences restart from the last
+    // FP64 true residual (R64 still holds it).
+    bk_status discard_cycle(int s) {
+        const int c0 = part.col0[s], n = part.col0[s + 1] - c0;
+        BK_CUDA_TRY(cudaMemsetAsync((char*)Xlo.data + (size_t)c0 * Xlo.cstride * 16, 0,
+                                    (size_t)n * Xlo.cstride * 16, st));
+        BK_TRY(launch_cast(BK_FP64, field_cols(R64, c0), P, field_cols(R, c0), n, st));
+        launches++;
+        restart_now[s] = 1;
+        nrestart[s]++;
+        since[s] = 0;
+        rmax_since[s] = m_upd[s];
+        return BK_OK;
+    }
+
+    // Restart the recurrences of the systems flagged in restart_now: P = R and,
+    // for BiCGGR, V = W (W = A R must already hold the new residual's image).
+    bk_status apply_restarts() {
+        for (int s = 0; s < nsys; ++s) {
+            if (!restart_now[s]) continue;
+            const int c0 = part.col0[s], n = part.col0[s + 1] - c0;
+            BK_TRY(copy_cols(Pb, R, c0, n, P));
+            if (method == BK_BICGGR) BK_TRY(copy_cols(Vb, Wb, c0, n, P));
+            BK_CUDA_TRY(cudaMemsetAsync(info_g + s, 0, sizeof(int), st));
+            restart_now[s] = 0;
+        }
+        return BK_OK;
+    }
+
+    // After the new residual R_{k+1} exists: stopping rule, breakdown flags and,
+    // in mixed precision, FP64 reliable updates and the cycle guards.
     bk_status check(int k) {
         BK_TRY(residual_norms());
-        std::vector<int> upd;
+        std::vector<int> upd, bad;
+        const double delta = prm->reliable_delta > 0 ? prm->reliable_delta : 0.1;
+        const int kmax = 50;  // forced FP64 update after this many iterations without one
         for (int s = 0; s < nsys; ++s) {
             if (done[s]) continue;
             iters[s] = k + 1;
             mv[s] += 2;
-            if (info_a_h[s] || info_g_h[s] || zbad_h[s]) {
-                done[s] = 2;
-                continue;
-            }
+            const bool brk = info_a_h[s] || info_g_h[s] || zbad_h[s];
             const double m = sys_max(s);
             hist[s].push_back(m);
-            if (!std::isfinite(m)) {
-                done[s] = 2;
+            if (!mixed) {
+                if (brk || !std::isfinite(m)) done[s] = 2;
+                else if (m <= prm->tol) done[s] = 1;
                 continue;
             }
-            if (!mixed) {
-                if (m <= prm->tol) done[s] = 1;
+            since[s]++;
+            if (brk || !std::isfinite(m) || m > 1e3 * m_upd[s]) {
+                bad.push_back(s);
                 continue;
             }
             rmax_since[s] = std::max(rmax_since[s], m);
-            const double delta = prm->reliable_delta > 0 ? prm->reliable_delta : 0.1;
-            if (m <= prm->tol || m < delta * rmax_since[s]) upd.push_back(s);
+            if (m <= prm->tol || m < delta * rmax_since[s] || since[s] >= kmax) upd.push_back(s);
+        }
+        for (int s : bad) {
+            BK_TRY(discard_cycle(s));
+            hist[s].back() = m_upd[s];
+            if (nrestart[s] > 100) done[s] = 2;
         }
         if (!upd.empty()) {
             BK_TRY(reliable_update(upd));
@@ -752,6 +875,8 @@ struct Solve {
                 const double m = sys_max(s);  // FP64 true residual
                 hist[s].back() = m;
                 rmax_since[s] = m;
+                m_upd[s] = m;
+                since[s] = 0;
                 if (m <= prm->tol) done[s] = 1;
             }
         }
@@ -836,6 +961,7 @@ struct Solve {
                 g.Y = Vb;
                 BK_TRY(genop(g));
             }
+            BK_TRY(apply_restarts());
             std::swap(G_RR, G_RRn);
         }
         return BK_OK;
@@ -920,9 +1046,9 @@ struct Solve {
                 g.ym = 1.0;
                 g.skip = info_g;
                 BK_TRY(genop(g));
-                // systems skipped by genop keep P: copy is not needed because they stop
                 std::swap(Pb, Ptmp);
             }
+            BK_TRY(apply_restarts());
         }
         return BK_OK;
     }
@@ -994,6 +1120,10 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
     S.mv.assign(nsys, 0);
     S.mv64.assign(nsys, 0);
     S.nrel.assign(nsys, 0);
+    S.since.assign(nsys, 0);
+    S.nrestart.assign(nsys, 0);
+    S.restart_now.assign(nsys, 0);
+    S.m_upd.assign(nsys, 1.0);
     S.hist.resize(nsys);
     S.true_res.assign(Lt, 0.0);
 
@@ -1025,7 +1155,8 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
     for (int s = 0; s < nsys; ++s) {
         bk_solve_info& in = info[s];
         in.iterations = S.iters[s];
-        in.matvecs = S.mv[s] + (prm->method == BK_BICGGR ? 0 : 0);
+        in.matvecs = S.mv[s];
+        in.restarts = S.nrestart[s];
         in.matvecs_fp64 = S.mv64[s] + 1;  // + final true residual
         in.reliable_updates = S.nrel[s];
         in.breakdown = S.done[s] == 2;
@@ -1037,7 +1168,7 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
         rm = S.hist[s].empty() ? 0.0 : S.hist[s].back();
         in.true_res_max = tm;
         in.rec_res_max = rm;
-        in.converged = S.done[s] == 1 && (S.mixed ? tm <= prm->tol * 10.0 : true);
+        in.converged = S.done[s] == 1;
         if (in.history && prm->record_history) {
             const int n = std::min((int)S.hist[s].size(), prm->maxiter + 1);
             for (int i = 0; i < n; ++i) in.history[i] = S.hist[s][i];

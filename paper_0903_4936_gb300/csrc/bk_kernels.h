@@ -22,7 +22,8 @@ struct DslashOp {
     int residual;
     const double* kappa;   // host array, ncol entries (kappa of column col0 + j)
     int site_block;        // launch shape: sites per thread block (0 = default)
-    int col_block;         // columns per thread block (0 = default)
+    int col_block;         // column groups per thread block (0 = default)
+    int rpt;               // columns per thread: 1, 2 or 4 (0 = 1; FP64 always 1)
 };
 bk_status launch_dslash(int prec, const DslashOp& op, cudaStream_t st);
 

@@ -18,6 +18,8 @@
 #include "bk_common.cuh"
 #include "bk_kernels.h"
 
+#include <algorithm>
+
 namespace {
 
 template <int P>
@@ -93,45 +95,92 @@ __device__ __forceinline__ void load_link(const L* __restrict__ U, int mu, int s
     }
 }
 
-template <int P, int MU>
-__device__ __forceinline__ void hop_dir(const DArgs<P>& a, const int (&co)[4], int s, int c,
-                                        cx<typename Prec<P>::real> (&acc)[12]) {
+// Spinor load that leaves the FP16 per-site scale out of the values: the
+// projection is linear, so the scale is applied to the 12 projected reals
+// instead of the 24 loaded ones.  Returns the scale (1 for FP32 / FP64).
+template <int P>
+__device__ __forceinline__ typename Prec<P>::real load_raw(const Field& f, int c, int s,
+                                                           cx<typename Prec<P>::real> (&v)[12]) {
+    if constexpr (P == BK_FP16) {
+        const uint4* p = (const uint4*)f.data + (size_t)c * f.cstride + s;
+        const float sc = f.norm[(size_t)c * f.V + s];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 q = p[(size_t)k * f.V];
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                float2 g = __half22float2(*reinterpret_cast<const __half2*>(&w[m]));
+                v[4 * k + m] = mk(g.x, g.y);
+            }
+        }
+        return sc;
+    } else {
+        load_spinor<P>(f, c, s, v);
+        return typename Prec<P>::real(1);
+    }
+}
+
+// One direction mu, forward and backward hop, for RPT columns of one site.
+template <int P, int MU, int RPT>
+__device__ __forceinline__ void hop_dir(const DArgs<P>& a, const int (&co)[4], int s, int c0, int nr,
+                                        cx<typename Prec<P>::real> (&acc)[RPT][12]) {
     using R = typename Prec<P>::real;
     const int Lm = a.L[MU], sm = a.st[MU];
     const int sf = co[MU] == Lm - 1 ? s - (Lm - 1) * sm : s + sm;
     const int sb = co[MU] == 0 ? s + (Lm - 1) * sm : s - sm;
     {   // forward: (1 - gamma_mu) U_mu(n) x(n + mu)
-        cx<R> q[12], h[6], w[6], u[9];
-        load_spinor<P>(a.x, c, sf, q);
-        project<MU, -1>(q, h);
+        cx<R> u[9];
         load_link(a.U, MU, s, a.V, u);
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh)
+        for (int r = 0; r < RPT; ++r) {
+            if (r < nr) {
+                cx<R> q[12], h[6], w[6];
+                const R sc = load_raw<P>(a.x, c0 + r, sf, q);
+                project<MU, -1>(q, h);
+                if constexpr (P == BK_FP16) {
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                cx<R> t = u[3 * i] * h[3 * hh];
-                cmac(t, u[3 * i + 1], h[3 * hh + 1]);
-                cmac(t, u[3 * i + 2], h[3 * hh + 2]);
-                w[3 * hh + i] = t;
+                    for (int k = 0; k < 6; ++k) h[k] = sc * h[k];
+                }
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        cx<R> t = u[3 * i] * h[3 * hh];
+                        cmac(t, u[3 * i + 1], h[3 * hh + 1]);
+                        cmac(t, u[3 * i + 2], h[3 * hh + 2]);
+                        w[3 * hh + i] = t;
+                    }
+                reconstruct<MU, -1>(w, acc[r]);
             }
-        reconstruct<MU, -1>(w, acc);
+        }
     }
     {   // backward: (1 + gamma_mu) U_mu(n - mu)^+ x(n - mu)
-        cx<R> q[12], h[6], w[6], u[9];
-        load_spinor<P>(a.x, c, sb, q);
-        project<MU, +1>(q, h);
+        cx<R> u[9];
         load_link(a.U, MU, sb, a.V, u);
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh)
+        for (int r = 0; r < RPT; ++r) {
+            if (r < nr) {
+                cx<R> q[12], h[6], w[6];
+                const R sc = load_raw<P>(a.x, c0 + r, sb, q);
+                project<MU, +1>(q, h);
+                if constexpr (P == BK_FP16) {
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                cx<R> t = mk(R(0), R(0));
-                cjmac(t, u[i], h[3 * hh]);
-                cjmac(t, u[3 + i], h[3 * hh + 1]);
-                cjmac(t, u[6 + i], h[3 * hh + 2]);
-                w[3 * hh + i] = t;
+                    for (int k = 0; k < 6; ++k) h[k] = sc * h[k];
+                }
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        cx<R> t = mk(R(0), R(0));
+                        cjmac(t, u[i], h[3 * hh]);
+                        cjmac(t, u[3 + i], h[3 * hh + 1]);
+                        cjmac(t, u[6 + i], h[3 * hh + 2]);
+                        w[3 * hh + i] = t;
+                    }
+                reconstruct<MU, +1>(w, acc[r]);
             }
-        reconstruct<MU, +1>(w, acc);
+        }
     }
 }
 
@@ -173,17 +222,22 @@ __device__ __forceinline__ void load_clov_block(const float4* __restrict__ C, in
 }
 
 // FP64 needs more registers per thread: cap its blocks at 256 threads.
-template <int P>
-constexpr int dslash_max_threads() { return P == BK_FP64 ? 256 : 512; }
+template <int P, int RPT = 1>
+constexpr int dslash_max_threads() { return (P == BK_FP64 || RPT > 1) ? 256 : 512; }
 
-template <int P>
-__global__ void __launch_bounds__(dslash_max_threads<P>()) k_dslash(const __grid_constant__ DArgs<P> a) {
+// Thread (site s, column group g) computes columns col0 + g*RPT + r, r < RPT:
+// each link and clover block is loaded into registers once and applied to the
+// RPT columns.
+template <int P, int RPT>
+__global__ void __launch_bounds__(dslash_max_threads<P, RPT>()) k_dslash(const __grid_constant__ DArgs<P> a) {
     using R = typename Prec<P>::real;
     const int tid = threadIdx.x;
     const int s = blockIdx.x * a.SX + (tid % a.SX);
-    const int cl = blockIdx.y * (blockDim.x / a.SX) + tid / a.SX;
-    if (s >= a.V || cl >= a.ncol) return;
-    const int c = a.col0 + cl;
+    const int g = blockIdx.y * (blockDim.x / a.SX) + tid / a.SX;
+    const int cl0 = g * RPT;
+    if (s >= a.V || cl0 >= a.ncol) return;
+    const int nr = min(RPT, a.ncol - cl0);
+    const int c0 = a.col0 + cl0;
     int co[4];
     {
         int r = s;
@@ -194,49 +248,58 @@ __global__ void __launch_bounds__(dslash_max_threads<P>()) k_dslash(const __grid
         co[2] = r % a.L[2];
         co[3] = r / a.L[2];
     }
-    cx<R> acc[12];
+    cx<R> acc[RPT][12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = mk(R(0), R(0));
-    hop_dir<P, 0>(a, co, s, c, acc);
-    hop_dir<P, 1>(a, co, s, c, acc);
-    hop_dir<P, 2>(a, co, s, c, acc);
-    hop_dir<P, 3>(a, co, s, c, acc);
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[r][k] = mk(R(0), R(0));
+    hop_dir<P, 0, RPT>(a, co, s, c0, nr, acc);
+    hop_dir<P, 1, RPT>(a, co, s, c0, nr, acc);
+    hop_dir<P, 2, RPT>(a, co, s, c0, nr, acc);
+    hop_dir<P, 3, RPT>(a, co, s, c0, nr, acc);
 
-    cx<R> q[12];
-    load_spinor<P>(a.x, c, s, q);
-    {   // clover: chiral blocks act on a = u + l and b = u - l
-        cx<R> v[6], yv[6];
+    // clover: the chiral blocks act on a = u + l (block 0) and b = u - l (block 1)
+#pragma unroll
+    for (int blk = 0; blk < 2; ++blk) {
         R m[36];
+        load_clov_block(a.C, blk, s, a.V, m);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) v[k] = q[k] + q[k + 6];
-        load_clov_block(a.C, 0, s, a.V, m);
-        herm6(m, v, yv);
+        for (int r = 0; r < RPT; ++r) {
+            if (r < nr) {
+                cx<R> q[12], v[6], yv[6];
+                const R sc = load_raw<P>(a.x, c0 + r, s, q);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            acc[k] = acc[k] + yv[k];
-            acc[k + 6] = acc[k + 6] + yv[k];
-        }
+                for (int k = 0; k < 6; ++k) v[k] = blk == 0 ? q[k] + q[k + 6] : q[k] - q[k + 6];
+                if constexpr (P == BK_FP16) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) v[k] = q[k] - q[k + 6];
-        load_clov_block(a.C, 1, s, a.V, m);
-        herm6(m, v, yv);
+                    for (int k = 0; k < 6; ++k) v[k] = sc * v[k];
+                }
+                herm6(m, v, yv);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            acc[k] = acc[k] + yv[k];
-            acc[k + 6] = acc[k + 6] - yv[k];
+                for (int k = 0; k < 6; ++k) {
+                    acc[r][k] = acc[r][k] + yv[k];
+                    acc[r][k + 6] = blk == 0 ? acc[r][k + 6] + yv[k] : acc[r][k + 6] - yv[k];
+                }
+            }
         }
     }
-    const R kap = (R)a.kappa[cl];
-    cx<R> out[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) out[k] = q[k] - kap * acc[k];
-    if (a.residual) {
-        cx<R> bb[12];
-        load_spinor<P>(a.b, c, s, bb);
+    for (int r = 0; r < RPT; ++r) {
+        if (r < nr) {
+            cx<R> q[12], out[12];
+            load_spinor<P>(a.x, c0 + r, s, q);
+            const R kap = (R)a.kappa[cl0 + r];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) out[k] = bb[k] - out[k];
+            for (int k = 0; k < 12; ++k) out[k] = q[k] - kap * acc[r][k];
+            if (a.residual) {
+                cx<R> bb[12];
+                load_spinor<P>(a.b, c0 + r, s, bb);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) out[k] = bb[k] - out[k];
+            }
+            store_spinor<P>(a.y, c0 + r, s, out);
+        }
     }
-    store_spinor<P>(a.y, c, s, out);
 }
 
 template <int P>
@@ -271,19 +334,32 @@ bk_status dslash_impl(const DslashOp& op, cudaStream_t st) {
     a.ncol = op.ncol;
     a.residual = op.residual;
     for (int j = 0; j < op.ncol; ++j) a.kappa[j] = op.kappa[j];
-    // Launch shape: BY columns x SX sites per block.
+    // Launch shape: RPT columns per thread, BY column groups x SX sites per block.
+    int rpt = op.rpt > 0 ? op.rpt : 1;
+    if (P == BK_FP64) rpt = 1;
+    if (rpt != 1 && rpt != 2 && rpt != 4) rpt = 1;
+    const int ngroups = (op.ncol + rpt - 1) / rpt;
     int BY = op.col_block, SX = op.site_block;
-    if (BY <= 0) {
-        const int nyb = (op.ncol + 15) / 16;
-        BY = (op.ncol + nyb - 1) / nyb;
-    }
-    if (SX <= 0) SX = BY <= 8 ? 32 : 16;
-    const int maxt = dslash_max_threads<P>();
+    const int maxt = rpt > 1 ? 256 : dslash_max_threads<P>();
+    if (SX <= 0) SX = 16;
     if (SX > maxt) SX = maxt;
+    if (BY <= 0) {
+        const int maxby = std::max(1, 256 / SX);
+        const int nyb = (ngroups + maxby - 1) / maxby;
+        BY = (ngroups + nyb - 1) / nyb;
+    }
     if (SX * BY > maxt) BY = maxt / SX;
     a.SX = SX;
-    dim3 grid((op.V + SX - 1) / SX, (op.ncol + BY - 1) / BY);
-    k_dslash<P><<<grid, SX * BY, 0, st>>>(a);
+    dim3 grid((op.V + SX - 1) / SX, (ngroups + BY - 1) / BY);
+    if constexpr (P == BK_FP64) {
+        k_dslash<P, 1><<<grid, SX * BY, 0, st>>>(a);
+    } else {
+        switch (rpt) {
+            case 2: k_dslash<P, 2><<<grid, SX * BY, 0, st>>>(a); break;
+            case 4: k_dslash<P, 4><<<grid, SX * BY, 0, st>>>(a); break;
+            default: k_dslash<P, 1><<<grid, SX * BY, 0, st>>>(a); break;
+        }
+    }
     BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
 }
