@@ -142,6 +142,27 @@ bk_status bk_block_xmy(bk_ctx* ctx, const void* X, const double* M, const double
 bk_status bk_small_solve(int L, const double* G, const double* H, const double s[2],
                          double* Xs, int* info, void* stream);
 
+/* Complex inner product of two canonical FP64 device blocks of L columns:
+ * result = sum over every entry of conj(A) * B (host {re, im}); FP64 partial
+ * sums per thread block, summed in a fixed order.  Synchronises the stream. */
+bk_status bk_dot(bk_ctx* ctx, const double* A, const double* B, int L, double result[2], void* stream);
+
+/* Link derivative for the adjoint of a solve (gradient with respect to the
+ * gauge field).  With H the hopping term and C the clover term of Eq. (wd-op)
+ * (C as built by bk_build_clover, c_SW included),
+ *     f(U) = Re sum_i < lam_i, (H[U] + C[U]) x_i >
+ * changes by df = Re sum_{n,mu} Tr(dU_mu(n) Sigma_mu(n)); F_mu_nu is
+ * differentiated through the four clover leaves of Section 2.  X, Lam:
+ * canonical FP64 device blocks of L columns.  out (device):
+ *   mode 0: scale * Sigma                  [4][V][3][3] complex
+ *   mode 1: scale * Sigma^+  (the complex gradient G with df = Re sum conj(G) dU)
+ *   mode 2: scale * Re Tr(i T_a U Sigma)   [4][V][8] real, T_a = lambda_a / 2:
+ *           the derivative along U -> exp(i eps T_a) U (projection on su(3)).
+ * For L = Re <eta, D_W^-1 B> use x = D_W^-1 B, lam = D_W^-H eta and scale = kappa.
+ * Uses library workspace (10 V * 9 complex).  Errors: NO_GAUGE, INVALID_ARG, CUDA. */
+bk_status bk_gauge_force(bk_ctx* ctx, const double* X, const double* Lam, int L, int mode, double scale,
+                         double* out, void* stream);
+
 /* ---------------------------------------------------------------- solves */
 
 typedef struct bk_solve_params {
@@ -164,6 +185,9 @@ typedef struct bk_solve_params {
                                  L columns, same location as B)            */
     uint64_t seed;         /* seed of rtilde_mode 0                           */
     const double* rtilde;  /* rtilde_mode 2 only                              */
+    int restart_on_update; /* mixed precision: 1 = restart the recurrences
+                              (P = R, V = A R) from every FP64 residual; 0 =
+                              keep them (residual replacement only)           */
     int record_history;    /* 1: info->history[k] = max_i rel. residual       */
     int timing;            /* 1: time every dslash launch with CUDA events    */
 } bk_solve_params;

@@ -21,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import BKError, PREC, METHOD, SolveInfo, SolveParams, check, lib
 
-__all__ = ["Lattice", "BKError", "PREC", "METHOD", "load"]
+__all__ = ["Lattice", "BKError", "PREC", "METHOD", "load", "block_solve_autograd", "small_solve"]
 
 
 def load():
@@ -165,8 +165,30 @@ class Lattice:
                                  _prec(prec), _stream_ptr(self.device)), "bk_block_xmy")
         return Y
 
+    def dot(self, A: torch.Tensor, B: torch.Tensor) -> complex:
+        """sum conj(A) B over two canonical blocks (FP64 device reduction)."""
+        self._check_block(A, "A")
+        self._check_block(B, "B")
+        r = (C.c_double * 2)()
+        check(lib().bk_dot(self._h, _ptr(A), _ptr(B), A.shape[0], r, _stream_ptr(self.device)), "bk_dot")
+        return complex(r[0], r[1])
+
+    def gauge_force(self, X: torch.Tensor, Lam: torch.Tensor, mode=0, scale=1.0) -> torch.Tensor:
+        """Link derivative of Re sum <Lam, (H + C) X> (see bk_gauge_force).
+        mode 0/1: complex128 [4, V, 3, 3] (Sigma / Sigma^+); mode 2: float64 [4, V, 8]."""
+        self._check_block(X, "X")
+        self._check_block(Lam, "Lam")
+        if mode == 2:
+            out = torch.empty((4, self.V, 8), dtype=torch.float64, device=self.device)
+        else:
+            out = torch.empty((4, self.V, 3, 3), dtype=torch.complex128, device=self.device)
+        check(lib().bk_gauge_force(self._h, _ptr(X), _ptr(Lam), X.shape[0], int(mode), float(scale), _ptr(out),
+                                   _stream_ptr(self.device)), "bk_gauge_force")
+        return out
+
     # ------------------------------------------------------------ solves
-    def _params(self, method, prec, tol, maxiter, delta, x0_given, on_host, rtilde, seed, history, timing):
+    def _params(self, method, prec, tol, maxiter, delta, x0_given, on_host, rtilde, seed, history, timing,
+                restart=False):
         """rtilde: None -> seeded Gaussian R~_0 (library default), "r0" -> R~_0 = R_0,
         tensor -> the caller's block (canonical layout, where B lives)."""
         mode, ptr = 0, None
@@ -178,7 +200,7 @@ class Lattice:
             mode, ptr = 2, C.c_void_p(rtilde.data_ptr())
         return SolveParams(METHOD[method] if isinstance(method, str) else int(method), _prec(prec), float(tol),
                            int(maxiter), float(delta), int(x0_given), int(on_host), mode, int(seed), ptr,
-                           int(history), int(timing))
+                           int(bool(restart)), int(history), int(timing))
 
     @staticmethod
     def _info_dict(info: SolveInfo, hist_buf, res_buf):
@@ -189,7 +211,7 @@ class Lattice:
 
     def block_solve(self, B: torch.Tensor, kappa: float, method="bicggr", prec="fp64", tol=1e-10, maxiter=2000,
                     X0: torch.Tensor | None = None, delta=0.0, rtilde=None, seed=0, history=False,
-                    timing=False, out: torch.Tensor | None = None, raise_on_fail=True):
+                    timing=False, out: torch.Tensor | None = None, raise_on_fail=True, restart=False):
         """Solve D_W X = B (Eq. (linear_mrhs)).  B on the GPU, or on the host
         (then pinned memory is best): X is returned where B lives."""
         self._check_block(B, "B")
@@ -203,7 +225,7 @@ class Lattice:
             if rtilde.shape != B.shape or rtilde.is_cuda != B.is_cuda:
                 raise ValueError("rtilde must have B's shape and location")
         prm = self._params(method, prec, tol, maxiter, delta, X0 is not None, on_host, rtilde, seed, history,
-                           timing)
+                           timing, restart)
         info = SolveInfo()
         res_buf = (C.c_double * L)()
         info.true_res = C.cast(res_buf, C.POINTER(C.c_double))
@@ -220,7 +242,7 @@ class Lattice:
 
     def block_solve_batched(self, B: torch.Tensor, kappas: Sequence[float], Ls: Sequence[int], method="bicggr",
                             prec="fp64", tol=1e-10, maxiter=2000, delta=0.0, rtilde=None, seed=0, history=False,
-                            timing=False, raise_on_fail=True):
+                            timing=False, raise_on_fail=True, restart=False):
         """Several systems (kappa_s, L_s columns each, concatenated in B)."""
         self._check_block(B, "B")
         nsys = len(Ls)
@@ -228,7 +250,8 @@ class Lattice:
             raise ValueError("B must hold sum(Ls) columns and one kappa per system")
         on_host = not B.is_cuda
         X = torch.empty_like(B, pin_memory=on_host) if on_host else torch.empty_like(B)
-        prm = self._params(method, prec, tol, maxiter, delta, False, on_host, rtilde, seed, history, timing)
+        prm = self._params(method, prec, tol, maxiter, delta, False, on_host, rtilde, seed, history, timing,
+                           restart)
         infos = (SolveInfo * nsys)()
         res_bufs, hist_bufs = [], []
         for s in range(nsys):
@@ -251,6 +274,51 @@ class Lattice:
         if raise_on_fail:
             check(st, "bk_block_solve_batched")
         return X, out
+
+
+class _BlockSolve(torch.autograd.Function):
+    """X = D_W(U, kappa)^-1 B with the adjoint of Section 3's solve.
+
+    backward: lam = D^-H g = gamma_5 D^-1 gamma_5 g (gamma_5-hermiticity of
+    D_W), grad_B = lam, grad_kappa = Re <lam, X - B> / kappa (D = 1 - kappa M,
+    M X = (X - B) / kappa), grad_U = kappa Sigma^+ from bk_gauge_force.  The
+    adjoint solve recomputes, it stores no Krylov history."""
+
+    @staticmethod
+    def forward(ctx, B, kappa, U, lat, csw, method, prec, tol, maxiter):
+        lat.upload_gauge(U.detach())
+        lat.build_clover(csw)
+        k = float(kappa)
+        X, info = lat.block_solve(B.detach().contiguous(), k, method=method, prec=prec, tol=tol, maxiter=maxiter)
+        ctx.save_for_backward(B.detach(), X, U.detach())
+        ctx.lat, ctx.csw, ctx.k = lat, csw, k
+        ctx.opts = dict(method=method, prec=prec, tol=tol, maxiter=maxiter)
+        return X
+
+    @staticmethod
+    def backward(ctx, gX):
+        B, X, U = ctx.saved_tensors
+        lat, k = ctx.lat, ctx.k
+        lat.upload_gauge(U)
+        lat.build_clover(ctx.csw)
+        Z, _ = lat.block_solve(lat.gamma5(gX.contiguous()), k, **ctx.opts)
+        lam = lat.gamma5(Z)
+        gB = lam if ctx.needs_input_grad[0] else None
+        gk = None
+        if ctx.needs_input_grad[1]:
+            d = lat.dot(lam, X) - lat.dot(lam, B)
+            gk = torch.tensor(d.real / k, dtype=torch.float64, device=X.device)
+        gU = None
+        if ctx.needs_input_grad[2]:
+            gU = lat.gauge_force(X, lam, mode=1, scale=k).reshape(U.shape)
+        return gB, gk, gU, None, None, None, None, None, None
+
+
+def block_solve_autograd(lat: "Lattice", B: torch.Tensor, kappa: torch.Tensor, U: torch.Tensor, csw: float,
+                         method="bicggr", prec="fp64", tol=1e-12, maxiter=5000) -> torch.Tensor:
+    """Differentiable X = D_W^-1 B with respect to B, kappa (0-d float64 tensor)
+    and the gauge field U (complex128 [4, Lt, Lz, Ly, Lx, 3, 3])."""
+    return _BlockSolve.apply(B, kappa, U, lat, csw, method, prec, tol, maxiter)
 
 
 def small_solve(G: torch.Tensor, H: torch.Tensor, scale=1.0):

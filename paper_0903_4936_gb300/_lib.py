@@ -24,7 +24,7 @@ EXPORTED = [
     "bk_status_string", "bk_last_error", "bk_create", "bk_destroy", "bk_upload_gauge",
     "bk_build_clover", "bk_field_bytes", "bk_pack", "bk_unpack", "bk_dslash_dev", "bk_dslash",
     "bk_gamma5", "bk_block_gram", "bk_block_xmy", "bk_small_solve", "bk_block_solve",
-    "bk_block_solve_batched",
+    "bk_block_solve_batched", "bk_dot", "bk_gauge_force",
 ]
 
 
@@ -32,7 +32,8 @@ class SolveParams(C.Structure):
     _fields_ = [
         ("method", C.c_int), ("prec", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int),
         ("reliable_delta", C.c_double), ("x0_given", C.c_int), ("buffers_on_host", C.c_int),
-        ("rtilde_mode", C.c_int), ("seed", C.c_uint64), ("rtilde", C.c_void_p), ("record_history", C.c_int),
+        ("rtilde_mode", C.c_int), ("seed", C.c_uint64), ("rtilde", C.c_void_p), ("restart_on_update", C.c_int),
+        ("record_history", C.c_int),
         ("timing", C.c_int),
     ]
 
@@ -89,6 +90,8 @@ def lib():
                                      C.POINTER(SolveInfo), vp]),
         "bk_block_solve_batched": (C.c_int, [vp, C.POINTER(SolveParams), C.c_int, dp, ip, vp, vp,
                                              C.POINTER(SolveInfo), vp]),
+        "bk_dot": (C.c_int, [vp, vp, vp, C.c_int, dp, vp]),
+        "bk_gauge_force": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

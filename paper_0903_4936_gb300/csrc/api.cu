@@ -112,7 +112,7 @@ struct bk_ctx {
     // scratch of the single-operation entry points
     DevBuf s1, s2, part, scal;
     // solver workspace
-    DevBuf B64, X64, R64, Xlo, blk[8], small, spart, gwork, canonB, canonX, canonRt;
+    DevBuf B64, X64, R64, Xlo, blk[8], small, spart, gwork, canonB, canonX, canonRt, fscratch;
     HostBuf rb_host;
     std::vector<cudaEvent_t> events;
     // operator launch shapes chosen by the autotuner, keyed by (prec, residual, ncol)
@@ -121,6 +121,7 @@ struct bk_ctx {
     };
     std::map<long long, Shape> shapes;
     bool autotune = true;
+    bool verbose = false;  // BK_VERBOSE=1: one line per solve and per tuning decision on stderr
 };
 
 static const void* gauge_ptr(const bk_ctx* c, int prec) { return prec == BK_FP64 ? c->U64.p : c->U32.p; }
@@ -159,6 +160,8 @@ extern "C" bk_status bk_create(const int dims[4], int device, bk_ctx** out) {
     {
         const char* e = getenv("BK_AUTOTUNE");
         c->autotune = !(e && e[0] == '0');
+        const char* v = getenv("BK_VERBOSE");
+        c->verbose = v && v[0] == '1';
     }
     c->device = device;
     bk_status s;
@@ -178,7 +181,7 @@ extern "C" bk_status bk_destroy(bk_ctx* c) {
     cudaSetDevice(c->device);
     DevBuf* bufs[] = {&c->U64, &c->U32, &c->C64, &c->C32, &c->Utmp, &c->s1, &c->s2, &c->part, &c->scal,
                       &c->B64, &c->X64, &c->R64, &c->Xlo, &c->small, &c->spart, &c->gwork, &c->canonB,
-                      &c->canonX, &c->canonRt};
+                      &c->canonX, &c->canonRt, &c->fscratch};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : c->blk) b.release();
     c->rb_host.release();
@@ -305,6 +308,9 @@ static bk_status dslash_fields(bk_ctx* c, int prec, const double* kappa, Field x
             bk_ctx::Shape sh;
             BK_TRY(tune_shape(c, prec, op, st, sh));
             it = c->shapes.emplace(key, sh).first;
+            if (c->verbose)
+                fprintf(stderr, "[bkrylov] tuned operator prec=%d residual=%d ncol=%d: rpt=%d sites=%d groups=%d\n", prec,
+                        residual, ncol, sh.rpt, sh.sx, sh.by);
         }
         op.rpt = it->second.rpt;
         op.site_block = it->second.sx;
@@ -384,6 +390,31 @@ extern "C" bk_status bk_small_solve(int L, const double* G, const double* H, con
     bk_status r = launch_small_solve(G, H, nullptr, Xs, info, p, st, gwork, s);
     if (gwork) cudaFreeAsync(gwork, st);
     return r;
+}
+
+extern "C" bk_status bk_gauge_force(bk_ctx* c, const double* X, const double* Lam, int L, int mode, double scale,
+                                    double* out, void* stream) {
+    BK_CHECK_ARG(c && X && Lam && out && L >= 1 && mode >= 0 && mode <= 2, "bad argument to bk_gauge_force");
+    if (!c->has_gauge || !c->has_clover) {
+        bk_set_error("bk_gauge_force needs bk_upload_gauge and bk_build_clover first");
+        return BK_ERR_NO_GAUGE;
+    }
+    BK_CUDA_TRY(cudaSetDevice(c->device));
+    BK_TRY(c->fscratch.ensure(force_scratch_bytes(c->V)));
+    return launch_gauge_force(c->U64.as<double2>(), X, Lam, L, c->dims, c->csw, mode, scale, out, c->fscratch.p,
+                              (cudaStream_t)stream);
+}
+
+extern "C" bk_status bk_dot(bk_ctx* c, const double* A, const double* B, int L, double result[2], void* stream) {
+    BK_CHECK_ARG(c && A && B && result && L >= 1, "bad argument to bk_dot");
+    BK_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    BK_TRY(c->fscratch.ensure(force_scratch_bytes(c->V)));
+    BK_TRY(c->scal.ensure(2 * sizeof(double)));
+    BK_TRY(launch_canon_dot(A, B, (long long)L * c->V * 12, c->scal.as<double>(), c->fscratch.p, st));
+    BK_CUDA_TRY(cudaMemcpyAsync(result, c->scal.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    BK_CUDA_TRY(cudaStreamSynchronize(st));
+    return BK_OK;
 }
 
 // ================================================================= solver
@@ -566,9 +597,14 @@ struct Solve {
         return g;
     }
 
+    double t_sync_ms = 0.0;
+    int n_sync = 0;
     bk_status readback() {
         BK_CUDA_TRY(cudaMemcpyAsync(rbh, rb_dev, rb_bytes, cudaMemcpyDeviceToHost, st));
+        const auto t0 = std::chrono::steady_clock::now();
         BK_CUDA_TRY(cudaStreamSynchronize(st));
+        t_sync_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        n_sync++;
         if (prm->timing) BK_TRY(harvest_events());
         return BK_OK;
     }
@@ -878,6 +914,7 @@ struct Solve {
                 m_upd[s] = m;
                 since[s] = 0;
                 if (m <= prm->tol) done[s] = 1;
+                else if (prm->restart_on_update) restart_now[s] = 1;
             }
         }
         update_active();
@@ -955,13 +992,24 @@ struct Solve {
                 g.ym = 1.0;
                 g.skip = info_g;
                 BK_TRY(genop(g));
-                // V = W + Y gamma
-                g.E[0] = Wb;
-                g.Mi[0] = Yb;
-                g.Y = Vb;
-                BK_TRY(genop(g));
+                if (!mixed) {
+                    // V = W + Y gamma (the paper's recursion)
+                    g.E[0] = Wb;
+                    g.Mi[0] = Yb;
+                    g.Y = Vb;
+                    BK_TRY(genop(g));
+                }
             }
             BK_TRY(apply_restarts());
+            if (mixed) {
+                // Low-precision inner iterations: V = A P formed explicitly.  It
+                // equals W + Y gamma in exact arithmetic; the recursion drifts
+                // from A P under FP32 rounding and the L x L systems built on V
+                // then lose the iteration.
+                BK_TRY(dslash(P, Pb, Vb, Pb, 0, Lt, 0));
+                for (int s = 0; s < nsys; ++s)
+                    if ((part.active >> s) & 1u) mv[s]++;
+            }
             std::swap(G_RR, G_RRn);
         }
         return BK_OK;
@@ -1150,6 +1198,9 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
         BK_CUDA_TRY(cudaStreamSynchronize(st));
     }
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (c->verbose)
+        fprintf(stderr, "[bkrylov] solve: %.1f ms wall, %d syncs waiting %.1f ms, %lld launches, %d dslash (%.1f ms events)\n",
+                ms, S.n_sync, S.t_sync_ms, S.launches, S.n_dslash, S.t_dslash);
 
     bk_status result = BK_OK;
     for (int s = 0; s < nsys; ++s) {

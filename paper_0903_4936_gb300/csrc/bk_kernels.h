@@ -101,3 +101,14 @@ struct GenOp {
     SysPart p;
 };
 bk_status launch_genop(int prec, const GenOp& g, int V, cudaStream_t st);
+
+// ---------------------------------------------------------------- force.cu
+size_t force_scratch_bytes(int V);
+// Derivative of Re sum_i <lam_i, (H + C) x_i> w.r.t. the links (see force.cu);
+// X, Lam canonical FP64 device blocks of L columns.  mode 0: scale*Sigma,
+// 1: scale*Sigma^+, 2: scale * Re Tr(i T_a U Sigma) (8 reals per link).
+bk_status launch_gauge_force(const double2* U64, const double* X, const double* Lam, int L, const int dims[4],
+                             double csw, int mode, double scale, double* out, void* scratch, cudaStream_t st);
+// result_dev (complex FP64, device) = sum conj(A) B over ncomplex entries
+bk_status launch_canon_dot(const double* A, const double* B, long long ncomplex, double* result_dev,
+                           void* scratch, cudaStream_t st);

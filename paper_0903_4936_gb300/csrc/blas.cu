@@ -76,6 +76,16 @@ struct Chunk<BK_FP16> {
     __device__ static float scale(const Field& f, int c, int s) { return f.norm[(size_t)c * f.V + s]; }
 };
 
+template <typename R>
+__device__ __forceinline__ cx<R> warp_sum_cx(cx<R> v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.r += __shfl_xor_sync(0xffffffffu, v.r, o);
+        v.i += __shfl_xor_sync(0xffffffffu, v.i, o);
+    }
+    return v;
+}
+
 __device__ __forceinline__ double2 warp_sum(double2 v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -155,15 +165,15 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_gram(Field A, Field B, GramTil
                     for (int m = 0; m < cpc; ++m) cjmac(acc[i][j], a[i][m], b[j][m]);
         }
     }
-    // FP64 reduction over the block
+    // warp sums in the arithmetic precision, FP64 across warps and blocks
     __shared__ double2 red[GRAM_THREADS / 32][GT * GT];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < GT; ++i)
 #pragma unroll
         for (int j = 0; j < GT; ++j) {
-            double2 v = warp_sum(make_double2((double)acc[i][j].r, (double)acc[i][j].i));
-            if (lane == 0) red[wid][i * GT + j] = v;
+            const cx<R> v = warp_sum_cx(acc[i][j]);
+            if (lane == 0) red[wid][i * GT + j] = make_double2((double)v.r, (double)v.i);
         }
     __syncthreads();
     if (threadIdx.x < GT * GT) {
@@ -209,11 +219,13 @@ GramTiles make_tiles(const SysPart& p) {
     return g;
 }
 
+// Blocks per tile: enough blocks in total to fill the GPU (>= 4 per SM of
+// 152), but at least 8 sites per thread so that the block reduction stays a
+// small part of the work.
 int gram_nbx(int ntiles, int V) {
-    const int target = 2048;
-    int nbx = (target + ntiles - 1) / ntiles;
-    const int maxb = (V + GRAM_THREADS - 1) / GRAM_THREADS;
-    return std::max(1, std::min(nbx, maxb));
+    const int want = (4 * 152 + ntiles - 1) / ntiles;
+    const int maxb = std::max(1, V / (GRAM_THREADS * 8));
+    return std::max(1, std::min(want, maxb));
 }
 
 // ---------------------------------------------------------------- column dots
@@ -249,8 +261,8 @@ __global__ void __launch_bounds__(DOT_THREADS) k_coldot(DotArgs d, double2* __re
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < MAX_PAIRS; ++k) {
-        double2 v = warp_sum(make_double2((double)acc[k].r, (double)acc[k].i));
-        if (lane == 0) red[wid][k] = v;
+        const cx<R> v = warp_sum_cx(acc[k]);
+        if (lane == 0) red[wid][k] = make_double2((double)v.r, (double)v.i);
     }
     __syncthreads();
     if (threadIdx.x < d.npair) {
@@ -275,9 +287,9 @@ __global__ void k_coldot_finish(const double2* __restrict__ partial, int n, int 
 }
 
 int dot_nbx(int L, int V) {
-    int nbx = (1024 + L - 1) / L;
-    const int maxb = (V + DOT_THREADS - 1) / DOT_THREADS;
-    return std::max(1, std::min(nbx, maxb));
+    const int want = (4 * 152 + L - 1) / L;
+    const int maxb = std::max(1, V / (DOT_THREADS * 8));
+    return std::max(1, std::min(want, maxb));
 }
 
 // ---------------------------------------------------------------- Y = Z + c (X M)
@@ -470,34 +482,42 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_small_solve(const double2* __
 //   X_j      += xa Xin_j + xm matpart_j          (X in FP64 for FP64 blocks, else FP32)
 // coefficient value = mult * (ptr ? ptr[s] : 1), ptr complex FP64 per system.
 
-template <int P>
+template <int P, int J>
 __global__ void __launch_bounds__(128) k_genop(const __grid_constant__ GenOp g, int V) {
     using R = typename Prec<P>::real;
     constexpr int PX = P == BK_FP64 ? BK_FP64 : BK_FP32;
     using RX = typename Prec<PX>::real;
     const int site = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
     if (site >= V) return;
-    const int s = sys_of_col(g.p, j);
+    // column group blockIdx.y -> system s, columns [j0, j0 + nj)
+    int t = blockIdx.y, s = 0;
+    for (; s < g.p.nsys; ++s) {
+        const int ng = (g.p.col0[s + 1] - g.p.col0[s] + J - 1) / J;
+        if (t < ng) break;
+        t -= ng;
+    }
+    if (s >= g.p.nsys) return;
     if (!((g.p.active >> s) & 1u)) return;
     if (g.skip && g.skip[s] != 0) return;
     const int c0 = g.p.col0[s], Ls = g.p.col0[s + 1] - c0;
+    const int j0 = c0 + t * J;
+    const int nj = min(J, c0 + Ls - j0);
     auto coef = [&](const double* ptr, double mult) -> cx<R> {
         if (!ptr) return mk((R)mult, R(0));
         const double2 v = ((const double2*)ptr)[s];
         return mk((R)(mult * v.x), (R)(mult * v.y));
     };
-    cx<R> mp[12];
+    cx<R> mp[J][12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) mp[k] = mk(R(0), R(0));
+    for (int jj = 0; jj < J; ++jj)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) mp[jj][k] = mk(R(0), R(0));
     if (g.M) {
         const double2* Ms = (const double2*)g.M + g.p.coef_off[s];
         cx<R> mc[GENOP_MAXMI];
 #pragma unroll
         for (int u = 0; u < GENOP_MAXMI; ++u) mc[u] = coef(g.ma[u], g.ma_mult[u]);
         for (int i = 0; i < Ls; ++i) {
-            const double2 m = Ms[i * Ls + (j - c0)];
-            const cx<R> mij = mk((R)m.x, (R)m.y);
             cx<R> comb[12];
             {
                 cx<R> v[12];
@@ -515,39 +535,51 @@ __global__ void __launch_bounds__(128) k_genop(const __grid_constant__ GenOp g, 
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 12; ++k) cmac(mp[k], comb[k], mij);
-        }
-    }
-    if (g.hasY) {
-        cx<R> y[12];
-        const cx<R> ym = mk((R)g.ym, R(0));
+            for (int jj = 0; jj < J; ++jj) {
+                if (jj < nj) {
+                    const double2 m = Ms[i * Ls + (j0 - c0 + jj)];
+                    const cx<R> mij = mk((R)m.x, (R)m.y);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) y[k] = ym * mp[k];
-#pragma unroll
-        for (int t = 0; t < GENOP_MAXE; ++t) {
-            if (t < g.ne) {
-                const cx<R> a = coef(g.ea[t], g.ea_mult[t]);
-                cx<R> v[12];
-                load_spinor<P>(g.E[t], j, site, v);
-#pragma unroll
-                for (int k = 0; k < 12; ++k) cmac(y[k], a, v[k]);
+                    for (int k = 0; k < 12; ++k) cmac(mp[jj][k], comb[k], mij);
+                }
             }
         }
-        store_spinor<P>(g.Y, j, site, y);
     }
-    if (g.hasX) {
-        cx<RX> x[12];
-        load_spinor<PX>(g.X, j, site, x);
-        cx<R> v[12];
-        load_spinor<P>(g.Xin, j, site, v);
-        const cx<R> a = coef(g.xa, g.xa_mult);
-        const RX xm = (RX)g.xm;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            const cx<R> t = a * v[k];
-            x[k] = x[k] + mk((RX)t.r, (RX)t.i) + xm * mk((RX)mp[k].r, (RX)mp[k].i);
+    for (int jj = 0; jj < J; ++jj) {
+        if (jj >= nj) continue;
+        const int j = j0 + jj;
+        if (g.hasY) {
+            cx<R> y[12];
+            const cx<R> ym = mk((R)g.ym, R(0));
+#pragma unroll
+            for (int k = 0; k < 12; ++k) y[k] = ym * mp[jj][k];
+#pragma unroll
+            for (int tt = 0; tt < GENOP_MAXE; ++tt) {
+                if (tt < g.ne) {
+                    const cx<R> a = coef(g.ea[tt], g.ea_mult[tt]);
+                    cx<R> v[12];
+                    load_spinor<P>(g.E[tt], j, site, v);
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) cmac(y[k], a, v[k]);
+                }
+            }
+            store_spinor<P>(g.Y, j, site, y);
         }
-        store_spinor<PX>(g.X, j, site, x);
+        if (g.hasX) {
+            cx<RX> x[12];
+            load_spinor<PX>(g.X, j, site, x);
+            cx<R> v[12];
+            load_spinor<P>(g.Xin, j, site, v);
+            const cx<R> a = coef(g.xa, g.xa_mult);
+            const RX xm = (RX)g.xm;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                const cx<R> tv = a * v[k];
+                x[k] = x[k] + mk((RX)tv.r, (RX)tv.i) + xm * mk((RX)mp[jj][k].r, (RX)mp[jj][k].i);
+            }
+            store_spinor<PX>(g.X, j, site, x);
+        }
     }
 }
 
@@ -654,13 +686,25 @@ bk_status launch_small_solve(const double* G, const double* H, const double* sca
 bk_status launch_genop(int prec, const GenOp& g, int V, cudaStream_t st) {
     const int L = g.p.col0[g.p.nsys];
     if (L <= 0) return BK_OK;
-    dim3 grid((V + 127) / 128, L);
+    // J output columns per thread: each loaded input spinor serves J outputs
+    int minL = L;
+    for (int s = 0; s < g.p.nsys; ++s) minL = std::min(minL, g.p.col0[s + 1] - g.p.col0[s]);
+    int J = g.M ? (prec == BK_FP64 ? 2 : 4) : 1;
+    if (minL < J) J = 1;
+    int ngroups = 0;
+    for (int s = 0; s < g.p.nsys; ++s) ngroups += (g.p.col0[s + 1] - g.p.col0[s] + J - 1) / J;
+    dim3 grid((V + 127) / 128, ngroups);
+#define BK_GENOP(PP)                                                                  \
+    if (J == 4) k_genop<PP, 4><<<grid, 128, 0, st>>>(g, V);                          \
+    else if (J == 2) k_genop<PP, 2><<<grid, 128, 0, st>>>(g, V);                     \
+    else k_genop<PP, 1><<<grid, 128, 0, st>>>(g, V);
     switch (prec) {
-        case BK_FP64: k_genop<BK_FP64><<<grid, 128, 0, st>>>(g, V); break;
-        case BK_FP32: k_genop<BK_FP32><<<grid, 128, 0, st>>>(g, V); break;
-        case BK_FP16: k_genop<BK_FP16><<<grid, 128, 0, st>>>(g, V); break;
+        case BK_FP64: BK_GENOP(BK_FP64) break;
+        case BK_FP32: BK_GENOP(BK_FP32) break;
+        case BK_FP16: BK_GENOP(BK_FP16) break;
         default: return BK_ERR_INVALID_ARG;
     }
+#undef BK_GENOP
     BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
 }

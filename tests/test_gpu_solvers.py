@@ -103,10 +103,10 @@ def c2():
     return dims, lat, U, B, dense.from_columns(Xo, dims), A
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_c2_solution_matches_oracle(c2, prec):
+@pytest.mark.parametrize("method,prec", [("bicggr", "fp64"), ("bicgstab", "fp64"), ("bicgstab", "fp32")])
+def test_c2_solution_matches_oracle(c2, method, prec):
     dims, lat, U, B, Xo, A = c2
-    X, info = lat.block_solve(torch.from_numpy(B).cuda(), 0.125, method="bicggr", prec=prec, tol=1e-10,
+    X, info = lat.block_solve(torch.from_numpy(B).cuda(), 0.125, method=method, prec=prec, tol=1e-10,
                               maxiter=1000)
     X = X.cpu().numpy()
     assert info["converged"] == 1 and info["true_res_max"] <= 1e-10
@@ -135,7 +135,7 @@ def test_batched_systems_match_individual(c1):
     kappas = [0.11, 0.12, 0.125]
     Ls = [2, 4, 3]
     Bs = synth.z4_noise(dims, sum(Ls), 77)
-    X, infos = lat.block_solve_batched(torch.from_numpy(Bs).cuda(), kappas, Ls, method="bicggr", prec="fp32",
+    X, infos = lat.block_solve_batched(torch.from_numpy(Bs).cuda(), kappas, Ls, method="bicgstab", prec="fp32",
                                        tol=1e-10, maxiter=1000)
     X = X.cpu().numpy()
     c0 = 0
@@ -150,7 +150,7 @@ def test_batched_systems_match_individual(c1):
 def test_host_buffers_path(c1):
     dims, lat, U, B, Xd, A = c1
     Bh = torch.from_numpy(B).pin_memory()
-    X, info = lat.block_solve(Bh, 0.12, method="bicggr", prec="fp32", tol=1e-10, maxiter=500)
+    X, info = lat.block_solve(Bh, 0.12, method="bicgstab", prec="fp32", tol=1e-10, maxiter=500)
     assert not X.is_cuda
     assert info["converged"] == 1
     assert _dev(X.numpy(), Xd) <= 1e-8
