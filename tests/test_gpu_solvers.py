@@ -214,3 +214,27 @@ def test_bicggr_residual_gap_vs_bicgstab(c2):
     _, ig = lat.block_solve(torch.from_numpy(B).cuda(), 0.125, method="bicggr", prec="fp64", tol=1e-12,
                             maxiter=1000)
     assert ig["true_res_max"] < 5e-12
+
+
+def test_batched_uneven_systems_c4_structure():
+    """The batched configuration's structure on an 8^4 lattice: six systems,
+    kappa 0.120 ... 0.130, L = 4, 12, 12, 24, 48, 96 (196 columns of Z4 noise)
+    in one batched mixed-precision solve (one operator launch for all columns
+    per step, L = 96 exercises the global-memory L x L solve).  Each system
+    must reach its FP64 true residual and agree with its own FP64 solve."""
+    import paper_0903_4936_gb300 as bk
+    dims = (8, 8, 8, 8)
+    lat, U = _setup(dims, 0.5, 1004)
+    kappas = [0.120, 0.122, 0.124, 0.126, 0.128, 0.130]
+    Ls = [4, 12, 12, 24, 48, 96]
+    B = synth.z4_noise(dims, sum(Ls), 4004)
+    Bt = torch.from_numpy(B).cuda()
+    X, infos = lat.block_solve_batched(Bt, kappas, Ls, method="bicgstab", prec="fp32", tol=1e-10, maxiter=3000)
+    X = X.cpu().numpy()
+    c0 = 0
+    for s, (k, L) in enumerate(zip(kappas, Ls)):
+        assert infos[s]["converged"] == 1 and infos[s]["true_res_max"] <= 1e-10, (s, infos[s])
+        Xs, info = lat.block_solve(Bt[c0:c0 + L].contiguous(), k, method="bicggr", prec="fp64", tol=1e-12,
+                                   maxiter=3000)
+        assert _dev(X[c0:c0 + L], Xs.cpu().numpy()) <= 1e-8
+        c0 += L
