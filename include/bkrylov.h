@@ -125,6 +125,30 @@ bk_status bk_gamma5(bk_ctx* ctx, const double* X, double* Y, int L, void* stream
 bk_status bk_block_gram(bk_ctx* ctx, const void* A, const void* B, int L, bk_prec prec,
                         double* G, void* stream);
 
+/* The Gram matrix of bk_block_gram, computed without any allocation.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory at the point of the call -- programs that carve all
+ * of HBM into their own pools up front (a cudaMalloc would fail or fragment
+ * them) and callers that cannot afford the device-wide synchronisation a
+ * cudaMalloc/cudaFree may cause in the middle of a time-critical sequence.
+ * It needs no context: V is the number of lattice sites of the blocks.
+ *   - The per-block partial sums live in a fixed 2 MiB device array
+ *     (131072 complex FP64 slots) that every GPU loading the library holds
+ *     until the process exits.  L must satisfy 16 * ceil(L/4)^2 <= 131072
+ *     (L <= 360); larger L returns BK_ERR_INVALID_ARG and bk_block_gram must
+ *     be used.  Fewer thread blocks are used when the array would not hold
+ *     the usual number; the result is the same sum in a different order.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array and overwrites it; each slot a call
+ *     reads is written earlier in the same call, so nothing needs clearing,
+ *     but calls whose work overlaps on the GPU (other streams, other host
+ *     threads) race on it and must be serialised by the caller.
+ * Arguments and result as bk_block_gram.  Errors: INVALID_ARG, CUDA.      */
+bk_status bk_block_gram_noalloc(int V, const void* A, const void* B, int L, bk_prec prec, double* G,
+                                void* stream);
+
 /* Block linear combination (Section 3, products such as S_k alpha_k):
  *     Y = Z + c * (X M)     with X, Y, Z device blocks of L columns in prec,
  * M an L x L complex FP64 device matrix (row-major, (X M)_j = sum_i X_i M_ij)

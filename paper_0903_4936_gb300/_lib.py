@@ -24,7 +24,7 @@ EXPORTED = [
     "bk_status_string", "bk_last_error", "bk_create", "bk_destroy", "bk_upload_gauge",
     "bk_build_clover", "bk_field_bytes", "bk_pack", "bk_unpack", "bk_dslash_dev", "bk_dslash",
     "bk_gamma5", "bk_block_gram", "bk_block_xmy", "bk_small_solve", "bk_block_solve",
-    "bk_block_solve_batched", "bk_dot", "bk_gauge_force",
+    "bk_block_solve_batched", "bk_dot", "bk_gauge_force", "bk_block_gram_noalloc",
 ]
 
 
@@ -91,6 +91,7 @@ def lib():
         "bk_block_solve_batched": (C.c_int, [vp, C.POINTER(SolveParams), C.c_int, dp, ip, vp, vp,
                                              C.POINTER(SolveInfo), vp]),
         "bk_dot": (C.c_int, [vp, vp, vp, C.c_int, dp, vp]),
+        "bk_block_gram_noalloc": (C.c_int, [C.c_int, vp, vp, C.c_int, C.c_int, vp, vp]),
         "bk_gauge_force": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, vp, vp]),
     }
     for name, (res, args) in sig.items():

@@ -708,3 +708,79 @@ bk_status launch_genop(int prec, const GenOp& g, int V, cudaStream_t st) {
     BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
 }
+
+// ---------------------------------------------------------------- Gram without allocation
+//
+// bk_block_gram_noalloc: the Gram reduction of bk_block_gram with its
+// per-block partial sums kept in a fixed, file-scope device array instead of
+// library workspace, so the call itself never allocates.  See bkrylov.h.
+
+#include <mutex>
+
+namespace {
+
+// Partial-sum slots (complex FP64) shared by every bk_block_gram_noalloc call
+// in the process: 2 MiB of device memory on every GPU that loads the library.
+constexpr int NOALLOC_GRAM_SLOTS = 131072;
+static __device__ __align__(256) double2 g_gram_noalloc_scratch[NOALLOC_GRAM_SLOTS];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[64] = {nullptr};
+
+}  // namespace
+
+extern "C" bk_status bk_block_gram_noalloc(int V, const void* A, const void* B, int L, bk_prec prec, double* G,
+                                           void* stream) {
+    if (V < 16 || !A || !B || !G || L < 1 || (prec != BK_FP64 && prec != BK_FP32 && prec != BK_FP16)) {
+        bk_set_error("bad argument to bk_block_gram_noalloc");
+        return BK_ERR_INVALID_ARG;
+    }
+    SysPart p = single_part(L);
+    GramTiles g = make_tiles(p);
+    const int ntiles = g.cum[BK_MAX_SYS];
+    // One slot per (tile, tile entry, thread block); at least one block per tile must fit.
+    const long long per_block = (long long)ntiles * GT * GT;
+    if (per_block > NOALLOC_GRAM_SLOTS) {
+        bk_set_error("bk_block_gram_noalloc: L = %d needs %lld partial-sum slots per block, more than the fixed %d "
+                     "(L <= 360 fits); use bk_block_gram",
+                     L, per_block, NOALLOC_GRAM_SLOTS);
+        return BK_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    BK_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        bk_set_error("bk_block_gram_noalloc: device index %d out of range", dev);
+        return BK_ERR_INVALID_ARG;
+    }
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_addr[dev]) {
+            void* ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_gram_noalloc_scratch);
+            if (e != cudaSuccess || !ptr) {
+                bk_set_error("bk_block_gram_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+                return BK_ERR_CUDA;
+            }
+            g_noalloc_addr[dev] = ptr;
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    int nbx = gram_nbx(ntiles, V);
+    const long long fit = NOALLOC_GRAM_SLOTS / per_block;
+    if (nbx > fit) nbx = (int)fit;
+    cudaStream_t st = (cudaStream_t)stream;
+    const Field fa = make_field((void*)A, L, V, prec), fb = make_field((void*)B, L, V, prec);
+    double2* part = (double2*)scratch;
+    dim3 grid(nbx, ntiles);
+    switch (prec) {
+        case BK_FP64: k_gram<BK_FP64><<<grid, GRAM_THREADS, 0, st>>>(fa, fb, g, part, V); break;
+        case BK_FP32: k_gram<BK_FP32><<<grid, GRAM_THREADS, 0, st>>>(fa, fb, g, part, V); break;
+        default: k_gram<BK_FP16><<<grid, GRAM_THREADS, 0, st>>>(fa, fb, g, part, V); break;
+    }
+    BK_CUDA_TRY(cudaGetLastError());
+    const int ne = ntiles * GT * GT;
+    k_gram_finish<<<(ne + 127) / 128, 128, 0, st>>>(part, g, nbx, (double2*)G, ntiles);
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}
