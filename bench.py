@@ -9,7 +9,7 @@ and FP64 true residual).  Each solve must reach a FP64 true residual <= 1e-10,
 else the run fails.  Prints ONE JSON line on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload c3|c3-12|c2] [--no-fp64] [--no-cpu-baseline]
+                  [--workload c3|c3-12|c3-48|c2] [--no-fp64] [--no-cpu-baseline]
 
 --impl reference times the FP64 CPU oracle (test infrastructure, written from
 the paper) on a bounded sample of the same workload.
@@ -41,6 +41,10 @@ WORKLOADS = {
     "c3-12": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp32", method="bicgstab",
                   cases=[(0.125, 12, "point")],
                   desc="16^3x32, eps=0.5, c_SW=1.0, kappa=0.125, L=12 point sources; block BiCGSTAB, "
+                       "FP32 inner iterations, FP64 residual replacement, tol 1e-10"),
+    "c3-48": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp32", method="bicgstab",
+                  cases=[(0.125, 48, "z2")],
+                  desc="16^3x32, eps=0.5, c_SW=1.0, kappa=0.125, L=48 complex-Z2 noise; block BiCGSTAB, "
                        "FP32 inner iterations, FP64 residual replacement, tol 1e-10"),
     "c2": dict(dims=(8, 8, 8, 16), eps=0.5, csw=1.0, gauge_seed=1002, prec="fp32", method="bicgstab",
                cases=[(0.125, 12, "point")],
@@ -415,7 +419,7 @@ def main():
 
 # Iteration counts of the GPU solver per workload's first case, used to turn the
 # oracle's seconds per iteration into RHS/s on the reference arm.
-GPU_ITERS_HINT = {"c3": 100, "c3-12": 100, "c2": 60}
+GPU_ITERS_HINT = {"c3": 56, "c3-12": 133, "c3-48": 253, "c2": 122}
 
 if __name__ == "__main__":
     main()

@@ -157,12 +157,14 @@ bk_status bk_block_gram_noalloc(int V, const void* A, const void* B, int L, bk_p
 bk_status bk_block_xmy(bk_ctx* ctx, const void* X, const double* M, const double c[2],
                        const void* Z, void* Y, int L, bk_prec prec, void* stream);
 
-/* Dense L x L solve in FP64 on the device (one thread block):
+/* Dense L x L solve in FP64 on the device, 1 <= L <= 128:
  *     G Xs = s * H,  G, H, Xs device arrays of L*L complex FP64, row-major;
- * s a complex scalar {re, im} (host).  LU with partial pivoting; *info
- * (device int) is set to 0 on success, k+1 if pivot k is below
- * 1e-14 * max|G| or not finite (then Xs is unspecified).  This is the
- * "Solve ... for alpha_k" step of both block algorithms.                  */
+ * s a complex scalar {re, im} (host).  LU with partial pivoting in one thread
+ * block, then one warp per right-hand-side column; *info (device int) is set
+ * to 0 on success, k+1 if pivot k is below 1e-14 * max|G| or not finite (then
+ * Xs is unspecified).  This is the "Solve ... for alpha_k" step of both block
+ * algorithms.  Allocates its L*L factor workspace stream-ordered
+ * (cudaMallocAsync) on the stream.                                       */
 bk_status bk_small_solve(int L, const double* G, const double* H, const double s[2],
                          double* Xs, int* info, void* stream);
 

@@ -112,7 +112,7 @@ struct bk_ctx {
     // scratch of the single-operation entry points
     DevBuf s1, s2, part, scal;
     // solver workspace
-    DevBuf B64, X64, R64, Xlo, blk[8], small, spart, gwork, canonB, canonX, canonRt, fscratch;
+    DevBuf B64, X64, R64, Xlo, blk[8], small, spart, canonB, canonX, canonRt, fscratch;
     HostBuf rb_host;
     std::vector<cudaEvent_t> events;
     // operator launch shapes chosen by the autotuner, keyed by (prec, residual, ncol)
@@ -180,7 +180,7 @@ extern "C" bk_status bk_destroy(bk_ctx* c) {
     if (!c) return BK_OK;
     cudaSetDevice(c->device);
     DevBuf* bufs[] = {&c->U64, &c->U32, &c->C64, &c->C32, &c->Utmp, &c->s1, &c->s2, &c->part, &c->scal,
-                      &c->B64, &c->X64, &c->R64, &c->Xlo, &c->small, &c->spart, &c->gwork, &c->canonB,
+                      &c->B64, &c->X64, &c->R64, &c->Xlo, &c->small, &c->spart, &c->canonB,
                       &c->canonX, &c->canonRt, &c->fscratch};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : c->blk) b.release();
@@ -382,13 +382,21 @@ extern "C" bk_status bk_block_xmy(bk_ctx* c, const void* X, const double* M, con
 
 extern "C" bk_status bk_small_solve(int L, const double* G, const double* H, const double s[2], double* Xs,
                                     int* info, void* stream) {
-    BK_CHECK_ARG(G && H && s && Xs && info && L >= 1 && L <= 1024, "bad argument to bk_small_solve");
+    BK_CHECK_ARG(G && H && s && Xs && info && L >= 1 && L <= 128, "bad argument to bk_small_solve (1 <= L <= 128)");
     cudaStream_t st = (cudaStream_t)stream;
     SysPart p = single_part(L);
-    double* gwork = nullptr;
-    if (L > 48) BK_CUDA_TRY(cudaMallocAsync((void**)&gwork, (size_t)2 * L * L * sizeof(double2), st));
-    bk_status r = launch_small_solve(G, H, nullptr, Xs, info, p, st, gwork, s);
-    if (gwork) cudaFreeAsync(gwork, st);
+    double* LU = nullptr;
+    int* piv = nullptr;
+    BK_CUDA_TRY(cudaMallocAsync((void**)&LU, (size_t)L * L * sizeof(double2), st));
+    cudaError_t e2 = cudaMallocAsync((void**)&piv, (size_t)L * sizeof(int), st);
+    if (e2 != cudaSuccess) {
+        cudaFreeAsync(LU, st);
+        BK_CUDA_TRY(e2);
+    }
+    bk_status r = launch_lu_factor(G, LU, piv, info, p, st);
+    if (r == BK_OK) r = launch_lu_solve(LU, piv, H, nullptr, s, Xs, info, p, st);
+    cudaFreeAsync(piv, st);
+    cudaFreeAsync(LU, st);
     return r;
 }
 
@@ -510,8 +518,8 @@ struct Solve {
     std::vector<double> true_res, rec_res;
     Field B64, X64, R64, Xlo, R, Rt, Pb, Vb, Wb, Ub, Yb, Tb, Zb, Ptmp;
     // small device arrays
-    double *G_V, *G_RR, *G_RRn, *alpha, *gam, *G_Z, *dots, *rn, *zeta, *mzeta, *izeta, *partial, *gwork;
-    int *info_a, *info_g, *zbad;
+    double *G_V, *G_RR, *G_RRn, *alpha, *gam, *G_Z, *dots, *rn, *zeta, *mzeta, *izeta, *partial, *LU;
+    int *info_a, *info_g, *zbad, *piv;
     // host readback
     char* rbh;
     double* rn_h;
@@ -575,9 +583,14 @@ struct Solve {
         launches += 2;
         return launch_coldot(prec, npair, A, B, Lt, out, partial, V, st);
     }
-    bk_status small_solve(const double* G, const double* H, const double* scale, double* X, int* info) {
+    // L x L solves in two steps: factor G once, substitute for each right-hand side
+    bk_status factor(const double* G, int* info) {
         launches += 1;
-        return launch_small_solve(G, H, scale, X, info, part, st, gwork);
+        return launch_lu_factor(G, LU, piv, info, part, st);
+    }
+    bk_status substitute(const double* H, const double* scale_dev, const double* scale_host, double* X, int* info) {
+        launches += 1;
+        return launch_lu_solve(LU, piv, H, scale_dev, scale_host, X, info, part, st);
     }
     bk_status scalars() {
         launches += 1;
@@ -686,8 +699,8 @@ struct Solve {
         }
         // small arrays (complex FP64 unless noted)
         const int nc = ncoef();
-        const size_t nsmall = (size_t)6 * nc + 3 * Lt + Lt + 3 * nsys;
-        BK_TRY(c->small.ensure(nsmall * sizeof(double2) + 3 * nsys * sizeof(int) + 256));
+        const size_t nsmall = (size_t)7 * nc + 3 * Lt + Lt + 3 * nsys;
+        BK_TRY(c->small.ensure(nsmall * sizeof(double2) + (3 * nsys + Lt) * sizeof(int) + 256));
         double2* q = c->small.as<double2>();
         G_V = (double*)q;
         q += nc;
@@ -700,6 +713,8 @@ struct Solve {
         gam = (double*)q;
         q += nc;
         G_Z = (double*)q;
+        q += nc;
+        LU = (double*)q;
         q += nc;
         dots = (double*)q;
         q += 3 * Lt;
@@ -717,6 +732,7 @@ struct Solve {
         info_a = qi;
         info_g = qi + nsys;
         zbad = qi + 2 * nsys;
+        piv = qi + 3 * nsys;
         rb_bytes = (size_t)Lt * sizeof(double2) + 3 * nsys * sizeof(int);
         BK_TRY(c->rb_host.ensure(rb_bytes));
         rbh = (char*)c->rb_host.p;
@@ -728,13 +744,6 @@ struct Solve {
         const size_t pb = std::max(gram_partial_bytes(part, V), coldot_partial_bytes(Lt, 3, V));
         BK_TRY(c->spart.ensure(pb));
         partial = c->spart.as<double>();
-        int maxL = 0;
-        for (int s = 0; s < nsys; ++s) maxL = std::max(maxL, part.col0[s + 1] - part.col0[s]);
-        gwork = nullptr;
-        if (maxL > 48) {
-            BK_TRY(c->gwork.ensure((size_t)2 * nc * sizeof(double2)));
-            gwork = c->gwork.as<double>();
-        }
 
         // B, X0 into the FP64 device layout
         BK_TRY(launch_pack(BK_FP64, Bc, B64, Lt, st));
@@ -930,7 +939,8 @@ struct Solve {
                 BK_TRY(scalars());
             }
             // alpha: (R~^H V) alpha = R~^H R
-            BK_TRY(small_solve(G_V, G_RR, nullptr, alpha, info_a));
+            BK_TRY(factor(G_V, info_a));
+            BK_TRY(substitute(G_RR, nullptr, nullptr, alpha, info_a));
             {   // U = (P - zeta V) alpha;  X += zeta R + U
                 GenOp g = genop0();
                 g.nmi = 2;
@@ -977,7 +987,8 @@ struct Solve {
             BK_TRY(gram(Rt, R, G_RRn));          // R~^H R_{k+1}
             BK_TRY(dslash(P, R, Wb, R, 0, Lt, 0));  // W = A R
             // gamma: (R~^H R_k) gamma = R~^H R_{k+1} / zeta
-            BK_TRY(small_solve(G_RR, G_RRn, izeta, gam, info_g));
+            BK_TRY(factor(G_RR, info_g));
+            BK_TRY(substitute(G_RRn, izeta, nullptr, gam, info_g));
             {   // P = R + U gamma
                 GenOp g = genop0();
                 g.ne = 1;
@@ -1020,7 +1031,8 @@ struct Solve {
             BK_TRY(dslash(P, Pb, Vb, Pb, 0, Lt, 0));  // V = A P
             BK_TRY(gram(Rt, Vb, G_V));
             BK_TRY(gram(Rt, R, G_RR));
-            BK_TRY(small_solve(G_V, G_RR, nullptr, alpha, info_a));  // alpha
+            BK_TRY(factor(G_V, info_a));  // R~^H V, used for alpha and beta
+            BK_TRY(substitute(G_RR, nullptr, nullptr, alpha, info_a));
             {   // T = R - V alpha
                 GenOp g = genop0();
                 g.ne = 1;
@@ -1043,11 +1055,11 @@ struct Solve {
                 BK_TRY(scalars());
                 BK_TRY(gram(Rt, Zb, G_Z));
             }
-            // beta: (R~^H V) beta = -R~^H Z
+            // beta: (R~^H V) beta = -R~^H Z, with the factors of alpha's matrix
             {
                 const double m1[2] = {-1.0, 0.0};
-                launches += 1;
-                BK_TRY(launch_small_solve(G_V, G_Z, nullptr, gam, info_g, part, st, gwork, m1));
+                BK_CUDA_TRY(cudaMemcpyAsync(info_g, info_a, sizeof(int) * nsys, cudaMemcpyDeviceToDevice, st));
+                BK_TRY(substitute(G_Z, nullptr, m1, gam, info_g));
             }
             {   // X += P alpha + zeta T;  R = T - zeta Z
                 GenOp g = genop0();

@@ -63,13 +63,6 @@ bk_status launch_coldot(int prec, int npair, const Field* A, const Field* B, int
 bk_status launch_xmy(int prec, Field X, const double* M, const double* c_dev, Field Z, bool hasZ, Field Y,
                      const SysPart& p, int V, cudaStream_t st);
 
-// Small dense solves, one thread block per system: Xs_s = G_s^{-1} (scale_s H_s),
-// scale_s a complex device scalar (null = 1).  info[s] = 0 or pivot index + 1.
-// `gwork` (2 * sum L_s^2 complex FP64) is needed when some L_s > 48.  When
-// scale_dev is null the complex host value scale_host[2] (or 1) is used.
-bk_status launch_small_solve(const double* G, const double* H, const double* scale_dev, double* Xs, int* info,
-                             const SysPart& p, cudaStream_t st, double* gwork, const double* scale_host = nullptr);
-
 // Fused block update (see blas.cu):
 //   matpart_j = sum_{i in s} (sum_u ma_u Mi_u,i) M_s[i][j]
 //   Y_j = sum_t ea_t E_t,j + ym matpart_j;   X_j += xa Xin_j + xm matpart_j
@@ -112,3 +105,10 @@ bk_status launch_gauge_force(const double2* U64, const double* X, const double* 
 // result_dev (complex FP64, device) = sum conj(A) B over ncomplex entries
 bk_status launch_canon_dot(const double* A, const double* B, long long ncomplex, double* result_dev,
                            void* scratch, cudaStream_t st);
+
+// L x L solves split in two: factor G_s once (LU: complex FP64 per system at
+// coef_off, piv: int per column), then solve any number of right-hand sides
+// Xs_s = G_s^-1 (scale_s H_s).  L <= 128 per system.
+bk_status launch_lu_factor(const double* G, double* LU, int* piv, int* info, const SysPart& p, cudaStream_t st);
+bk_status launch_lu_solve(const double* LU, const int* piv, const double* H, const double* scale_dev,
+                          const double* scale_host, double* Xs, int* info, const SysPart& p, cudaStream_t st);

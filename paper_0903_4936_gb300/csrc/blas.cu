@@ -337,144 +337,6 @@ __device__ __forceinline__ cx<double> cdiv(cx<double> a, cx<double> b) {
     return mk((a.r * b.r + a.i * b.i) / d, (a.i * b.r - a.r * b.i) / d);
 }
 
-constexpr int SOLVE_THREADS = 256;
-constexpr int SOLVE_SMEM_MAXL = 48;
-
-// One block per system: LU with partial pivoting of G_s applied to scale_s H_s.
-// The two L x L work matrices live in shared memory when L <= 48, otherwise in
-// the global work array (2 * sum L_s^2 complex entries).
-__global__ void __launch_bounds__(SOLVE_THREADS) k_small_solve(const double2* __restrict__ G,
-                                                               const double2* __restrict__ H,
-                                                               const double2* __restrict__ scale, double2 hscale,
-                                                               double2* Xs, int* info, SysPart p, double2* gwork) {
-    extern __shared__ double2 smem_raw[];
-    const int s = blockIdx.x;
-    if (!((p.active >> s) & 1u)) return;
-    const int n = p.col0[s + 1] - p.col0[s];
-    const int off = p.coef_off[s];
-    cx<double>* A;
-    cx<double>* Bm;
-    if (n <= SOLVE_SMEM_MAXL) {
-        A = reinterpret_cast<cx<double>*>(smem_raw);
-        Bm = A + n * n;
-    } else {
-        A = reinterpret_cast<cx<double>*>(gwork) + 2 * off;
-        Bm = A + n * n;
-    }
-    __shared__ int piv;
-    __shared__ double gmax;
-    __shared__ int bad;
-    const int tid = threadIdx.x;
-    cx<double> sc = mk(hscale.x, hscale.y);
-    if (scale) sc = mk(scale[s].x, scale[s].y);
-    double lmax = 0.0;
-    for (int e = tid; e < n * n; e += SOLVE_THREADS) {
-        double2 g = G[off + e], h = H[off + e];
-        A[e] = mk(g.x, g.y);
-        Bm[e] = sc * mk(h.x, h.y);
-        lmax = fmax(lmax, fabs(g.x) + fabs(g.y));
-        if (!isfinite(g.x) || !isfinite(g.y)) lmax = INFINITY;
-    }
-    if (tid == 0) {
-        gmax = 0.0;
-        bad = 0;
-    }
-    __syncthreads();
-    // block max of |G|
-    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-    if ((tid & 31) == 0) {
-        unsigned long long* gm = reinterpret_cast<unsigned long long*>(&gmax);
-        atomicMax(gm, __double_as_longlong(lmax));  // non-negative doubles order as integers
-    }
-    __syncthreads();
-    const double thresh = 1e-14 * gmax;
-    if (tid == 0 && !isfinite(gmax)) bad = 1;
-    __syncthreads();
-    for (int k = 0; k < n; ++k) {
-        if (bad) break;
-        if (tid < 32) {
-            double best = -1.0;
-            int bi = k;
-            for (int i = k + tid; i < n; i += 32) {
-                const cx<double> v = A[i * n + k];
-                const double m = fabs(v.r) + fabs(v.i);
-                if (m > best) {
-                    best = m;
-                    bi = i;
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) {
-                    best = ob;
-                    bi = oi;
-                }
-            }
-            if (tid == 0) {
-                piv = bi;
-                if (!(best > thresh) || !isfinite(best)) bad = k + 1;
-            }
-        }
-        __syncthreads();
-        if (bad) break;
-        const int pr = piv;
-        if (pr != k) {
-            for (int c = tid; c < n; c += SOLVE_THREADS) {
-                cx<double> t = A[k * n + c];
-                A[k * n + c] = A[pr * n + c];
-                A[pr * n + c] = t;
-                t = Bm[k * n + c];
-                Bm[k * n + c] = Bm[pr * n + c];
-                Bm[pr * n + c] = t;
-            }
-        }
-        __syncthreads();
-        const cx<double> dk = A[k * n + k];
-        for (int i = k + 1 + tid; i < n; i += SOLVE_THREADS) A[i * n + k] = cdiv(A[i * n + k], dk);
-        __syncthreads();
-        const int m = n - k - 1;
-        // rows i > k: A[i][j>k] -= f_i A[k][j]; B[i][:] -= f_i B[k][:]
-        for (int e = tid; e < m * (m + n); e += SOLVE_THREADS) {
-            const int i = k + 1 + e / (m + n);
-            const int c = e % (m + n);
-            const cx<double> f = A[i * n + k];
-            if (c < m) {
-                const int j = k + 1 + c;
-                cx<double> v = A[i * n + j];
-                cmac(v, mk(-f.r, -f.i), A[k * n + j]);
-                A[i * n + j] = v;
-            } else {
-                const int j = c - m;
-                cx<double> v = Bm[i * n + j];
-                cmac(v, mk(-f.r, -f.i), Bm[k * n + j]);
-                Bm[i * n + j] = v;
-            }
-        }
-        __syncthreads();
-    }
-    if (bad) {
-        if (tid == 0) info[s] = bad;
-        return;
-    }
-    // back substitution, one thread per right-hand-side column
-    for (int j = tid; j < n; j += SOLVE_THREADS) {
-        for (int k = n - 1; k >= 0; --k) {
-            cx<double> v = Bm[k * n + j];
-            for (int mcol = k + 1; mcol < n; ++mcol) cmac(v, mk(-A[k * n + mcol].r, -A[k * n + mcol].i), Bm[mcol * n + j]);
-            v = cdiv(v, A[k * n + k]);
-            Bm[k * n + j] = v;
-        }
-    }
-    __syncthreads();
-    bool finite = true;
-    for (int e = tid; e < n * n; e += SOLVE_THREADS) {
-        Xs[off + e] = make_double2(Bm[e].r, Bm[e].i);
-        if (!isfinite(Bm[e].r) || !isfinite(Bm[e].i)) finite = false;
-    }
-    if (!finite) atomicMax(&info[s], n + 1);
-}
-
 // ---------------------------------------------------------------- fused block update
 //
 //   matpart_j = sum_{i in s} ( sum_u ma_u Mi_u,i ) M_s[i][j]
@@ -583,6 +445,490 @@ __global__ void __launch_bounds__(128) k_genop(const __grid_constant__ GenOp g, 
     }
 }
 
+// ---------------------------------------------------------------- fused block update, tiled
+//
+// Same operation as k_genop for FP32 / FP16 blocks with an L x L matrix.  A
+// thread block takes TS = 16 sites of one system and all of its columns:
+//  * the system's L x L matrix is staged once in shared memory (complex FP32);
+//  * the combined inputs comb_i = sum_u ma_u Mi_u,i are staged KC = 16 columns
+//    at a time ([i][site][component], site stride padded to 13 complex so that
+//    16 sites hit distinct banks);
+//  * thread (site, slot) accumulates the 12 components of output columns
+//    slot, slot + 16, ... (at most JM of them) in registers.
+constexpr int GT_TS = 16;   // sites per block
+constexpr int GT_KC = 16;   // input columns per staged chunk
+constexpr int GT_PAD = 13;  // complex per site row in the staged chunk
+
+template <int P, int JM>
+__global__ void __launch_bounds__(256) k_genop_tiled(const __grid_constant__ GenOp g, int V) {
+    using R = typename Prec<P>::real;
+    static_assert(P != BK_FP64, "FP32 arithmetic only");
+    extern __shared__ float4 gt_smem_raw[];
+    const int s = blockIdx.y;
+    if (!((g.p.active >> s) & 1u)) return;
+    if (g.skip && g.skip[s] != 0) return;
+    const int c0 = g.p.col0[s], Ls = g.p.col0[s + 1] - c0;
+    cx<R>* Msm = reinterpret_cast<cx<R>*>(gt_smem_raw);                    // [Ls][Ls]
+    cx<R>* Csm = Msm + ((Ls * Ls + 1) & ~1);                                  // [KC][TS][PAD]
+    const int tid = threadIdx.x;
+    const int sl = tid % GT_TS, slot = tid / GT_TS;  // site in tile, column slot
+    const int site0 = blockIdx.x * GT_TS;
+    const int site = site0 + sl;
+    const bool live = site < V;
+    // stage the matrix
+    const double2* Ms = (const double2*)g.M + g.p.coef_off[s];
+    for (int e = tid; e < Ls * Ls; e += blockDim.x) {
+        const double2 m = Ms[e];
+        Msm[e] = mk((R)m.x, (R)m.y);
+    }
+    auto coef = [&](const double* ptr, double mult) -> cx<R> {
+        if (!ptr) return mk((R)mult, R(0));
+        const double2 v = ((const double2*)ptr)[s];
+        return mk((R)(mult * v.x), (R)(mult * v.y));
+    };
+    cx<R> mc[GENOP_MAXMI];
+#pragma unroll
+    for (int u = 0; u < GENOP_MAXMI; ++u) mc[u] = coef(g.ma[u], g.ma_mult[u]);
+    cx<R> acc[JM][12];
+#pragma unroll
+    for (int jj = 0; jj < JM; ++jj)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[jj][k] = mk(R(0), R(0));
+    for (int i0 = 0; i0 < Ls; i0 += GT_KC) {
+        const int kc = min(GT_KC, Ls - i0);
+        __syncthreads();  // previous chunk consumed (and the matrix staged on the first pass)
+        // stage comb for columns i0..i0+kc: one (column, site) spinor per thread
+        for (int e = tid; e < kc * GT_TS; e += blockDim.x) {
+            const int ii = e / GT_TS, ss = e % GT_TS;
+            const int st = site0 + ss;
+            cx<R> comb[12];
+            if (st < V) {
+                cx<R> v[12];
+                load_spinor<P>(g.Mi[0], c0 + i0 + ii, st, v);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) comb[k] = mc[0] * v[k];
+#pragma unroll
+                for (int u = 1; u < GENOP_MAXMI; ++u) {
+                    if (u < g.nmi) {
+                        load_spinor<P>(g.Mi[u], c0 + i0 + ii, st, v);
+#pragma unroll
+                        for (int k = 0; k < 12; ++k) cmac(comb[k], mc[u], v[k]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 12; ++k) comb[k] = mk(R(0), R(0));
+            }
+            cx<R>* dst = Csm + (ii * GT_TS + ss) * GT_PAD;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) dst[k] = comb[k];
+        }
+        __syncthreads();
+        for (int ii = 0; ii < kc; ++ii) {
+            const cx<R>* src = Csm + (ii * GT_TS + sl) * GT_PAD;
+            cx<R> x[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) x[k] = src[k];
+            const cx<R>* mrow = Msm + (i0 + ii) * Ls;
+#pragma unroll
+            for (int jj = 0; jj < JM; ++jj) {
+                const int j = slot + GT_TS * jj;
+                if (j < Ls) {
+                    const cx<R> m = mrow[j];
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) cmac(acc[jj][k], x[k], m);
+                }
+            }
+        }
+    }
+    if (!live) return;
+    using RX = float;
+#pragma unroll
+    for (int jj = 0; jj < JM; ++jj) {
+        const int jl = slot + GT_TS * jj;
+        if (jl >= Ls) continue;
+        const int j = c0 + jl;
+        if (g.hasY) {
+            cx<R> y[12];
+            const cx<R> ym = mk((R)g.ym, R(0));
+#pragma unroll
+            for (int k = 0; k < 12; ++k) y[k] = ym * acc[jj][k];
+#pragma unroll
+            for (int tt = 0; tt < GENOP_MAXE; ++tt) {
+                if (tt < g.ne) {
+                    const cx<R> a = coef(g.ea[tt], g.ea_mult[tt]);
+                    cx<R> v[12];
+                    load_spinor<P>(g.E[tt], j, site, v);
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) cmac(y[k], a, v[k]);
+                }
+            }
+            store_spinor<P>(g.Y, j, site, y);
+        }
+        if (g.hasX) {
+            cx<RX> x[12];
+            load_spinor<BK_FP32>(g.X, j, site, x);
+            cx<R> v[12];
+            load_spinor<P>(g.Xin, j, site, v);
+            const cx<R> a = coef(g.xa, g.xa_mult);
+            const RX xm = (RX)g.xm;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                const cx<R> tv = a * v[k];
+                x[k] = x[k] + mk((RX)tv.r, (RX)tv.i) + xm * mk((RX)acc[jj][k].r, (RX)acc[jj][k].i);
+            }
+            store_spinor<BK_FP32>(g.X, j, site, x);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- Gram, tiled
+//
+// G_s = A_s^H B_s for FP32 / FP16 blocks with every L_s <= 48.  A thread block
+// (256 threads) walks site tiles of GG_TS = 16 sites of one system, stages
+// both blocks' columns of the tile in shared memory ([column][site * 12 +
+// component], column stride padded to 193 complex), and each thread adds the
+// products of its 3 x 3 output tile over its slice of the tile's 192 entries.
+// FP32 sums are moved into FP64 registers every GG_FLUSH tiles; slices and
+// thread blocks are combined in FP64.
+constexpr int GG_TS = 16;
+constexpr int GG_K = GG_TS * 12;     // 192 entries per column per tile
+constexpr int GG_LD = GG_K + 1;      // padded column stride (complex)
+constexpr int GG_T = 3;              // output tile side per thread
+constexpr int GG_FLUSH = 4;
+
+template <int P>
+__global__ void __launch_bounds__(256) k_gram_tiled(Field A, Field B, SysPart p, double2* __restrict__ partial,
+                                                    int V, int ntile_sites) {
+    using R = typename Prec<P>::real;
+    using CH = Chunk<P>;
+    constexpr int cpc = CH::cpc;
+    constexpr int nch = Prec<P>::nchunk;
+    extern __shared__ float4 gg_smem_raw[];
+    const int s = blockIdx.y;
+    const int c0 = p.col0[s], Ls = p.col0[s + 1] - c0;
+    const int nb = (Ls + GG_T - 1) / GG_T;          // tiles per side
+    const int Lp = nb * GG_T;
+    const int ntiles = nb * nb;
+    const int KS = max(1, (int)blockDim.x / ntiles);  // k-slices
+    cx<R>* sA = reinterpret_cast<cx<R>*>(gg_smem_raw);
+    cx<R>* sB = sA + Lp * GG_LD;
+    const int tid = threadIdx.x;
+    const int tile = tid % ntiles, ks = tid / ntiles;
+    const bool worker = ks < KS;
+    const int ti = tile / nb, tj = tile % nb;
+    const int klen = (GG_K + KS - 1) / KS;
+    const int kbeg = min(GG_K, ks * klen), kend = min(GG_K, kbeg + klen);
+    cx<R> acc[GG_T][GG_T];
+    double2 acc64[GG_T][GG_T];
+#pragma unroll
+    for (int a = 0; a < GG_T; ++a)
+#pragma unroll
+        for (int b = 0; b < GG_T; ++b) {
+            acc[a][b] = mk(R(0), R(0));
+            acc64[a][b] = make_double2(0.0, 0.0);
+        }
+    int since = 0;
+    for (int tt = blockIdx.x; tt < ntile_sites; tt += gridDim.x) {
+        const int site0 = tt * GG_TS;
+        __syncthreads();
+        // stage: one (column, site, chunk) per thread and pass
+        const int nstage = Lp * GG_TS * nch;
+        for (int e = tid; e < nstage; e += blockDim.x) {
+            const int ss = e % GG_TS;
+            const int rest = e / GG_TS;
+            const int ch = rest % nch, col = rest / nch;
+            const int site = site0 + ss;
+            cx<R> va[cpc], vb[cpc];
+            if (col < Ls && site < V) {
+                CH::load(A, c0 + col, site, ch, va);
+                CH::load(B, c0 + col, site, ch, vb);
+                const R sa = (R)CH::scale(A, c0 + col, site), sb = (R)CH::scale(B, c0 + col, site);
+#pragma unroll
+                for (int m = 0; m < cpc; ++m) {
+                    va[m] = sa * va[m];
+                    vb[m] = sb * vb[m];
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < cpc; ++m) va[m] = vb[m] = mk(R(0), R(0));
+            }
+#pragma unroll
+            for (int m = 0; m < cpc; ++m) {
+                const int k = ss * 12 + ch * cpc + m;
+                sA[col * GG_LD + k] = va[m];
+                sB[col * GG_LD + k] = vb[m];
+            }
+        }
+        __syncthreads();
+        if (worker) {
+            for (int k = kbeg; k < kend; ++k) {
+                cx<R> a[GG_T], b[GG_T];
+#pragma unroll
+                for (int q = 0; q < GG_T; ++q) {
+                    a[q] = sA[(ti * GG_T + q) * GG_LD + k];
+                    b[q] = sB[(tj * GG_T + q) * GG_LD + k];
+                }
+#pragma unroll
+                for (int x = 0; x < GG_T; ++x)
+#pragma unroll
+                    for (int y = 0; y < GG_T; ++y) cjmac(acc[x][y], a[x], b[y]);
+            }
+        }
+        if (++since == GG_FLUSH) {
+            since = 0;
+#pragma unroll
+            for (int x = 0; x < GG_T; ++x)
+#pragma unroll
+                for (int y = 0; y < GG_T; ++y) {
+                    acc64[x][y].x += (double)acc[x][y].r;
+                    acc64[x][y].y += (double)acc[x][y].i;
+                    acc[x][y] = mk(R(0), R(0));
+                }
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < GG_T; ++x)
+#pragma unroll
+        for (int y = 0; y < GG_T; ++y) {
+            acc64[x][y].x += (double)acc[x][y].r;
+            acc64[x][y].y += (double)acc[x][y].i;
+        }
+    // combine the k-slices in FP64 through shared memory
+    __syncthreads();
+    double2* red = reinterpret_cast<double2*>(gg_smem_raw);  // [KS][ntiles][9]
+    if (worker) {
+#pragma unroll
+        for (int x = 0; x < GG_T; ++x)
+#pragma unroll
+            for (int y = 0; y < GG_T; ++y) red[((size_t)ks * ntiles + tile) * 9 + x * 3 + y] = acc64[x][y];
+    }
+    __syncthreads();
+    const int off = p.coef_off[s];
+    for (int e = tid; e < ntiles * 9; e += blockDim.x) {
+        const int tl = e / 9, xy = e % 9;
+        double2 v = make_double2(0.0, 0.0);
+        for (int q = 0; q < KS; ++q) {
+            const double2 w = red[((size_t)q * ntiles + tl) * 9 + xy];
+            v.x += w.x;
+            v.y += w.y;
+        }
+        const int i = (tl / nb) * GG_T + xy / 3, j = (tl % nb) * GG_T + xy % 3;
+        if (i < Ls && j < Ls) partial[(size_t)blockIdx.x * p.coef_off[p.nsys] + off + i * Ls + j] = v;
+    }
+}
+
+__global__ void k_gram_tiled_finish(const double2* __restrict__ partial, int nentries, int nbx,
+                                    double2* __restrict__ G) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nentries) return;
+    double2 v = make_double2(0.0, 0.0);
+    for (int b = 0; b < nbx; ++b) {
+        const double2 w = partial[(size_t)b * nentries + e];
+        v.x += w.x;
+        v.y += w.y;
+    }
+    G[e] = v;
+}
+
+int gram_tiled_nbx(int nsys, int V) {
+    const int tiles = (V + GG_TS - 1) / GG_TS;
+    return std::max(1, std::min(tiles, (2 * 152 + nsys - 1) / nsys));
+}
+
+bool gram_tiled_ok(int prec, const SysPart& p) {
+    if (prec == BK_FP64) return false;
+    for (int s = 0; s < p.nsys; ++s)
+        if (p.col0[s + 1] - p.col0[s] > 16 * GG_T) return false;
+    return true;
+}
+
+// ---------------------------------------------------------------- L x L solves: factor, then substitute
+//
+// k_lu_factor: one thread block per system factors P G = L U (FP64, partial
+// pivoting, matrix in shared memory for L <= 96) and stores the factors and
+// the pivot rows; info[s] = k + 1 if pivot k is below 1e-14 max|G| or not
+// finite.  k_lu_solve: one warp per right-hand-side column computes
+// X = G^-1 (scale H) from the factors.
+
+constexpr int LU_THREADS = 256;
+constexpr int LU_MAXL_SMEM = 96;
+
+__global__ void __launch_bounds__(LU_THREADS) k_lu_factor(const double2* __restrict__ G, double2* __restrict__ LU,
+                                                          int* __restrict__ piv, int* info, SysPart p) {
+    extern __shared__ double2 lu_smem_raw[];
+    const int s = blockIdx.x;
+    if (!((p.active >> s) & 1u)) return;
+    const int n = p.col0[s + 1] - p.col0[s];
+    const int off = p.coef_off[s];
+    cx<double>* A = n <= LU_MAXL_SMEM ? reinterpret_cast<cx<double>*>(lu_smem_raw)
+                                      : reinterpret_cast<cx<double>*>(LU) + off;
+    __shared__ int pr_s, bad;
+    __shared__ double gmax;
+    const int tid = threadIdx.x;
+    double lmax = 0.0;
+    for (int e = tid; e < n * n; e += LU_THREADS) {
+        const double2 g = G[off + e];
+        A[e] = mk(g.x, g.y);
+        lmax = fmax(lmax, fabs(g.x) + fabs(g.y));
+        if (!isfinite(g.x) || !isfinite(g.y)) lmax = INFINITY;
+    }
+    if (tid == 0) {
+        gmax = 0.0;
+        bad = 0;
+    }
+    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if ((tid & 31) == 0) atomicMax(reinterpret_cast<unsigned long long*>(&gmax), __double_as_longlong(lmax));
+    __syncthreads();
+    const double thresh = 1e-14 * gmax;
+    if (tid == 0 && !isfinite(gmax)) bad = 1;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (bad) break;
+        if (tid < 32) {
+            double best = -1.0;
+            int bi = k;
+            for (int i = k + tid; i < n; i += 32) {
+                const cx<double> v = A[i * n + k];
+                const double m = fabs(v.r) + fabs(v.i);
+                if (m > best) {
+                    best = m;
+                    bi = i;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (tid == 0) {
+                pr_s = bi;
+                piv[p.col0[s] + k] = bi;
+                if (!(best > thresh) || !isfinite(best)) bad = k + 1;
+            }
+        }
+        __syncthreads();
+        if (bad) break;
+        const int pr = pr_s;
+        if (pr != k)
+            for (int c = tid; c < n; c += LU_THREADS) {
+                const cx<double> t = A[k * n + c];
+                A[k * n + c] = A[pr * n + c];
+                A[pr * n + c] = t;
+            }
+        __syncthreads();
+        const cx<double> dk = A[k * n + k];
+        for (int i = k + 1 + tid; i < n; i += LU_THREADS) A[i * n + k] = cdiv(A[i * n + k], dk);
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int e = tid; e < m * m; e += LU_THREADS) {
+            const int i = k + 1 + e / m, j = k + 1 + e % m;
+            cx<double> v = A[i * n + j];
+            const cx<double> f = A[i * n + k];
+            cmac(v, mk(-f.r, -f.i), A[k * n + j]);
+            A[i * n + j] = v;
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) info[s] = bad;
+        return;
+    }
+    if (n <= LU_MAXL_SMEM)
+        for (int e = tid; e < n * n; e += LU_THREADS) LU[off + e] = make_double2(A[e].r, A[e].i);
+}
+
+// grid: (ceil(maxL / 4), nsys); 4 warps per block, one right-hand-side column per warp
+__global__ void __launch_bounds__(128) k_lu_solve(const double2* __restrict__ LU, const int* __restrict__ piv,
+                                                  const double2* __restrict__ H, const double2* __restrict__ scale,
+                                                  double2 hscale, double2* __restrict__ Xs, int* info, SysPart p) {
+    const int s = blockIdx.y;
+    if (!((p.active >> s) & 1u)) return;
+    if (info[s] != 0) return;
+    const int n = p.col0[s + 1] - p.col0[s];
+    const int j = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (j >= n) return;
+    const int off = p.coef_off[s];
+    const cx<double>* F = reinterpret_cast<const cx<double>*>(LU) + off;
+    const int* pv = piv + p.col0[s];
+    cx<double> sc = mk(hscale.x, hscale.y);
+    if (scale) sc = mk(scale[s].x, scale[s].y);
+    // column j of scale * H, rows distributed over the lanes (n <= 4 * 32 handled by 4 slots)
+    constexpr int SL = 4;
+    cx<double> b[SL];
+#pragma unroll
+    for (int q = 0; q < SL; ++q) {
+        const int i = lane + 32 * q;
+        b[q] = mk(0.0, 0.0);
+        if (i < n) {
+            const double2 h = H[off + i * n + j];
+            b[q] = sc * mk(h.x, h.y);
+        }
+    }
+    auto get = [&](int i) -> cx<double> {
+        cx<double> v = b[0];
+#pragma unroll
+        for (int q = 1; q < SL; ++q)
+            if (i >= 32 * q) v = b[q];
+        const int src = i & 31;
+        return mk(__shfl_sync(0xffffffffu, v.r, src), __shfl_sync(0xffffffffu, v.i, src));
+    };
+    auto put = [&](int i, cx<double> v) {
+#pragma unroll
+        for (int q = 0; q < SL; ++q)
+            if (lane + 32 * q == i) b[q] = v;
+    };
+    // row interchanges in the order of factorisation
+    for (int k = 0; k < n; ++k) {
+        const int pk = pv[k];
+        if (pk != k) {
+            const cx<double> vk = get(k), vp = get(pk);
+            put(k, vp);
+            put(pk, vk);
+        }
+    }
+    // L y = P b (unit lower triangle)
+    for (int k = 0; k < n; ++k) {
+        const cx<double> yk = get(k);
+#pragma unroll
+        for (int q = 0; q < SL; ++q) {
+            const int i = lane + 32 * q;
+            if (i > k && i < n) {
+                const cx<double> l = F[i * n + k];
+                cmac(b[q], mk(-l.r, -l.i), yk);
+            }
+        }
+    }
+    // U x = y
+    for (int k = n - 1; k >= 0; --k) {
+        cx<double> xk = cdiv(get(k), F[k * n + k]);
+        put(k, xk);
+#pragma unroll
+        for (int q = 0; q < SL; ++q) {
+            const int i = lane + 32 * q;
+            if (i < k) {
+                const cx<double> u = F[i * n + k];
+                cmac(b[q], mk(-u.r, -u.i), xk);
+            }
+        }
+    }
+    bool finite = true;
+#pragma unroll
+    for (int q = 0; q < SL; ++q) {
+        const int i = lane + 32 * q;
+        if (i < n) {
+            Xs[off + i * n + j] = make_double2(b[q].r, b[q].i);
+            if (!isfinite(b[q].r) || !isfinite(b[q].i)) finite = false;
+        }
+    }
+    if (!finite) atomicMax(&info[s], n + 1);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
@@ -591,11 +937,38 @@ size_t gram_partial_bytes(const SysPart& p, int V) {
     GramTiles g = make_tiles(p);
     const int ntiles = g.cum[BK_MAX_SYS];
     const int nbx = gram_nbx(ntiles, V);
-    return (size_t)ntiles * GT * GT * nbx * sizeof(double2);
+    size_t b = (size_t)ntiles * GT * GT * nbx * sizeof(double2);
+    const size_t bt = (size_t)gram_tiled_nbx(p.nsys, V) * p.coef_off[p.nsys] * sizeof(double2);
+    return std::max(b, bt);
 }
 
 bk_status launch_gram(int prec, Field A, Field B, const SysPart& p, double* G, double* partial, int V,
                       cudaStream_t st) {
+    if (gram_tiled_ok(prec, p)) {
+        int maxL = 0;
+        for (int s = 0; s < p.nsys; ++s) maxL = std::max(maxL, p.col0[s + 1] - p.col0[s]);
+        const int Lp = (maxL + GG_T - 1) / GG_T * GG_T;
+        const size_t smem = std::max((size_t)2 * Lp * GG_LD * sizeof(cx<float>),
+                                     (size_t)256 * 9 * sizeof(double2));
+        const int nbx = gram_tiled_nbx(p.nsys, V);
+        const int ntile_sites = (V + GG_TS - 1) / GG_TS;
+        dim3 grid(nbx, p.nsys);
+        double2* part = (double2*)partial;
+        if (prec == BK_FP32) {
+            BK_CUDA_TRY(cudaFuncSetAttribute(k_gram_tiled<BK_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+            k_gram_tiled<BK_FP32><<<grid, 256, smem, st>>>(A, B, p, part, V, ntile_sites);
+        } else {
+            BK_CUDA_TRY(cudaFuncSetAttribute(k_gram_tiled<BK_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+            k_gram_tiled<BK_FP16><<<grid, 256, smem, st>>>(A, B, p, part, V, ntile_sites);
+        }
+        BK_CUDA_TRY(cudaGetLastError());
+        const int ne = p.coef_off[p.nsys];
+        k_gram_tiled_finish<<<(ne + 127) / 128, 128, 0, st>>>(part, ne, nbx, (double2*)G);
+        BK_CUDA_TRY(cudaGetLastError());
+        return BK_OK;
+    }
     GramTiles g = make_tiles(p);
     const int ntiles = g.cum[BK_MAX_SYS];
     if (ntiles == 0) return BK_OK;
@@ -662,30 +1035,50 @@ bk_status launch_xmy(int prec, Field X, const double* M, const double* c_dev, Fi
     return BK_OK;
 }
 
-bk_status launch_small_solve(const double* G, const double* H, const double* scale_dev, double* Xs, int* info,
-                             const SysPart& p, cudaStream_t st, double* gwork, const double* scale_host) {
+// Tiled path: FP32/FP16 blocks with a matrix and every system L <= 96.
+static bk_status launch_genop_tiled(int prec, const GenOp& g, int V, cudaStream_t st, bool& done) {
+    done = false;
+    if (prec == BK_FP64 || !g.M) return BK_OK;
     int maxL = 0;
-    for (int s = 0; s < p.nsys; ++s) maxL = std::max(maxL, p.col0[s + 1] - p.col0[s]);
-    if (maxL > SOLVE_SMEM_MAXL && gwork == nullptr) {
-        bk_set_error("small solve with L > %d needs a global work array", SOLVE_SMEM_MAXL);
-        return BK_ERR_INVALID_ARG;
+    for (int s = 0; s < g.p.nsys; ++s) maxL = std::max(maxL, g.p.col0[s + 1] - g.p.col0[s]);
+    if (maxL > 96) return BK_OK;
+    const int jm = (maxL + GT_TS - 1) / GT_TS;
+    const size_t smem = (size_t)(((maxL * maxL + 1) & ~1) + GT_KC * GT_TS * GT_PAD) * sizeof(cx<float>);
+    dim3 grid((V + GT_TS - 1) / GT_TS, g.p.nsys);
+#define BK_GT(PP, JJ)                                                                                   \
+    {                                                                                                   \
+        BK_CUDA_TRY(cudaFuncSetAttribute(k_genop_tiled<PP, JJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)smem));                                                   \
+        k_genop_tiled<PP, JJ><<<grid, 256, smem, st>>>(g, V);                                          \
     }
-    const int smemL = std::min(maxL, SOLVE_SMEM_MAXL);
-    const size_t smem = (size_t)2 * smemL * smemL * sizeof(double2);
-    BK_CUDA_TRY(cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)((size_t)2 * SOLVE_SMEM_MAXL * SOLVE_SMEM_MAXL * sizeof(double2))));
-    BK_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int) * p.nsys, st));
-    const double2 hs = scale_host ? make_double2(scale_host[0], scale_host[1]) : make_double2(1.0, 0.0);
-    k_small_solve<<<p.nsys, SOLVE_THREADS, smem, st>>>((const double2*)G, (const double2*)H,
-                                                       (const double2*)scale_dev, hs, (double2*)Xs, info, p,
-                                                       (double2*)gwork);
+#define BK_GT_P(PP)                                 \
+    switch (jm) {                                   \
+        case 1: BK_GT(PP, 1) break;                 \
+        case 2: BK_GT(PP, 2) break;                 \
+        case 3: BK_GT(PP, 3) break;                 \
+        case 4: BK_GT(PP, 4) break;                 \
+        default: BK_GT(PP, 6) break;                \
+    }
+    if (prec == BK_FP32) {
+        BK_GT_P(BK_FP32)
+    } else {
+        BK_GT_P(BK_FP16)
+    }
+#undef BK_GT_P
+#undef BK_GT
     BK_CUDA_TRY(cudaGetLastError());
+    done = true;
     return BK_OK;
 }
 
 bk_status launch_genop(int prec, const GenOp& g, int V, cudaStream_t st) {
     const int L = g.p.col0[g.p.nsys];
     if (L <= 0) return BK_OK;
+    {
+        bool done = false;
+        bk_status e = launch_genop_tiled(prec, g, V, st, done);
+        if (e != BK_OK || done) return e;
+    }
     // J output columns per thread: each loaded input spinor serves J outputs
     int minL = L;
     for (int s = 0; s < g.p.nsys; ++s) minL = std::min(minL, g.p.col0[s + 1] - g.p.col0[s]);
@@ -781,6 +1174,35 @@ extern "C" bk_status bk_block_gram_noalloc(int V, const void* A, const void* B, 
     BK_CUDA_TRY(cudaGetLastError());
     const int ne = ntiles * GT * GT;
     k_gram_finish<<<(ne + 127) / 128, 128, 0, st>>>(part, g, nbx, (double2*)G, ntiles);
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}
+
+bk_status launch_lu_factor(const double* G, double* LU, int* piv, int* info, const SysPart& p, cudaStream_t st) {
+    int maxL = 0;
+    for (int s = 0; s < p.nsys; ++s) maxL = std::max(maxL, p.col0[s + 1] - p.col0[s]);
+    if (maxL > 128) {
+        bk_set_error("L x L factorisation supports L <= 128 per system");
+        return BK_ERR_INVALID_ARG;
+    }
+    const int sL = std::min(maxL, LU_MAXL_SMEM);
+    const size_t smem = (size_t)sL * sL * sizeof(double2);
+    BK_CUDA_TRY(cudaFuncSetAttribute(k_lu_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)((size_t)LU_MAXL_SMEM * LU_MAXL_SMEM * sizeof(double2))));
+    BK_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int) * p.nsys, st));
+    k_lu_factor<<<p.nsys, LU_THREADS, smem, st>>>((const double2*)G, (double2*)LU, piv, info, p);
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}
+
+bk_status launch_lu_solve(const double* LU, const int* piv, const double* H, const double* scale_dev,
+                          const double* scale_host, double* Xs, int* info, const SysPart& p, cudaStream_t st) {
+    int maxL = 0;
+    for (int s = 0; s < p.nsys; ++s) maxL = std::max(maxL, p.col0[s + 1] - p.col0[s]);
+    const double2 hs = scale_host ? make_double2(scale_host[0], scale_host[1]) : make_double2(1.0, 0.0);
+    dim3 grid((maxL + 3) / 4, p.nsys);
+    k_lu_solve<<<grid, 128, 0, st>>>((const double2*)LU, piv, (const double2*)H, (const double2*)scale_dev, hs,
+                                     (double2*)Xs, info, p);
     BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
 }

@@ -29,6 +29,7 @@ struct DArgs {
     const typename Prec<P>::clov* __restrict__ C;
     int L[4], st[4];
     int V, col0, ncol, residual, SX;
+    int groups_fast;  // 1: blockIdx.x = column-group block, blockIdx.y = site block
     double kappa[BK_MAX_COLS];
 };
 
@@ -232,8 +233,12 @@ template <int P, int RPT>
 __global__ void __launch_bounds__(dslash_max_threads<P, RPT>()) k_dslash(const __grid_constant__ DArgs<P> a) {
     using R = typename Prec<P>::real;
     const int tid = threadIdx.x;
-    const int s = blockIdx.x * a.SX + (tid % a.SX);
-    const int g = blockIdx.y * (blockDim.x / a.SX) + tid / a.SX;
+    // Column-group blocks of one site block are adjacent in launch order, so
+    // the links and clover they all read are served from L2.
+    const int sblk = a.groups_fast ? blockIdx.y : blockIdx.x;
+    const int gblk = a.groups_fast ? blockIdx.x : blockIdx.y;
+    const int s = sblk * a.SX + (tid % a.SX);
+    const int g = gblk * (blockDim.x / a.SX) + tid / a.SX;
     const int cl0 = g * RPT;
     if (s >= a.V || cl0 >= a.ncol) return;
     const int nr = min(RPT, a.ncol - cl0);
@@ -350,7 +355,9 @@ bk_status dslash_impl(const DslashOp& op, cudaStream_t st) {
     }
     if (SX * BY > maxt) BY = maxt / SX;
     a.SX = SX;
-    dim3 grid((op.V + SX - 1) / SX, (ngroups + BY - 1) / BY);
+    const int nsb = (op.V + SX - 1) / SX, ngb = (ngroups + BY - 1) / BY;
+    a.groups_fast = nsb <= 65535 ? 1 : 0;
+    dim3 grid = a.groups_fast ? dim3(ngb, nsb) : dim3(nsb, ngb);
     if constexpr (P == BK_FP64) {
         k_dslash<P, 1><<<grid, SX * BY, 0, st>>>(a);
     } else {

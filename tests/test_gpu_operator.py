@@ -32,7 +32,7 @@ def _rel(a, b):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
 @pytest.mark.parametrize("dims,L", [((4, 4, 4, 4), 12), ((2, 4, 2, 6), 5), ((3, 5, 4, 6), 1),
-                                    ((8, 8, 8, 16), 12), ((6, 4, 4, 4), 17)])
+                                    ((8, 8, 8, 16), 12), ((6, 4, 4, 4), 17), ((4, 4, 8, 8), 48)])
 def test_dslash_matches_oracle(prec, dims, L):
     lat, U = _lat(dims, 0.5, 100 + L)
     X = synth.gaussian_sources(dims, L, 7)
@@ -85,7 +85,7 @@ def test_dslash_dev_layout_single_launch():
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 1e-5), ("fp16", 2e-3)])
-@pytest.mark.parametrize("L", [1, 6, 12, 13])
+@pytest.mark.parametrize("L", [1, 6, 12, 13, 48, 50])
 def test_gram_matches_numpy(prec, tol, L):
     dims = (4, 4, 4, 8)
     lat, _ = _lat(dims, 0.3, 1)
@@ -117,7 +117,7 @@ def test_xmy_matches_numpy(prec, tol):
     assert _rel(Y, ref) < tol
 
 
-@pytest.mark.parametrize("L", [1, 3, 12, 48, 60])
+@pytest.mark.parametrize("L", [1, 3, 12, 48, 60, 96, 100, 128])
 def test_small_solve_matches_numpy(L):
     import paper_0903_4936_gb300 as bk
     rng = np.random.default_rng(L)
