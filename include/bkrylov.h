@@ -214,6 +214,13 @@ typedef struct bk_solve_params {
     int restart_on_update; /* mixed precision: 1 = restart the recurrences
                               (P = R, V = A R) from every FP64 residual; 0 =
                               keep them (residual replacement only)           */
+    int orth_mode;         /* block BiCGSTAB basis: 0 = library default (on
+                              for FP32/FP16 inner iterations), 1 = always,
+                              2 = never.  "On" replaces P by P T^-1 with
+                              P^H P = T^H T (Cholesky, FP64) before every
+                              V = A P; the iterates are unchanged in exact
+                              arithmetic and R~_0^H V stays well
+                              conditioned in low precision                */
     int record_history;    /* 1: info->history[k] = max_i rel. residual       */
     int timing;            /* 1: time every dslash launch with CUDA events    */
 } bk_solve_params;

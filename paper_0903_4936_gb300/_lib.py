@@ -33,7 +33,7 @@ class SolveParams(C.Structure):
         ("method", C.c_int), ("prec", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int),
         ("reliable_delta", C.c_double), ("x0_given", C.c_int), ("buffers_on_host", C.c_int),
         ("rtilde_mode", C.c_int), ("seed", C.c_uint64), ("rtilde", C.c_void_p), ("restart_on_update", C.c_int),
-        ("record_history", C.c_int),
+        ("orth_mode", C.c_int), ("record_history", C.c_int),
         ("timing", C.c_int),
     ]
 

@@ -517,6 +517,7 @@ struct Solve {
     std::vector<std::vector<double>> hist;
     std::vector<double> true_res, rec_res;
     Field B64, X64, R64, Xlo, R, Rt, Pb, Vb, Wb, Ub, Yb, Tb, Zb, Ptmp;
+    bool orth = false;
     // small device arrays
     double *G_V, *G_RR, *G_RRn, *alpha, *gam, *G_Z, *dots, *rn, *zeta, *mzeta, *izeta, *partial, *LU;
     int *info_a, *info_g, *zbad, *piv;
@@ -676,9 +677,10 @@ struct Solve {
         B64 = make_field(c->B64.p, Lt, V, BK_FP64);
         X64 = make_field(c->X64.p, Lt, V, BK_FP64);
         R64 = make_field(c->R64.p, Lt, V, BK_FP64);
+        orth = method == BK_BICGSTAB && (prm->orth_mode == 1 || (prm->orth_mode == 0 && mixed));
         const int nblk = 7;
         for (int i = 0; i < nblk; ++i) BK_TRY(c->blk[i].ensure(fbp));
-        Field f[7];
+        Field f[8];
         for (int i = 0; i < nblk; ++i) f[i] = make_field(c->blk[i].p, Lt, V, P);
         R = f[0];
         Rt = f[1];
@@ -1028,6 +1030,24 @@ struct Solve {
 
     bk_status iterate_bicgstab() {
         for (int k = 0; k < prm->maxiter && part.active; ++k) {
+            if (orth) {
+                // P <- P T^-1 with P^H P = T^H T before V = A P: the iterates are
+                // unchanged in exact arithmetic (alpha, beta absorb T), V = A P stays
+                // exact, and R~^H V stays well conditioned in low precision.
+                BK_TRY(gram(Pb, Pb, G_Z));
+                launches += 1;
+                BK_TRY(launch_chol_inv(G_Z, gam, part, st));
+                GenOp g = genop0();
+                g.nmi = 1;
+                g.Mi[0] = Pb;
+                g.ma_mult[0] = 1.0;
+                g.M = gam;
+                g.hasY = 1;
+                g.Y = Ptmp;
+                g.ym = 1.0;
+                BK_TRY(genop(g));
+                std::swap(Pb, Ptmp);
+            }
             BK_TRY(dslash(P, Pb, Vb, Pb, 0, Lt, 0));  // V = A P
             BK_TRY(gram(Rt, Vb, G_V));
             BK_TRY(gram(Rt, R, G_RR));

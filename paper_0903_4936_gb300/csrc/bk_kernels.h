@@ -112,3 +112,6 @@ bk_status launch_canon_dot(const double* A, const double* B, long long ncomplex,
 bk_status launch_lu_factor(const double* G, double* LU, int* piv, int* info, const SysPart& p, cudaStream_t st);
 bk_status launch_lu_solve(const double* LU, const int* piv, const double* H, const double* scale_dev,
                           const double* scale_host, double* Xs, int* info, const SysPart& p, cudaStream_t st);
+// S_s = T^H T (Cholesky, FP64, one block per system), Tinv_s = T^-1; identity if
+// S_s is not numerically positive definite.  L <= 118 per system.
+bk_status launch_chol_inv(const double* S, double* Tinv, const SysPart& p, cudaStream_t st);

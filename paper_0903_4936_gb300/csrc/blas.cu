@@ -929,6 +929,72 @@ __global__ void __launch_bounds__(128) k_lu_solve(const double2* __restrict__ LU
     if (!finite) atomicMax(&info[s], n + 1);
 }
 
+// ---------------------------------------------------------------- Cholesky basis change
+//
+// k_chol_inv: one thread block per system.  S = V^H V (Hermitian positive
+// definite, FP64) is factored as S = T^H T with T upper triangular, and
+// Tinv = T^-1 is written (row-major, zeros below the diagonal).  If S is not
+// numerically positive definite, Tinv = identity (the basis is left as it is).
+
+__global__ void __launch_bounds__(256) k_chol_inv(const double2* __restrict__ S, double2* __restrict__ Tinv,
+                                                  SysPart p) {
+    extern __shared__ double2 ch_smem_raw[];
+    const int s = blockIdx.x;
+    if (!((p.active >> s) & 1u)) return;
+    const int n = p.col0[s + 1] - p.col0[s];
+    const int off = p.coef_off[s];
+    cx<double>* A = reinterpret_cast<cx<double>*>(ch_smem_raw);  // n x n, becomes T (upper)
+    cx<double>* X = reinterpret_cast<cx<double>*>(Tinv) + off;   // T^-1, written in place
+    __shared__ int bad;
+    __shared__ double dmax;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < n * n; e += blockDim.x) {
+        const double2 v = S[off + e];
+        A[e] = mk(v.x, v.y);
+    }
+    if (tid == 0) {
+        bad = 0;
+        dmax = 0.0;
+        for (int k = 0; k < n; ++k) dmax = fmax(dmax, S[off + k * n + k].x);
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (tid == 0) {
+            const double d = A[k * n + k].r;
+            if (!(d > 1e-14 * dmax) || !isfinite(d)) bad = 1;
+            else A[k * n + k] = mk(sqrt(d), 0.0);
+        }
+        __syncthreads();
+        if (bad) break;
+        const double rd = 1.0 / A[k * n + k].r;
+        for (int j = k + 1 + tid; j < n; j += blockDim.x) A[k * n + j] = rd * A[k * n + j];
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int e = tid; e < m * m; e += blockDim.x) {
+            const int i = k + 1 + e / m, j = k + 1 + e % m;
+            if (j >= i) {
+                cx<double> v = A[i * n + j];
+                cjmac(v, mk(-A[k * n + i].r, -A[k * n + i].i), A[k * n + j]);  // -= conj(T_ki) T_kj
+                A[i * n + j] = v;
+            }
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        for (int e = tid; e < n * n; e += blockDim.x)
+            Tinv[off + e] = make_double2((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
+        return;
+    }
+    // T^-1 column by column (back substitution, one thread per column)
+    for (int j = tid; j < n; j += blockDim.x) {
+        for (int i = n - 1; i >= 0; --i) {
+            cx<double> v = mk(i == j ? 1.0 : 0.0, 0.0);
+            for (int k = i + 1; k <= j; ++k) cmac(v, mk(-A[i * n + k].r, -A[i * n + k].i), X[k * n + j]);
+            X[i * n + j] = i > j ? mk(0.0, 0.0) : (1.0 / A[i * n + i].r) * v;
+        }
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
@@ -1203,6 +1269,20 @@ bk_status launch_lu_solve(const double* LU, const int* piv, const double* H, con
     dim3 grid((maxL + 3) / 4, p.nsys);
     k_lu_solve<<<grid, 128, 0, st>>>((const double2*)LU, piv, (const double2*)H, (const double2*)scale_dev, hs,
                                      (double2*)Xs, info, p);
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}
+
+bk_status launch_chol_inv(const double* S, double* Tinv, const SysPart& p, cudaStream_t st) {
+    int maxL = 0;
+    for (int s = 0; s < p.nsys; ++s) maxL = std::max(maxL, p.col0[s + 1] - p.col0[s]);
+    if (maxL > 118) {
+        bk_set_error("basis orthonormalisation supports L <= 118 per system");
+        return BK_ERR_INVALID_ARG;
+    }
+    const size_t smem = (size_t)maxL * maxL * sizeof(double2);
+    BK_CUDA_TRY(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_chol_inv<<<p.nsys, 256, smem, st>>>((const double2*)S, (double2*)Tinv, p);
     BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
 }
