@@ -248,6 +248,8 @@ typedef struct bk_solve_info {
     int n_dslash_inner;    /* dslash launches in the inner precision          */
     double time_dslash_inner_ms; /* event time of those (timing = 1)          */
     long long n_launches;  /* kernels launched by the call                    */
+    long long cols_dslash_inner; /* columns summed over the inner-precision
+                                    dslash launches (converged systems drop out) */
 } bk_solve_info;
 
 /* Solve D_W X = B (Eq. (linear_mrhs)) for L right-hand sides with one kappa

@@ -47,6 +47,7 @@ class SolveInfo(C.Structure):
         ("history_len", C.c_int), ("time_total_ms", C.c_double), ("time_dslash_ms", C.c_double),
         ("n_dslash", C.c_int), ("n_dslash_inner", C.c_int), ("time_dslash_inner_ms", C.c_double),
         ("n_launches", C.c_longlong),
+        ("cols_dslash_inner", C.c_longlong),
     ]
 
 

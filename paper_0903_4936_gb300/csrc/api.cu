@@ -490,10 +490,19 @@ __global__ void k_random(Field f, int V, uint64_t seed) {
     for (int k = 0; k < 12; ++k) {
         const uint64_t idx = (((uint64_t)c * V + site) * 12 + k);
         const uint64_t a = splitmix64(seed ^ (2 * idx)), b = splitmix64(seed ^ (2 * idx + 1));
-        const double u1 = ((a >> 11) + 1) * (1.0 / 9007199254740993.0);
-        const double u2 = (b >> 11) * (1.0 / 9007199254740992.0);
-        const double r = sqrt(-log(u1));  // |z| of a complex Gaussian with E|z|^2 = 1
-        v[k] = mk((R)(r * cospi(2 * u2)), (R)(r * sinpi(2 * u2)));
+        if (P == BK_FP64) {
+            const double u1 = ((a >> 11) + 1) * (1.0 / 9007199254740993.0);
+            const double u2 = (b >> 11) * (1.0 / 9007199254740992.0);
+            const double r = sqrt(-log(u1));  // |z| of a complex Gaussian with E|z|^2 = 1
+            v[k] = mk((R)(r * cospi(2 * u2)), (R)(r * sinpi(2 * u2)));
+        } else {  // a low-precision shadow block needs no FP64 transcendentals
+            const float u1 = (float)((a >> 40) + 1) * (1.0f / 16777217.0f);
+            const float u2 = (float)(b >> 40) * (1.0f / 16777216.0f);
+            const float r = sqrtf(-logf(u1));
+            float sn, cs;
+            sincospif(2.0f * u2, &sn, &cs);
+            v[k] = mk((R)(r * cs), (R)(r * sn));
+        }
     }
     store_spinor<P>(f, c, site, v);
 }
@@ -530,6 +539,7 @@ struct Solve {
     // counters
     long long launches = 0;
     int n_dslash = 0, n_dslash_inner = 0;
+    long long cols_inner = 0;
     double t_dslash = 0, t_dslash_inner = 0;
     std::vector<std::pair<int, bool>> ev_pending;  // (event index, inner)
     int ev_used = 0;
@@ -572,7 +582,33 @@ struct Solve {
         }
         launches += (ncol + BK_MAX_COLS - 1) / BK_MAX_COLS;
         n_dslash++;
-        if (prec == P) n_dslash_inner++;
+        if (prec == P) {
+            n_dslash_inner++;
+            cols_inner += ncol;
+        }
+        return BK_OK;
+    }
+
+    // Column ranges [c0, c0 + n) covered by maximal runs of consecutive
+    // systems whose bit is set in mask (systems own consecutive columns).
+    std::vector<std::pair<int, int>> col_runs(unsigned mask) const {
+        std::vector<std::pair<int, int>> r;
+        for (int s = 0; s < nsys;) {
+            if (!((mask >> s) & 1u)) {
+                ++s;
+                continue;
+            }
+            int e = s;
+            while (e + 1 < nsys && ((mask >> (e + 1)) & 1u)) ++e;
+            r.push_back({part.col0[s], part.col0[e + 1] - part.col0[s]});
+            s = e + 1;
+        }
+        return r;
+    }
+
+    // y = D x over the columns of the systems still iterating only
+    bk_status dslash_active(Field x, Field y, Field b) {
+        for (const auto& cr : col_runs(part.active)) BK_TRY(dslash(P, x, y, b, cr.first, cr.second, 0));
         return BK_OK;
     }
 
@@ -580,9 +616,22 @@ struct Solve {
         launches += 2;
         return launch_gram(P, A, B, part, G, partial, V, st);
     }
-    bk_status coldot(int prec, int npair, const Field* A, const Field* B, double* out) {
+    bk_status coldot(int prec, int npair, const Field* A, const Field* B, double* out, int ncol = -1) {
         launches += 2;
-        return launch_coldot(prec, npair, A, B, Lt, out, partial, V, st);
+        return launch_coldot(prec, npair, A, B, ncol < 0 ? Lt : ncol, out, partial, V, st);
+    }
+    // pairs of column dots over the active systems' columns: out[k * Lt + j]
+    bk_status coldot_active(int npair, const Field* A, const Field* B, double* out) {
+        for (const auto& cr : col_runs(part.active)) {
+            Field a[2], b[2];
+            for (int k = 0; k < npair; ++k) {
+                a[k] = field_cols(A[k], cr.first);
+                b[k] = field_cols(B[k], cr.first);
+            }
+            launches += 2;
+            BK_TRY(launch_coldot(P, npair, a, b, cr.second, out + 2 * (size_t)cr.first, partial, V, st, Lt));
+        }
+        return BK_OK;
     }
     // L x L solves in two steps: factor G once, substitute for each right-hand side
     bk_status factor(const double* G, int* info) {
@@ -625,9 +674,17 @@ struct Solve {
 
     // squared FP64 column norms of R (inner precision) into rn; then readback
     bk_status residual_norms() {
-        Field a[1] = {R}, b[1] = {R};
-        BK_TRY(coldot(P, 1, a, b, rn));
+        BK_TRY(norms_runs(P, R, part.active));
         return readback();
+    }
+
+    // squared FP64 norms of the columns of f owned by the systems in mask, into rn
+    bk_status norms_runs(int prec, Field f, unsigned mask) {
+        for (const auto& cr : col_runs(mask)) {
+            Field a[1] = {field_cols(f, cr.first)};
+            BK_TRY(coldot(prec, 1, a, a, rn + 2 * (size_t)cr.first, cr.second));
+        }
+        return BK_OK;
     }
 
     double rel(int j) const { return std::sqrt(std::max(rn_h[2 * j], 0.0)) / bnorm[j]; }
@@ -644,8 +701,14 @@ struct Solve {
     // FP64 residual replacement for system s: X64 += Xlo, R64 = B - A X64, R = R64.
     // Leaves the FP64 residual norms of s in rn_h after a readback.
     bk_status reliable_update(const std::vector<int>& sys) {
+        unsigned mask = 0;
         for (int s : sys) {
-            const int c0 = part.col0[s], n = part.col0[s + 1] - c0;
+            mask |= 1u << s;
+            mv64[s]++;
+            nrel[s]++;
+        }
+        for (const auto& cr : col_runs(mask)) {
+            const int c0 = cr.first, n = cr.second;
             if (mixed) {
                 dim3 grid((V + 127) / 128, n);
                 k_accum<<<grid, 128, 0, st>>>(field_cols(X64, c0), field_cols(Xlo, c0), V);
@@ -653,7 +716,6 @@ struct Solve {
                 launches++;
             }
             BK_TRY(dslash(BK_FP64, X64, R64, B64, c0, n, 1));
-            mv64[s]++;
             if (P != BK_FP64) {
                 BK_TRY(launch_cast(BK_FP64, field_cols(R64, c0), P, field_cols(R, c0), n, st));
             } else {
@@ -662,10 +724,8 @@ struct Solve {
                                             (size_t)n * R.cstride * 16, cudaMemcpyDeviceToDevice, st));
             }
             launches++;
-            nrel[s]++;
         }
-        Field a[1] = {R64}, b[1] = {R64};
-        BK_TRY(coldot(BK_FP64, 1, a, b, rn));
+        BK_TRY(norms_runs(BK_FP64, R64, mask));
         return readback();
     }
 
@@ -937,7 +997,7 @@ struct Solve {
             {   // G_V = R~^H V; traces Tr(W^H R), Tr(W^H W)
                 BK_TRY(gram(Rt, Vb, G_V));
                 Field a[2] = {Wb, Wb}, b[2] = {R, Wb};
-                BK_TRY(coldot(P, 2, a, b, dots));
+                BK_TRY(coldot_active(2, a, b, dots));
                 BK_TRY(scalars());
             }
             // alpha: (R~^H V) alpha = R~^H R
@@ -965,7 +1025,7 @@ struct Solve {
                 g.skip = info_a;
                 BK_TRY(genop(g));
             }
-            BK_TRY(dslash(P, Ub, Yb, Ub, 0, Lt, 0));  // Y = A U
+            BK_TRY(dslash_active(Ub, Yb, Ub));  // Y = A U
             {   // R <- R - zeta W - Y
                 GenOp g = genop0();
                 g.ne = 3;
@@ -987,7 +1047,7 @@ struct Solve {
             part.active &= before;
             if (!part.active) break;
             BK_TRY(gram(Rt, R, G_RRn));          // R~^H R_{k+1}
-            BK_TRY(dslash(P, R, Wb, R, 0, Lt, 0));  // W = A R
+            BK_TRY(dslash_active(R, Wb, R));  // W = A R
             // gamma: (R~^H R_k) gamma = R~^H R_{k+1} / zeta
             BK_TRY(factor(G_RR, info_g));
             BK_TRY(substitute(G_RRn, izeta, nullptr, gam, info_g));
@@ -1019,7 +1079,7 @@ struct Solve {
                 // equals W + Y gamma in exact arithmetic; the recursion drifts
                 // from A P under FP32 rounding and the L x L systems built on V
                 // then lose the iteration.
-                BK_TRY(dslash(P, Pb, Vb, Pb, 0, Lt, 0));
+                BK_TRY(dslash_active(Pb, Vb, Pb));
                 for (int s = 0; s < nsys; ++s)
                     if ((part.active >> s) & 1u) mv[s]++;
             }
@@ -1048,7 +1108,7 @@ struct Solve {
                 BK_TRY(genop(g));
                 std::swap(Pb, Ptmp);
             }
-            BK_TRY(dslash(P, Pb, Vb, Pb, 0, Lt, 0));  // V = A P
+            BK_TRY(dslash_active(Pb, Vb, Pb));  // V = A P
             BK_TRY(gram(Rt, Vb, G_V));
             BK_TRY(gram(Rt, R, G_RR));
             BK_TRY(factor(G_V, info_a));  // R~^H V, used for alpha and beta
@@ -1068,10 +1128,10 @@ struct Solve {
                 g.skip = info_a;
                 BK_TRY(genop(g));
             }
-            BK_TRY(dslash(P, Tb, Zb, Tb, 0, Lt, 0));  // Z = A T
+            BK_TRY(dslash_active(Tb, Zb, Tb));  // Z = A T
             {
                 Field a[2] = {Zb, Zb}, b[2] = {Tb, Zb};
-                BK_TRY(coldot(P, 2, a, b, dots));  // Tr(Z^H T), Tr(Z^H Z)
+                BK_TRY(coldot_active(2, a, b, dots));  // Tr(Z^H T), Tr(Z^H Z)
                 BK_TRY(scalars());
                 BK_TRY(gram(Rt, Zb, G_Z));
             }
@@ -1265,6 +1325,7 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
         in.n_dslash = S.n_dslash;
         in.n_dslash_inner = S.n_dslash_inner;
         in.n_launches = S.launches;
+        in.cols_dslash_inner = S.cols_inner;
         if (S.done[s] == 2 && result == BK_OK) result = BK_ERR_BREAKDOWN;
         if (S.done[s] == 0 && result == BK_OK) result = BK_ERR_NOT_CONVERGED;
     }

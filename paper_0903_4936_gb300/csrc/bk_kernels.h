@@ -54,10 +54,11 @@ size_t gram_partial_bytes(const SysPart& p, int V);
 bk_status launch_gram(int prec, Field A, Field B, const SysPart& p, double* G, double* partial, int V,
                       cudaStream_t st);
 
-// Column dot products: out[k * L + j] = (A_k)_j^H (B_k)_j for pairs k < npair.
+// Column dot products: out[k * ldo + j] = (A_k)_j^H (B_k)_j for pairs k < npair
+// (ldo = L when not given).
 size_t coldot_partial_bytes(int L, int npair, int V);
 bk_status launch_coldot(int prec, int npair, const Field* A, const Field* B, int L, double* out,
-                        double* partial, int V, cudaStream_t st);
+                        double* partial, int V, cudaStream_t st, int ldo = 0);
 
 // Y_j = Z_j + c_s * sum_{i in s} X_i M_s[i][j]  (Z may be null; c per system, complex FP64)
 bk_status launch_xmy(int prec, Field X, const double* M, const double* c_dev, Field Z, bool hasZ, Field Y,

@@ -275,7 +275,9 @@ __global__ void __launch_bounds__(DOT_THREADS) k_coldot(DotArgs d, double2* __re
     }
 }
 
-__global__ void k_coldot_finish(const double2* __restrict__ partial, int n, int nbx, double2* __restrict__ out) {
+// out[k * ldo + j] for pair k, column j < L (entry e = k * L + j of the partial sums)
+__global__ void k_coldot_finish(const double2* __restrict__ partial, int n, int nbx, double2* __restrict__ out,
+                                int L, int ldo) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     double2 v = make_double2(0.0, 0.0);
@@ -283,7 +285,7 @@ __global__ void k_coldot_finish(const double2* __restrict__ partial, int n, int 
         v.x += partial[(size_t)e * nbx + b].x;
         v.y += partial[(size_t)e * nbx + b].y;
     }
-    out[e] = v;
+    out[(size_t)(e / L) * ldo + e % L] = v;
 }
 
 int dot_nbx(int L, int V) {
@@ -441,6 +443,101 @@ __global__ void __launch_bounds__(128) k_genop(const __grid_constant__ GenOp g, 
                 x[k] = x[k] + mk((RX)tv.r, (RX)tv.i) + xm * mk((RX)mp[jj][k].r, (RX)mp[jj][k].i);
             }
             store_spinor<PX>(g.X, j, site, x);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- fused block update, small systems
+//
+// Same operation as k_genop for FP32 blocks whose systems all have L_s <= LS
+// (LS = 4, 6, 8 or 12).  The product with the L x L matrix acts on every
+// spinor component independently, so a thread takes one site and one 16-byte
+// chunk (two complex components) of every column of its system: lane = site
+// keeps each load a 512-byte row, the L_s x 2 outputs stay in registers, and
+// the system's matrix is read from shared memory as a broadcast.
+// Grid: (sites / 256, 6 chunks, systems).
+template <int LS>
+__global__ void __launch_bounds__(256) k_genop_chunk(const __grid_constant__ GenOp g, int V) {
+    const int s = blockIdx.z;
+    if (!((g.p.active >> s) & 1u)) return;
+    if (g.skip && g.skip[s] != 0) return;
+    __shared__ cx<float> Msm[LS * LS];
+    const int c0 = g.p.col0[s], Ls = g.p.col0[s + 1] - c0;
+    if (g.M) {
+        const double2* Ms = (const double2*)g.M + g.p.coef_off[s];
+        for (int e = threadIdx.x; e < Ls * Ls; e += blockDim.x) {
+            const double2 m = Ms[e];
+            Msm[e] = mk((float)m.x, (float)m.y);
+        }
+    }
+    __syncthreads();
+    const int site = blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= V) return;
+    const int ch = blockIdx.y;
+    auto coef = [&](const double* ptr, double mult) -> cx<float> {
+        if (!ptr) return mk((float)mult, 0.f);
+        const double2 v = ((const double2*)ptr)[s];
+        return mk((float)(mult * v.x), (float)(mult * v.y));
+    };
+    auto at = [&](const Field& f, int col) -> float4* {
+        return (float4*)f.data + (size_t)col * f.cstride + (size_t)ch * V + site;
+    };
+    cx<float> acc[LS][2];
+#pragma unroll
+    for (int j = 0; j < LS; ++j) acc[j][0] = acc[j][1] = mk(0.f, 0.f);
+    if (g.M) {
+        cx<float> mc[GENOP_MAXMI];
+#pragma unroll
+        for (int u = 0; u < GENOP_MAXMI; ++u) mc[u] = coef(g.ma[u], g.ma_mult[u]);
+#pragma unroll
+        for (int i = 0; i < LS; ++i) {
+            if (i < Ls) {
+                float4 q = __ldg(at(g.Mi[0], c0 + i));
+                cx<float> c[2] = {mc[0] * mk(q.x, q.y), mc[0] * mk(q.z, q.w)};
+                if (g.nmi > 1) {
+                    q = __ldg(at(g.Mi[1], c0 + i));
+                    cmac(c[0], mc[1], mk(q.x, q.y));
+                    cmac(c[1], mc[1], mk(q.z, q.w));
+                }
+#pragma unroll
+                for (int j = 0; j < LS; ++j) {
+                    if (j < Ls) {
+                        const cx<float> m = Msm[i * Ls + j];
+                        cmac(acc[j][0], c[0], m);
+                        cmac(acc[j][1], c[1], m);
+                    }
+                }
+            }
+        }
+    }
+    cx<float> ea[GENOP_MAXE];
+#pragma unroll
+    for (int t = 0; t < GENOP_MAXE; ++t) ea[t] = coef(g.ea[t], g.ea_mult[t]);
+    const cx<float> xa = coef(g.xa, g.xa_mult);
+    const float ym = (float)g.ym, xm = (float)g.xm;
+#pragma unroll
+    for (int j = 0; j < LS; ++j) {
+        if (j >= Ls) continue;
+        if (g.hasY) {
+            cx<float> y[2] = {ym * acc[j][0], ym * acc[j][1]};
+#pragma unroll
+            for (int t = 0; t < GENOP_MAXE; ++t) {
+                if (t < g.ne) {
+                    const float4 q = __ldg(at(g.E[t], c0 + j));
+                    cmac(y[0], ea[t], mk(q.x, q.y));
+                    cmac(y[1], ea[t], mk(q.z, q.w));
+                }
+            }
+            *at(g.Y, c0 + j) = make_float4(y[0].r, y[0].i, y[1].r, y[1].i);
+        }
+        if (g.hasX) {
+            float4* xp = at(g.X, c0 + j);
+            const float4 x = *xp;
+            const float4 v = __ldg(at(g.Xin, c0 + j));
+            cx<float> x0 = mk(x.x, x.y) + xm * acc[j][0], x1 = mk(x.z, x.w) + xm * acc[j][1];
+            cmac(x0, xa, mk(v.x, v.y));
+            cmac(x1, xa, mk(v.z, v.w));
+            *xp = make_float4(x0.r, x0.i, x1.r, x1.i);
         }
     }
 }
@@ -718,19 +815,6 @@ __global__ void __launch_bounds__(256) k_gram_tiled(Field A, Field B, SysPart p,
     }
 }
 
-__global__ void k_gram_tiled_finish(const double2* __restrict__ partial, int nentries, int nbx,
-                                    double2* __restrict__ G) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nentries) return;
-    double2 v = make_double2(0.0, 0.0);
-    for (int b = 0; b < nbx; ++b) {
-        const double2 w = partial[(size_t)b * nentries + e];
-        v.x += w.x;
-        v.y += w.y;
-    }
-    G[e] = v;
-}
-
 int gram_tiled_nbx(int nsys, int V) {
     const int tiles = (V + GG_TS - 1) / GG_TS;
     return std::max(1, std::min(tiles, (2 * 152 + nsys - 1) / nsys));
@@ -741,6 +825,190 @@ bool gram_tiled_ok(int prec, const SysPart& p) {
     for (int s = 0; s < p.nsys; ++s)
         if (p.col0[s + 1] - p.col0[s] > 16 * GG_T) return false;
     return true;
+}
+
+// ---------------------------------------------------------------- Gram, small systems
+//
+// G_s = A_s^H B_s for FP32 / FP16 blocks whose systems all have L_s <= 12.
+// A warp owns one T x T tile of G_s (T = 4 or 6, so G_s is one or four tiles)
+// and streams 32 consecutive sites per step, lane = site: every load is one
+// 512-byte row of a 16-byte chunk, and the warps of a block that need the same
+// column of the same sites meet it in L1.  Products accumulate in FP32 per
+// lane over GS_FLUSH sites, are then summed across the warp by butterfly
+// shuffles, and each lane keeps its share of the 2 T^2 sums in FP64; site
+// groups and thread blocks are combined in FP64.  Systems that have left the
+// iteration (bit clear in p.active) are skipped.
+constexpr int GS_THREADS = 256;
+constexpr int GS_FLUSH = 8;
+constexpr int GS_TARGET_BLOCKS = 2 * 152;
+
+template <int P>
+struct RawChunk;
+template <>
+struct RawChunk<BK_FP32> {
+    typedef float4 T;
+    __device__ static float4 ld(const Field& f, int c, int s, int k) {
+        return __ldg((const float4*)f.data + (size_t)c * f.cstride + (size_t)k * f.V + s);
+    }
+    __device__ static cx<float> get(const float4& q, int m) { return m == 0 ? mk(q.x, q.y) : mk(q.z, q.w); }
+    __device__ static float scale(const Field&, int, int) { return 1.f; }
+};
+template <>
+struct RawChunk<BK_FP16> {
+    typedef uint4 T;
+    __device__ static uint4 ld(const Field& f, int c, int s, int k) {
+        return __ldg((const uint4*)f.data + (size_t)c * f.cstride + (size_t)k * f.V + s);
+    }
+    __device__ static cx<float> get(const uint4& q, int m) {
+        const uint32_t w = m == 0 ? q.x : (m == 1 ? q.y : (m == 2 ? q.z : q.w));
+        const float2 g = __half22float2(*reinterpret_cast<const __half2*>(&w));
+        return mk(g.x, g.y);
+    }
+    __device__ static float scale(const Field& f, int c, int s) { return __ldg(f.norm + (size_t)c * f.V + s); }
+};
+
+template <int P, int T>
+__global__ void __launch_bounds__(GS_THREADS) k_gram_small(Field A, Field B, SysPart p,
+                                                           double2* __restrict__ partial, int V) {
+    using RC = RawChunk<P>;
+    constexpr int nch = Prec<P>::nchunk, cpc = Chunk<P>::cpc;
+    constexpr int NV = 2 * T * T;        // real sums of one tile
+    constexpr int NS = (NV + 31) / 32;   // FP64 shares per lane
+    constexpr int NW = GS_THREADS / 32;
+    __shared__ double red[NW][NS * 32];
+    const int s = blockIdx.y;
+    if (!((p.active >> s) & 1u)) return;
+    const int c0 = p.col0[s], Ls = p.col0[s + 1] - c0;
+    const int nt = (Ls + T - 1) / T, ntiles = nt * nt;  // 1 or 4
+    const int G = NW / ntiles;                          // site groups per block
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = warp % ntiles, grp = warp / ntiles;
+    const int ti = tile / nt, tj = tile % nt;
+    int ca[T], cb[T];
+#pragma unroll
+    for (int x = 0; x < T; ++x) {
+        ca[x] = c0 + min(ti * T + x, Ls - 1);  // clamped: rows / columns past L_s are discarded
+        cb[x] = c0 + min(tj * T + x, Ls - 1);
+    }
+    float acc[NV];
+    double sh[NS];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = 0.f;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) sh[q] = 0.0;
+    auto flush = [&]() {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            float v = acc[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((q & 31) == lane) sh[q >> 5] += (double)v;
+            acc[q] = 0.f;
+        }
+    };
+    const int stride = gridDim.x * G * 32;
+    int since = 0;
+    for (int base = (blockIdx.x * G + grp) * 32; base < V; base += stride) {
+        const int site = base + lane;
+        if (site < V) {
+            float sa[T], sb[T];
+#pragma unroll
+            for (int x = 0; x < T; ++x) {
+                sa[x] = RC::scale(A, ca[x], site);
+                sb[x] = RC::scale(B, cb[x], site);
+            }
+#pragma unroll
+            for (int ch = 0; ch < nch; ++ch) {
+                typename RC::T ra[T], rb[T];
+#pragma unroll
+                for (int x = 0; x < T; ++x) {
+                    ra[x] = RC::ld(A, ca[x], site, ch);
+                    rb[x] = RC::ld(B, cb[x], site, ch);
+                }
+#pragma unroll
+                for (int m = 0; m < cpc; ++m) {
+                    cx<float> a[T], b[T];
+#pragma unroll
+                    for (int x = 0; x < T; ++x) {
+                        a[x] = sa[x] * RC::get(ra[x], m);
+                        b[x] = sb[x] * RC::get(rb[x], m);
+                    }
+#pragma unroll
+                    for (int x = 0; x < T; ++x)
+#pragma unroll
+                        for (int y = 0; y < T; ++y) {
+                            float& re = acc[2 * (x * T + y)];
+                            float& im = acc[2 * (x * T + y) + 1];
+                            re = fmaf(a[x].r, b[y].r, re);
+                            re = fmaf(a[x].i, b[y].i, re);
+                            im = fmaf(a[x].r, b[y].i, im);
+                            im = fmaf(-a[x].i, b[y].r, im);
+                        }
+                }
+            }
+        }
+        if (++since == GS_FLUSH) {  // warp-uniform
+            since = 0;
+            flush();
+        }
+    }
+    flush();
+#pragma unroll
+    for (int q = 0; q < NS; ++q) red[warp][q * 32 + lane] = sh[q];
+    __syncthreads();
+    const int off = p.coef_off[s];
+    for (int e = threadIdx.x; e < ntiles * T * T; e += blockDim.x) {
+        const int tl = e / (T * T), xy = e % (T * T);
+        const int i = (tl / nt) * T + xy / T, j = (tl % nt) * T + xy % T;
+        double2 v = make_double2(0.0, 0.0);
+        for (int g = 0; g < G; ++g) {
+            v.x += red[g * ntiles + tl][2 * xy];
+            v.y += red[g * ntiles + tl][2 * xy + 1];
+        }
+        if (i < Ls && j < Ls) partial[(size_t)blockIdx.x * p.coef_off[p.nsys] + off + i * Ls + j] = v;
+    }
+}
+
+// G[e] = sum over blocks b of partial[b * ne + e]: one warp per entry, lanes
+// stride over the blocks, FP64 throughout (fixed order, so reproducible).
+__global__ void k_gram_finish_warp(const double2* __restrict__ partial, int ne, int nbx,
+                                   double2* __restrict__ G) {
+    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= ne) return;
+    double2 v = make_double2(0.0, 0.0);
+    for (int b = lane; b < nbx; b += 32) {
+        const double2 w = partial[(size_t)b * ne + e];
+        v.x += w.x;
+        v.y += w.y;
+    }
+    v = warp_sum(v);
+    if (lane == 0) G[e] = v;
+}
+
+// Tile side of k_gram_small for this partition, 0 if it does not apply.
+static int gram_small_T(int prec, const SysPart& p) {
+    if (prec == BK_FP64) return 0;
+    int maxL = 0;
+    for (int s = 0; s < p.nsys; ++s) maxL = std::max(maxL, p.col0[s + 1] - p.col0[s]);
+    if (maxL <= 4) return 4;
+    if (maxL <= 6) return 6;
+    if (maxL <= 8) return 4;
+    if (maxL <= 12) return 6;
+    return 0;
+}
+
+static int gram_small_nbx(const SysPart& p, int V, int T, int nthreads) {
+    int na = 0, maxtiles = 1;
+    for (int s = 0; s < p.nsys; ++s) {
+        if ((p.active >> s) & 1u) ++na;
+        const int nt = (p.col0[s + 1] - p.col0[s] + T - 1) / T;
+        maxtiles = std::max(maxtiles, nt * nt);
+    }
+    const int G = (nthreads / 32) / maxtiles;
+    const int groups = (V + 31) / 32;
+    const int cap = std::max(1, (groups + G - 1) / G);
+    return std::max(1, std::min(cap, (GS_TARGET_BLOCKS + std::max(na, 1) - 1) / std::max(na, 1)));
 }
 
 // ---------------------------------------------------------------- L x L solves: factor, then substitute
@@ -1005,11 +1273,30 @@ size_t gram_partial_bytes(const SysPart& p, int V) {
     const int nbx = gram_nbx(ntiles, V);
     size_t b = (size_t)ntiles * GT * GT * nbx * sizeof(double2);
     const size_t bt = (size_t)gram_tiled_nbx(p.nsys, V) * p.coef_off[p.nsys] * sizeof(double2);
-    return std::max(b, bt);
+    const size_t bs = (size_t)GS_TARGET_BLOCKS * p.coef_off[p.nsys] * sizeof(double2);
+    return std::max(std::max(b, bt), bs);
 }
 
 bk_status launch_gram(int prec, Field A, Field B, const SysPart& p, double* G, double* partial, int V,
                       cudaStream_t st) {
+    if (const int T = gram_small_T(prec, p)) {
+        if (!p.active) return BK_OK;
+        const int nbx = gram_small_nbx(p, V, T, GS_THREADS);
+        dim3 grid(nbx, p.nsys);
+        double2* part = (double2*)partial;
+        if (prec == BK_FP32) {
+            if (T == 4) k_gram_small<BK_FP32, 4><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
+            else k_gram_small<BK_FP32, 6><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
+        } else {
+            if (T == 4) k_gram_small<BK_FP16, 4><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
+            else k_gram_small<BK_FP16, 6><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
+        }
+        BK_CUDA_TRY(cudaGetLastError());
+        const int ne = p.coef_off[p.nsys];
+        k_gram_finish_warp<<<(ne + 7) / 8, 256, 0, st>>>(part, ne, nbx, (double2*)G);
+        BK_CUDA_TRY(cudaGetLastError());
+        return BK_OK;
+    }
     if (gram_tiled_ok(prec, p)) {
         int maxL = 0;
         for (int s = 0; s < p.nsys; ++s) maxL = std::max(maxL, p.col0[s + 1] - p.col0[s]);
@@ -1031,7 +1318,7 @@ bk_status launch_gram(int prec, Field A, Field B, const SysPart& p, double* G, d
         }
         BK_CUDA_TRY(cudaGetLastError());
         const int ne = p.coef_off[p.nsys];
-        k_gram_tiled_finish<<<(ne + 127) / 128, 128, 0, st>>>(part, ne, nbx, (double2*)G);
+        k_gram_finish_warp<<<(ne + 7) / 8, 256, 0, st>>>(part, ne, nbx, (double2*)G);
         BK_CUDA_TRY(cudaGetLastError());
         return BK_OK;
     }
@@ -1054,12 +1341,15 @@ bk_status launch_gram(int prec, Field A, Field B, const SysPart& p, double* G, d
     return BK_OK;
 }
 
+// Enough for any launch over at most L columns (the block count grows as L shrinks).
 size_t coldot_partial_bytes(int L, int npair, int V) {
-    return (size_t)L * npair * dot_nbx(L, V) * sizeof(double2);
+    size_t m = 0;
+    for (int l = 1; l <= L; ++l) m = std::max(m, (size_t)l * npair * dot_nbx(l, V));
+    return m * sizeof(double2);
 }
 
 bk_status launch_coldot(int prec, int npair, const Field* A, const Field* B, int L, double* out, double* partial,
-                        int V, cudaStream_t st) {
+                        int V, cudaStream_t st, int ldo) {
     if (L <= 0) return BK_OK;
     if (npair < 1 || npair > MAX_PAIRS) return BK_ERR_INVALID_ARG;
     DotArgs d;
@@ -1079,7 +1369,7 @@ bk_status launch_coldot(int prec, int npair, const Field* A, const Field* B, int
     }
     BK_CUDA_TRY(cudaGetLastError());
     const int n = npair * L;
-    k_coldot_finish<<<(n + 127) / 128, 128, 0, st>>>(part, n, nbx, (double2*)out);
+    k_coldot_finish<<<(n + 127) / 128, 128, 0, st>>>(part, n, nbx, (double2*)out, L, ldo > 0 ? ldo : L);
     BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
 }
@@ -1104,9 +1394,24 @@ bk_status launch_xmy(int prec, Field X, const double* M, const double* c_dev, Fi
 // Tiled path: FP32/FP16 blocks with a matrix and every system L <= 96.
 static bk_status launch_genop_tiled(int prec, const GenOp& g, int V, cudaStream_t st, bool& done) {
     done = false;
-    if (prec == BK_FP64 || !g.M) return BK_OK;
+    if (prec == BK_FP64) return BK_OK;
     int maxL = 0;
     for (int s = 0; s < g.p.nsys; ++s) maxL = std::max(maxL, g.p.col0[s + 1] - g.p.col0[s]);
+    if (prec == BK_FP32 && maxL <= 12) {
+        if (!g.p.active) {
+            done = true;
+            return BK_OK;
+        }
+        dim3 grid((V + 255) / 256, Prec<BK_FP32>::nchunk, g.p.nsys);
+        if (maxL <= 4) k_genop_chunk<4><<<grid, 256, 0, st>>>(g, V);
+        else if (maxL <= 6) k_genop_chunk<6><<<grid, 256, 0, st>>>(g, V);
+        else if (maxL <= 8) k_genop_chunk<8><<<grid, 256, 0, st>>>(g, V);
+        else k_genop_chunk<12><<<grid, 256, 0, st>>>(g, V);
+        BK_CUDA_TRY(cudaGetLastError());
+        done = true;
+        return BK_OK;
+    }
+    if (!g.M) return BK_OK;
     if (maxL > 96) return BK_OK;
     const int jm = (maxL + GT_TS - 1) / GT_TS;
     const size_t smem = (size_t)(((maxL * maxL + 1) & ~1) + GT_KC * GT_TS * GT_PAD) * sizeof(cx<float>);

@@ -85,7 +85,7 @@ def test_dslash_dev_layout_single_launch():
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 1e-5), ("fp16", 2e-3)])
-@pytest.mark.parametrize("L", [1, 6, 12, 13, 48, 50])
+@pytest.mark.parametrize("L", [1, 3, 6, 8, 12, 13, 48, 50])
 def test_gram_matches_numpy(prec, tol, L):
     dims = (4, 4, 4, 8)
     lat, _ = _lat(dims, 0.3, 1)

@@ -130,10 +130,14 @@ def test_fp16_inner_reports_its_true_residual(c1):
         assert tr <= 1e-10
 
 
-def test_batched_systems_match_individual(c1):
+@pytest.mark.parametrize("kappas,Ls", [([0.11, 0.12, 0.125], [2, 4, 3]),
+                                        ([0.11, 0.125, 0.12, 0.115], [6, 12, 5, 8]),
+                                        ([0.12] * 6, [1, 6, 6, 6, 6, 6])])
+def test_batched_systems_match_individual(c1, kappas, Ls):
+    """Systems of several sizes in one mixed-precision solve: the L x L
+    algebra's one-tile (L <= 6) and four-tile (L <= 12) register layouts, and
+    systems leaving the iteration at different steps."""
     dims, lat, U, B, Xd, A = c1
-    kappas = [0.11, 0.12, 0.125]
-    Ls = [2, 4, 3]
     Bs = synth.z4_noise(dims, sum(Ls), 77)
     X, infos = lat.block_solve_batched(torch.from_numpy(Bs).cuda(), kappas, Ls, method="bicgstab", prec="fp32",
                                        tol=1e-10, maxiter=1000)
