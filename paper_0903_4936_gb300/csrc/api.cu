@@ -525,6 +525,7 @@ struct Solve {
     std::vector<double> m_upd;
     std::vector<std::vector<double>> hist;
     std::vector<double> true_res, rec_res;
+    std::vector<char> res_known;     // per system: true_res already holds the final FP64 residual
     Field B64, X64, R64, Xlo, R, Rt, Pb, Vb, Wb, Ub, Yb, Tb, Zb, Ptmp;
     bool orth = false;
     // small device arrays
@@ -984,7 +985,13 @@ struct Solve {
                 rmax_since[s] = m;
                 m_upd[s] = m;
                 since[s] = 0;
-                if (m <= prm->tol) done[s] = 1;
+                if (m <= prm->tol) {
+                    // converged on an FP64 true residual of the final X (Xlo was
+                    // just folded in): finish() need not recompute it
+                    done[s] = 1;
+                    res_known[s] = 1;
+                    for (int j = part.col0[s]; j < part.col0[s + 1]; ++j) true_res[j] = rel(j);
+                }
                 else if (prm->restart_on_update) restart_now[s] = 1;
             }
         }
@@ -1195,22 +1202,31 @@ struct Solve {
 
     // Final FP64 true residual of every column and the solution in canonical layout.
     bk_status finish(double* Xc) {
+        // systems whose final FP64 true residual is not known yet: all but those
+        // that converged on an FP64 residual replacement (mixed precision)
+        unsigned need = 0;
+        for (int s = 0; s < nsys; ++s)
+            if (!res_known[s]) {
+                need |= 1u << s;
+                mv64[s]++;
+            }
         part.active = nsys >= 32 ? 0xffffffffu : ((1u << nsys) - 1u);
-        if (mixed) {
-            dim3 grid((V + 127) / 128, Lt);
-            k_accum<<<grid, 128, 0, st>>>(X64, Xlo, V);
-            BK_CUDA_TRY(cudaGetLastError());
-            launches++;
+        for (const auto& cr : col_runs(need)) {
+            if (mixed) {
+                dim3 grid((V + 127) / 128, cr.second);
+                k_accum<<<grid, 128, 0, st>>>(field_cols(X64, cr.first), field_cols(Xlo, cr.first), V);
+                BK_CUDA_TRY(cudaGetLastError());
+                launches++;
+            }
+            BK_TRY(dslash(BK_FP64, X64, R64, B64, cr.first, cr.second, 1));
         }
-        BK_TRY(dslash(BK_FP64, X64, R64, B64, 0, Lt, 1));
-        {
-            Field a[1] = {R64}, b[1] = {R64};
-            BK_TRY(coldot(BK_FP64, 1, a, b, rn));
-        }
+        BK_TRY(norms_runs(BK_FP64, R64, need));
         BK_TRY(launch_unpack(BK_FP64, X64, Xc, Lt, st));
         launches++;
         BK_TRY(readback());
-        for (int j = 0; j < Lt; ++j) true_res[j] = rel(j);
+        for (int s = 0; s < nsys; ++s)
+            if ((need >> s) & 1u)
+                for (int j = part.col0[s]; j < part.col0[s + 1]; ++j) true_res[j] = rel(j);
         return BK_OK;
     }
 };
@@ -1266,6 +1282,7 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
     S.m_upd.assign(nsys, 1.0);
     S.hist.resize(nsys);
     S.true_res.assign(Lt, 0.0);
+    S.res_known.assign(nsys, 0);
 
     const size_t canon_bytes = (size_t)Lt * c->V * 12 * sizeof(double2);
     const double* Bd = B;
@@ -1300,7 +1317,7 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
         in.iterations = S.iters[s];
         in.matvecs = S.mv[s];
         in.restarts = S.nrestart[s];
-        in.matvecs_fp64 = S.mv64[s] + 1;  // + final true residual
+        in.matvecs_fp64 = S.mv64[s];  // including the final true residual
         in.reliable_updates = S.nrel[s];
         in.breakdown = S.done[s] == 2;
         double tm = 0, rm = 0;
