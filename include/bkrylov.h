@@ -54,7 +54,11 @@ typedef enum bk_status {
 typedef enum bk_prec {
     BK_FP64 = 0, /* FP64 storage and arithmetic                               */
     BK_FP32 = 1, /* FP32 storage and arithmetic                               */
-    BK_FP16 = 2  /* FP16 storage (per site-column FP32 scale), FP32 arithmetic */
+    BK_FP16 = 2, /* FP16 storage (per site-column FP32 scale), FP32 arithmetic */
+    BK_DF64 = 3  /* FP64 storage (BK_FP64 layout), double-float arithmetic:
+                    every real is an unevaluated sum of two floats (about 46
+                    significand bits) on the FP32 pipes.  Operator calls only
+                    (bk_dslash, bk_dslash_dev)                               */
 } bk_prec;
 
 typedef enum bk_method {
@@ -223,12 +227,17 @@ typedef struct bk_solve_params {
                               conditioned in low precision                */
     int record_history;    /* 1: info->history[k] = max_i rel. residual       */
     int timing;            /* 1: time every dslash launch with CUDA events    */
+    int update_prec;       /* mixed precision: arithmetic of the residual
+                              replacements R = B - A X: 0 = FP64 (default),
+                              1 = double-float (BK_DF64).  The true residual
+                              that decides convergence is FP64 in both cases */
 } bk_solve_params;
 
 typedef struct bk_solve_info {
     int iterations;        /* completed loop bodies                           */
     int matvecs;           /* operator applications in the inner precision    */
-    int matvecs_fp64;      /* FP64 operator applications (residuals)          */
+    int matvecs_fp64;      /* FP64-class operator applications (residuals, in
+                              FP64 or double-float arithmetic)                */
     int reliable_updates;  /* FP64 residual replacements                      */
     int restarts;          /* mixed precision: low-precision cycles discarded
                               and restarted from the last FP64 residual

@@ -188,9 +188,12 @@ class Lattice:
 
     # ------------------------------------------------------------ solves
     def _params(self, method, prec, tol, maxiter, delta, x0_given, on_host, rtilde, seed, history, timing,
-                restart=False, orth=None):
+                restart=False, orth=None, update="fp64"):
         """rtilde: None -> seeded Gaussian R~_0 (library default), "r0" -> R~_0 = R_0,
-        tensor -> the caller's block (canonical layout, where B lives)."""
+        tensor -> the caller's block (canonical layout, where B lives).  update:
+        arithmetic of the mixed-precision residual replacements, "df64" or "fp64"."""
+        if update not in ("df64", "fp64"):
+            raise ValueError("update must be 'df64' or 'fp64'")
         mode, ptr = 0, None
         if isinstance(rtilde, str):
             if rtilde != "r0":
@@ -201,7 +204,7 @@ class Lattice:
         return SolveParams(METHOD[method] if isinstance(method, str) else int(method), _prec(prec), float(tol),
                            int(maxiter), float(delta), int(x0_given), int(on_host), mode, int(seed), ptr,
                            int(bool(restart)), 0 if orth is None else (1 if orth else 2), int(history),
-                           int(timing))
+                           int(timing), 1 if update == "df64" else 0)
 
     @staticmethod
     def _info_dict(info: SolveInfo, hist_buf, res_buf):
@@ -213,7 +216,7 @@ class Lattice:
     def block_solve(self, B: torch.Tensor, kappa: float, method="bicggr", prec="fp64", tol=1e-10, maxiter=2000,
                     X0: torch.Tensor | None = None, delta=0.0, rtilde=None, seed=0, history=False,
                     timing=False, out: torch.Tensor | None = None, raise_on_fail=True, restart=False,
-                    orth=None):
+                    orth=None, update="fp64"):
         """Solve D_W X = B (Eq. (linear_mrhs)).  B on the GPU, or on the host
         (then pinned memory is best): X is returned where B lives."""
         self._check_block(B, "B")
@@ -227,7 +230,7 @@ class Lattice:
             if rtilde.shape != B.shape or rtilde.is_cuda != B.is_cuda:
                 raise ValueError("rtilde must have B's shape and location")
         prm = self._params(method, prec, tol, maxiter, delta, X0 is not None, on_host, rtilde, seed, history,
-                           timing, restart, orth)
+                           timing, restart, orth, update)
         info = SolveInfo()
         res_buf = (C.c_double * L)()
         info.true_res = C.cast(res_buf, C.POINTER(C.c_double))
@@ -244,7 +247,7 @@ class Lattice:
 
     def block_solve_batched(self, B: torch.Tensor, kappas: Sequence[float], Ls: Sequence[int], method="bicggr",
                             prec="fp64", tol=1e-10, maxiter=2000, delta=0.0, rtilde=None, seed=0, history=False,
-                            timing=False, raise_on_fail=True, restart=False, orth=None):
+                            timing=False, raise_on_fail=True, restart=False, orth=None, update="fp64"):
         """Several systems (kappa_s, L_s columns each, concatenated in B)."""
         self._check_block(B, "B")
         nsys = len(Ls)
@@ -253,7 +256,7 @@ class Lattice:
         on_host = not B.is_cuda
         X = torch.empty_like(B, pin_memory=on_host) if on_host else torch.empty_like(B)
         prm = self._params(method, prec, tol, maxiter, delta, False, on_host, rtilde, seed, history, timing,
-                           restart, orth)
+                           restart, orth, update)
         infos = (SolveInfo * nsys)()
         res_bufs, hist_bufs = [], []
         for s in range(nsys):

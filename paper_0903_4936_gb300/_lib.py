@@ -16,7 +16,7 @@ STATUS_NAMES = {
     0: "BK_OK", 1: "BK_ERR_INVALID_ARG", 2: "BK_ERR_OUT_OF_MEMORY", 3: "BK_ERR_CUDA",
     4: "BK_ERR_NOT_CONVERGED", 5: "BK_ERR_BREAKDOWN", 6: "BK_ERR_NONFINITE", 7: "BK_ERR_NO_GAUGE",
 }
-PREC = {"fp64": 0, "fp32": 1, "fp16": 2}
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "df64": 3}
 METHOD = {"bicgstab": 0, "bicggr": 1}
 
 # Every symbol include/bkrylov.h declares.
@@ -34,7 +34,7 @@ class SolveParams(C.Structure):
         ("reliable_delta", C.c_double), ("x0_given", C.c_int), ("buffers_on_host", C.c_int),
         ("rtilde_mode", C.c_int), ("seed", C.c_uint64), ("rtilde", C.c_void_p), ("restart_on_update", C.c_int),
         ("orth_mode", C.c_int), ("record_history", C.c_int),
-        ("timing", C.c_int),
+        ("timing", C.c_int), ("update_prec", C.c_int),
     ]
 
 

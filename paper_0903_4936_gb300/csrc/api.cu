@@ -124,10 +124,14 @@ struct bk_ctx {
     bool verbose = false;  // BK_VERBOSE=1: one line per solve and per tuning decision on stderr
 };
 
-static const void* gauge_ptr(const bk_ctx* c, int prec) { return prec == BK_FP64 ? c->U64.p : c->U32.p; }
-static const void* clov_ptr(const bk_ctx* c, int prec) { return prec == BK_FP64 ? c->C64.p : c->C32.p; }
+static bool wide(int prec) { return prec == BK_FP64 || prec == BK_DF64; }
+static const void* gauge_ptr(const bk_ctx* c, int prec) { return wide(prec) ? c->U64.p : c->U32.p; }
+static const void* clov_ptr(const bk_ctx* c, int prec) { return wide(prec) ? c->C64.p : c->C32.p; }
 
 static bool valid_prec(int p) { return p == BK_FP64 || p == BK_FP32 || p == BK_FP16; }
+// operator calls also accept double-float arithmetic on FP64-layout blocks
+static bool valid_op_prec(int p) { return valid_prec(p) || p == BK_DF64; }
+static int storage_prec(int p) { return p == BK_DF64 ? BK_FP64 : p; }
 
 extern "C" const char* bk_status_string(bk_status s) {
     switch (s) {
@@ -222,8 +226,8 @@ extern "C" bk_status bk_build_clover(bk_ctx* c, double csw, void* stream) {
 }
 
 extern "C" size_t bk_field_bytes(const bk_ctx* c, int L, bk_prec prec) {
-    if (!c || L < 0 || !valid_prec(prec)) return 0;
-    return field_bytes(L, c->V, prec);
+    if (!c || L < 0 || !valid_op_prec(prec)) return 0;
+    return field_bytes(L, c->V, storage_prec(prec));
 }
 
 extern "C" bk_status bk_pack(bk_ctx* c, const double* X, void* Xd, int L, bk_prec prec, void* stream) {
@@ -246,7 +250,7 @@ extern "C" bk_status bk_unpack(bk_ctx* c, const void* Xd, double* X, int L, bk_p
 static bk_status tune_shape(bk_ctx* c, int prec, DslashOp op, cudaStream_t st, bk_ctx::Shape& best) {
     std::vector<bk_ctx::Shape> cands;
     const int rpts[3] = {1, 2, 4};
-    for (int ri = 0; ri < (prec == BK_FP64 ? 1 : 3); ++ri) {
+    for (int ri = 0; ri < (wide(prec) ? 1 : 3); ++ri) {
         const int rpt = rpts[ri];
         if (rpt > 1 && rpt > op.ncol) continue;
         const int ngroups = (op.ncol + rpt - 1) / rpt;
@@ -321,7 +325,7 @@ static bk_status dslash_fields(bk_ctx* c, int prec, const double* kappa, Field x
 
 extern "C" bk_status bk_dslash_dev(bk_ctx* c, const double* kappa, const void* Xd, void* Yd, int L, bk_prec prec,
                                    void* stream) {
-    BK_CHECK_ARG(c && kappa && Xd && Yd && L >= 1 && valid_prec(prec), "bad argument to bk_dslash_dev");
+    BK_CHECK_ARG(c && kappa && Xd && Yd && L >= 1 && valid_op_prec(prec), "bad argument to bk_dslash_dev");
     BK_CHECK_ARG(Xd != Yd, "bk_dslash_dev: X and Y must not overlap");
     if (!c->has_gauge || !c->has_clover) {
         bk_set_error("operator needs bk_upload_gauge and bk_build_clover first");
@@ -334,20 +338,21 @@ extern "C" bk_status bk_dslash_dev(bk_ctx* c, const double* kappa, const void* X
 
 extern "C" bk_status bk_dslash(bk_ctx* c, const double* kappa, const double* X, double* Y, int L, bk_prec prec,
                                void* stream) {
-    BK_CHECK_ARG(c && kappa && X && Y && L >= 1 && valid_prec(prec), "bad argument to bk_dslash");
+    BK_CHECK_ARG(c && kappa && X && Y && L >= 1 && valid_op_prec(prec), "bad argument to bk_dslash");
     if (!c->has_gauge || !c->has_clover) {
         bk_set_error("operator needs bk_upload_gauge and bk_build_clover first");
         return BK_ERR_NO_GAUGE;
     }
     BK_CUDA_TRY(cudaSetDevice(c->device));
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t nb = field_bytes(L, c->V, prec);
+    const int sp = storage_prec(prec);
+    const size_t nb = field_bytes(L, c->V, sp);
     BK_TRY(c->s1.ensure(nb));
     BK_TRY(c->s2.ensure(nb));
-    Field x = make_field(c->s1.p, L, c->V, prec), y = make_field(c->s2.p, L, c->V, prec);
-    BK_TRY(launch_pack(prec, X, x, L, st));
+    Field x = make_field(c->s1.p, L, c->V, sp), y = make_field(c->s2.p, L, c->V, sp);
+    BK_TRY(launch_pack(sp, X, x, L, st));
     BK_TRY(dslash_fields(c, prec, kappa, x, y, x, 0, L, 0, st));
-    return launch_unpack(prec, y, Y, L, st);
+    return launch_unpack(sp, y, Y, L, st);
 }
 
 extern "C" bk_status bk_gamma5(bk_ctx* c, const double* X, double* Y, int L, void* stream) {
@@ -528,6 +533,7 @@ struct Solve {
     std::vector<char> res_known;     // per system: true_res already holds the final FP64 residual
     Field B64, X64, R64, Xlo, R, Rt, Pb, Vb, Wb, Ub, Yb, Tb, Zb, Ptmp;
     bool orth = false;
+    int upd_prec = BK_FP64;  // arithmetic of the residual replacements
     // small device arrays
     double *G_V, *G_RR, *G_RRn, *alpha, *gam, *G_Z, *dots, *rn, *zeta, *mzeta, *izeta, *partial, *LU;
     int *info_a, *info_g, *zbad, *piv;
@@ -701,22 +707,24 @@ struct Solve {
 
     // FP64 residual replacement for system s: X64 += Xlo, R64 = B - A X64, R = R64.
     // Leaves the FP64 residual norms of s in rn_h after a readback.
-    bk_status reliable_update(const std::vector<int>& sys) {
+    // rprec: BK_FP64 or BK_DF64 arithmetic for B - A X; accum = false recomputes
+    // the residual of the current X64 (Xlo already folded in).
+    bk_status reliable_update(const std::vector<int>& sys, int rprec, bool accum) {
         unsigned mask = 0;
         for (int s : sys) {
             mask |= 1u << s;
             mv64[s]++;
-            nrel[s]++;
+            if (accum) nrel[s]++;
         }
         for (const auto& cr : col_runs(mask)) {
             const int c0 = cr.first, n = cr.second;
-            if (mixed) {
+            if (mixed && accum) {
                 dim3 grid((V + 127) / 128, n);
                 k_accum<<<grid, 128, 0, st>>>(field_cols(X64, c0), field_cols(Xlo, c0), V);
                 BK_CUDA_TRY(cudaGetLastError());
                 launches++;
             }
-            BK_TRY(dslash(BK_FP64, X64, R64, B64, c0, n, 1));
+            BK_TRY(dslash(rprec, X64, R64, B64, c0, n, 1));
             if (P != BK_FP64) {
                 BK_TRY(launch_cast(BK_FP64, field_cols(R64, c0), P, field_cols(R, c0), n, st));
             } else {
@@ -739,6 +747,7 @@ struct Solve {
         X64 = make_field(c->X64.p, Lt, V, BK_FP64);
         R64 = make_field(c->R64.p, Lt, V, BK_FP64);
         orth = method == BK_BICGSTAB && (prm->orth_mode == 1 || (prm->orth_mode == 0 && mixed));
+        upd_prec = (mixed && prm->update_prec == 1) ? BK_DF64 : BK_FP64;
         const int nblk = 7;
         for (int i = 0; i < nblk; ++i) BK_TRY(c->blk[i].ensure(fbp));
         Field f[8];
@@ -895,6 +904,14 @@ struct Solve {
         return BK_OK;
     }
 
+    // system s converged on an FP64 true residual of its final X (Xlo folded
+    // in), which finish() therefore need not recompute
+    void converged_fp64(int s) {
+        done[s] = 1;
+        res_known[s] = 1;
+        for (int j = part.col0[s]; j < part.col0[s + 1]; ++j) true_res[j] = rel(j);
+    }
+
     void update_active() {
         unsigned a = 0;
         for (int s = 0; s < nsys; ++s)
@@ -978,21 +995,29 @@ struct Solve {
             if (nrestart[s] > 100) done[s] = 2;
         }
         if (!upd.empty()) {
-            BK_TRY(reliable_update(upd));
+            BK_TRY(reliable_update(upd, upd_prec, true));
+            std::vector<int> conf;
             for (int s : upd) {
-                const double m = sys_max(s);  // FP64 true residual
+                const double m = sys_max(s);  // true residual (FP64 or double-float)
                 hist[s].back() = m;
                 rmax_since[s] = m;
                 m_upd[s] = m;
                 since[s] = 0;
-                if (m <= prm->tol) {
-                    // converged on an FP64 true residual of the final X (Xlo was
-                    // just folded in): finish() need not recompute it
-                    done[s] = 1;
-                    res_known[s] = 1;
-                    for (int j = part.col0[s]; j < part.col0[s + 1]; ++j) true_res[j] = rel(j);
-                }
+                if (m <= prm->tol && upd_prec != BK_FP64) conf.push_back(s);
+                else if (m <= prm->tol) converged_fp64(s);
                 else if (prm->restart_on_update) restart_now[s] = 1;
+            }
+            if (!conf.empty()) {
+                // convergence is decided on an FP64 true residual of the same X
+                BK_TRY(reliable_update(conf, BK_FP64, false));
+                for (int s : conf) {
+                    const double m = sys_max(s);
+                    hist[s].back() = m;
+                    rmax_since[s] = m;
+                    m_upd[s] = m;
+                    if (m <= prm->tol) converged_fp64(s);
+                    else if (prm->restart_on_update) restart_now[s] = 1;
+                }
             }
         }
         update_active();

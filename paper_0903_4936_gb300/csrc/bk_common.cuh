@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "bkrylov.h"
+#include "dd.cuh"
 
 // ----------------------------------------------------------------- complex
 
@@ -89,7 +90,20 @@ struct Prec<BK_FP16> {
     static constexpr int nclov = 18;
 };
 
-__host__ __device__ inline int prec_nchunk(int p) { return p == BK_FP64 ? 12 : (p == BK_FP32 ? 6 : 3); }
+// BK_DF64: double-float arithmetic on blocks stored in the BK_FP64 layout,
+// with the FP64 links and clover.
+template <>
+struct Prec<BK_DF64> {
+    typedef dd real;
+    typedef double2 link;
+    typedef double2 clov;
+    static constexpr int nchunk = 12;
+    static constexpr int nclov = 36;
+};
+
+__host__ __device__ inline int prec_nchunk(int p) {
+    return (p == BK_FP64 || p == BK_DF64) ? 12 : (p == BK_FP32 ? 6 : 3);
+}
 
 // A view of a device-layout block.  `data` points at column 0, chunk 0.
 struct Field {
@@ -159,6 +173,16 @@ __device__ __forceinline__ void load_spinor<BK_FP16>(const Field& f, int c, int 
     }
 }
 
+template <>
+__device__ __forceinline__ void load_spinor<BK_DF64>(const Field& f, int c, int s, cx<dd> (&v)[12]) {
+    const double2* p = (const double2*)f.data + (size_t)c * f.cstride + s;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        double2 q = p[(size_t)k * f.V];
+        v[k] = mk(dd(q.x), dd(q.y));
+    }
+}
+
 template <int P>
 __device__ __forceinline__ void store_spinor(const Field& f, int c, int s, const cx<typename Prec<P>::real> (&v)[12]);
 
@@ -167,6 +191,12 @@ __device__ __forceinline__ void store_spinor<BK_FP64>(const Field& f, int c, int
     double2* p = (double2*)f.data + (size_t)c * f.cstride + s;
 #pragma unroll
     for (int k = 0; k < 12; ++k) p[(size_t)k * f.V] = make_double2(v[k].r, v[k].i);
+}
+template <>
+__device__ __forceinline__ void store_spinor<BK_DF64>(const Field& f, int c, int s, const cx<dd> (&v)[12]) {
+    double2* p = (double2*)f.data + (size_t)c * f.cstride + s;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[(size_t)k * f.V] = make_double2((double)v[k].r, (double)v[k].i);
 }
 template <>
 __device__ __forceinline__ void store_spinor<BK_FP32>(const Field& f, int c, int s, const cx<float> (&v)[12]) {

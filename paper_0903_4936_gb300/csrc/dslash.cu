@@ -224,7 +224,7 @@ __device__ __forceinline__ void load_clov_block(const float4* __restrict__ C, in
 
 // FP64 needs more registers per thread: cap its blocks at 256 threads.
 template <int P, int RPT = 1>
-constexpr int dslash_max_threads() { return (P == BK_FP64 || RPT > 1) ? 256 : 512; }
+constexpr int dslash_max_threads() { return (P == BK_FP64 || P == BK_DF64 || RPT > 1) ? 256 : 512; }
 
 // Thread (site s, column group g) computes columns col0 + g*RPT + r, r < RPT:
 // each link and clover block is loaded into registers once and applied to the
@@ -341,7 +341,7 @@ bk_status dslash_impl(const DslashOp& op, cudaStream_t st) {
     for (int j = 0; j < op.ncol; ++j) a.kappa[j] = op.kappa[j];
     // Launch shape: RPT columns per thread, BY column groups x SX sites per block.
     int rpt = op.rpt > 0 ? op.rpt : 1;
-    if (P == BK_FP64) rpt = 1;
+    if (P == BK_FP64 || P == BK_DF64) rpt = 1;
     if (rpt != 1 && rpt != 2 && rpt != 4) rpt = 1;
     const int ngroups = (op.ncol + rpt - 1) / rpt;
     int BY = op.col_block, SX = op.site_block;
@@ -358,7 +358,7 @@ bk_status dslash_impl(const DslashOp& op, cudaStream_t st) {
     const int nsb = (op.V + SX - 1) / SX, ngb = (ngroups + BY - 1) / BY;
     a.groups_fast = nsb <= 65535 ? 1 : 0;
     dim3 grid = a.groups_fast ? dim3(ngb, nsb) : dim3(nsb, ngb);
-    if constexpr (P == BK_FP64) {
+    if constexpr (P == BK_FP64 || P == BK_DF64) {
         k_dslash<P, 1><<<grid, SX * BY, 0, st>>>(a);
     } else {
         switch (rpt) {
@@ -440,6 +440,7 @@ bk_status launch_dslash(int prec, const DslashOp& op, cudaStream_t st) {
         case BK_FP64: return dslash_impl<BK_FP64>(op, st);
         case BK_FP32: return dslash_impl<BK_FP32>(op, st);
         case BK_FP16: return dslash_impl<BK_FP16>(op, st);
+        case BK_DF64: return dslash_impl<BK_DF64>(op, st);
     }
     return BK_ERR_INVALID_ARG;
 }

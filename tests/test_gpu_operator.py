@@ -14,7 +14,9 @@ pytestmark = pytest.mark.gpu
 # paper's operator to rounding.  FP32: unit roundoff 6e-8 times ~50 terms
 # summed per output.  FP16 storage: inputs rounded to 11 mantissa bits
 # relative to each site's largest component (2.4e-4), plus the output store.
-TOL = {"fp64": 1e-13, "fp32": 2e-6, "fp16": 2e-3}
+# Double-float (df64): two floats per real, about 2^-46 per operation
+# (sloppy addition), ~50 terms per output.
+TOL = {"fp64": 1e-13, "df64": 1e-12, "fp32": 2e-6, "fp16": 2e-3}
 
 
 def _lat(dims, eps, seed, csw=1.0):
@@ -30,7 +32,7 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32", "fp16"])
 @pytest.mark.parametrize("dims,L", [((4, 4, 4, 4), 12), ((2, 4, 2, 6), 5), ((3, 5, 4, 6), 1),
                                     ((8, 8, 8, 16), 12), ((6, 4, 4, 4), 17), ((4, 4, 8, 8), 48)])
 def test_dslash_matches_oracle(prec, dims, L):
@@ -151,3 +153,22 @@ def test_dslash_full_size_sampled_sites_fp16():
     ref = dirac.apply_dirac_at(U, X, 0.125, 1.0, sites, dims)
     got = Y.reshape(12, V, 4, 3)[:, sites]
     assert _rel(got, ref) < TOL["fp16"]
+
+
+def test_df64_operator_tracks_fp64_where_fp32_cannot():
+    """Double-float arithmetic on FP64-layout blocks: the residual B - A X of a
+    nearly converged X (|B - A X| ~ 1e-9 |B|) agrees with the FP64 result to
+    well below the residual itself, which FP32 arithmetic cannot resolve."""
+    dims = (8, 8, 8, 8)
+    lat, U = _lat(dims, 0.5, 77)
+    B = synth.z2_noise(dims, 4, 3)
+    Bt = torch.from_numpy(B).cuda()
+    X, info = lat.block_solve(Bt, 0.124, prec="fp64", tol=1e-9, maxiter=2000)
+    AX64 = lat.dslash(X, 0.124, "fp64").cpu().numpy()
+    AXdd = lat.dslash(X, 0.124, "df64").cpu().numpy()
+    AX32 = lat.dslash(X, 0.124, "fp32").cpu().numpy()
+    r64, rdd, r32 = B - AX64, B - AXdd, B - AX32
+    nb = np.linalg.norm(B)
+    assert np.linalg.norm(r64) < 2e-9 * nb
+    assert np.linalg.norm(rdd - r64) < 1e-3 * np.linalg.norm(r64)
+    assert np.linalg.norm(r32 - r64) > 10 * np.linalg.norm(r64)

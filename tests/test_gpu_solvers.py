@@ -242,3 +242,21 @@ def test_batched_uneven_systems_c4_structure():
                                    maxiter=3000)
         assert _dev(X[c0:c0 + L], Xs.cpu().numpy()) <= 1e-8
         c0 += L
+
+
+@pytest.mark.parametrize("method", ["bicgstab", "bicggr"])
+def test_residual_replacement_arithmetic(c1, method):
+    """Mixed precision with FP64 (default) and double-float residual
+    replacements: both reach the FP64 true residual and the dense solution.
+    The FP32 inner recurrences follow the replaced residuals' last bits, so
+    the two runs take different (rounding-driven) paths: their iteration
+    counts agree to within a factor, not exactly."""
+    dims, lat, U, B, Xd, A = c1
+    Bt = torch.from_numpy(B).cuda()
+    out = {}
+    for upd in ("df64", "fp64"):
+        X, info = lat.block_solve(Bt, 0.12, method=method, prec="fp32", tol=1e-10, maxiter=1000, update=upd)
+        assert info["converged"] == 1 and info["true_res_max"] <= 1e-10
+        assert _dev(X.cpu().numpy(), Xd) <= 1e-8
+        out[upd] = info["iterations"]
+    assert max(out.values()) <= 1.5 * min(out.values()), out
