@@ -515,6 +515,14 @@ __global__ void __launch_bounds__(256) k_genop_chunk(const __grid_constant__ Gen
     for (int t = 0; t < GENOP_MAXE; ++t) ea[t] = coef(g.ea[t], g.ea_mult[t]);
     const cx<float> xa = coef(g.xa, g.xa_mult);
     const float ym = (float)g.ym, xm = (float)g.xm;
+    // X is read and written: load every column of it before the first store,
+    // which the compiler could not otherwise move loads across
+    float4 xold[LS];
+    if (g.hasX) {
+#pragma unroll
+        for (int j = 0; j < LS; ++j)
+            if (j < Ls) xold[j] = *at(g.X, c0 + j);
+    }
 #pragma unroll
     for (int j = 0; j < LS; ++j) {
         if (j >= Ls) continue;
@@ -532,7 +540,7 @@ __global__ void __launch_bounds__(256) k_genop_chunk(const __grid_constant__ Gen
         }
         if (g.hasX) {
             float4* xp = at(g.X, c0 + j);
-            const float4 x = *xp;
+            const float4 x = xold[j];
             const float4 v = __ldg(at(g.Xin, c0 + j));
             cx<float> x0 = mk(x.x, x.y) + xm * acc[j][0], x1 = mk(x.z, x.w) + xm * acc[j][1];
             cmac(x0, xa, mk(v.x, v.y));
@@ -830,7 +838,7 @@ bool gram_tiled_ok(int prec, const SysPart& p) {
 // ---------------------------------------------------------------- Gram, small systems
 //
 // G_s = A_s^H B_s for FP32 / FP16 blocks whose systems all have L_s <= 12.
-// A warp owns one T x T tile of G_s (T = 4 or 6, so G_s is one or four tiles)
+// A warp owns one T x T tile of G_s (T = 3, 4 or 6, so G_s is one or four tiles)
 // and streams 32 consecutive sites per step, lane = site: every load is one
 // 512-byte row of a 16-byte chunk, and the warps of a block that need the same
 // column of the same sites meet it in L1.  Products accumulate in FP32 per
@@ -991,8 +999,7 @@ static int gram_small_T(int prec, const SysPart& p) {
     if (prec == BK_FP64) return 0;
     int maxL = 0;
     for (int s = 0; s < p.nsys; ++s) maxL = std::max(maxL, p.col0[s + 1] - p.col0[s]);
-    if (maxL <= 4) return 4;
-    if (maxL <= 6) return 6;
+    if (maxL <= 6) return 3;  // four 3 x 3 tiles: 78 registers, 3 blocks per SM
     if (maxL <= 8) return 4;
     if (maxL <= 12) return 6;
     return 0;
@@ -1285,10 +1292,12 @@ bk_status launch_gram(int prec, Field A, Field B, const SysPart& p, double* G, d
         dim3 grid(nbx, p.nsys);
         double2* part = (double2*)partial;
         if (prec == BK_FP32) {
-            if (T == 4) k_gram_small<BK_FP32, 4><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
+            if (T == 3) k_gram_small<BK_FP32, 3><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
+            else if (T == 4) k_gram_small<BK_FP32, 4><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
             else k_gram_small<BK_FP32, 6><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
         } else {
-            if (T == 4) k_gram_small<BK_FP16, 4><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
+            if (T == 3) k_gram_small<BK_FP16, 3><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
+            else if (T == 4) k_gram_small<BK_FP16, 4><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
             else k_gram_small<BK_FP16, 6><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
         }
         BK_CUDA_TRY(cudaGetLastError());
