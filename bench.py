@@ -83,12 +83,17 @@ def sources(dims, L, kind, seed):
     return synth.gaussian_sources(dims, L, seed)
 
 
+# sources that define the operator kernel k_dslash (its own file and the
+# headers it includes)
+OPERATOR_SOURCES = ["paper_0903_4936_gb300/csrc/dslash.cu", "paper_0903_4936_gb300/csrc/bk_common.cuh",
+                    "paper_0903_4936_gb300/csrc/dd.cuh", "paper_0903_4936_gb300/csrc/bk_kernels.h",
+                    "include/bkrylov.h"]
+
+
 def source_hash():
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_0903_4936_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in OPERATOR_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -100,16 +105,21 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(workload):
-    """DRAM bytes per inner-operator launch from the committed ncu summary, if it
-    was taken on the current kernel sources; else None."""
+def ncu_traffic(prec, alg_bytes_per_launch):
+    """DRAM bytes per inner-operator launch: the measured DRAM / algorithmic
+    byte ratio of the committed ncu capture of the same kernel (a smaller
+    launch of the same shape), scaled to this run's average launch.  None
+    unless the capture was taken on the current kernel sources."""
     p = os.path.join(ROOT, "profiles", "dslash_traffic.json")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or alg_bytes_per_launch is None:
         return None
     d = json.load(open(p))
     if d.get("source_hash") != source_hash():
         return None
-    return d.get("per_launch_bytes", {}).get(workload)
+    c = d.get("captures", {}).get(prec)
+    if not c:
+        return None
+    return c["dram_bytes"] / c["alg_bytes"] * alg_bytes_per_launch
 
 
 class Clocks:
@@ -425,7 +435,7 @@ def main():
     hbm, peak_kind = measured_peaks()
     achieved = (agg["bytes_inner"] / agg["n_inner"]) / ((agg["t_inner"] / agg["n_inner"]) / 1e3) / 1e9 \
         if agg["n_inner"] else None
-    traffic = ncu_traffic(args.workload)
+    traffic = ncu_traffic(wl["prec"], agg["bytes_inner"] / agg["n_inner"] if agg["n_inner"] else None)
     line = {
         "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

@@ -112,7 +112,7 @@ struct bk_ctx {
     // scratch of the single-operation entry points
     DevBuf s1, s2, part, scal;
     // solver workspace
-    DevBuf B64, X64, R64, Xlo, blk[8], small, spart, canonB, canonX, canonRt, fscratch;
+    DevBuf B64, X64, R64, Xlo, blk[8], small, spart, canonB, canonX, canonRt, fscratch, ynorm;
     HostBuf rb_host;
     std::vector<cudaEvent_t> events;
     // operator launch shapes chosen by the autotuner, keyed by (prec, residual, ncol)
@@ -185,7 +185,7 @@ extern "C" bk_status bk_destroy(bk_ctx* c) {
     cudaSetDevice(c->device);
     DevBuf* bufs[] = {&c->U64, &c->U32, &c->C64, &c->C32, &c->Utmp, &c->s1, &c->s2, &c->part, &c->scal,
                       &c->B64, &c->X64, &c->R64, &c->Xlo, &c->small, &c->spart, &c->canonB,
-                      &c->canonX, &c->canonRt, &c->fscratch};
+                      &c->canonX, &c->canonRt, &c->fscratch, &c->ynorm};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : c->blk) b.release();
     c->rb_host.release();
@@ -534,6 +534,8 @@ struct Solve {
     Field B64, X64, R64, Xlo, R, Rt, Pb, Vb, Wb, Ub, Yb, Tb, Zb, Ptmp;
     bool orth = false;
     int upd_prec = BK_FP64;  // arithmetic of the residual replacements
+    double* ynorm = nullptr;  // per-block partial sums of ||R_j||^2 from the R update
+    bool norms_fused = false; // this iteration's norms are in ynorm
     // small device arrays
     double *G_V, *G_RR, *G_RRn, *alpha, *gam, *G_Z, *dots, *rn, *zeta, *mzeta, *izeta, *partial, *LU;
     int *info_a, *info_g, *zbad, *piv;
@@ -623,6 +625,11 @@ struct Solve {
         launches += 2;
         return launch_gram(P, A, B, part, G, partial, V, st);
     }
+    // G = A^H B and G2 = A^H B2 in one pass over A where possible
+    bk_status gram2(Field A, Field B, Field B2, double* G, double* G2) {
+        launches += 2;
+        return launch_gram2(P, A, B, B2, part, G, G2, partial, V, st);
+    }
     bk_status coldot(int prec, int npair, const Field* A, const Field* B, double* out, int ncol = -1) {
         launches += 2;
         return launch_coldot(prec, npair, A, B, ncol < 0 ? Lt : ncol, out, partial, V, st);
@@ -656,9 +663,9 @@ struct Solve {
         BK_CUDA_TRY(cudaGetLastError());
         return BK_OK;
     }
-    bk_status genop(const GenOp& g) {
+    bk_status genop(const GenOp& g, bool* ynorm_done = nullptr) {
         launches += 1;
-        return launch_genop(P, g, V, st);
+        return launch_genop(P, g, V, st, ynorm_done);
     }
     GenOp genop0() {
         GenOp g;
@@ -816,6 +823,12 @@ struct Solve {
         const size_t pb = std::max(gram_partial_bytes(part, V), coldot_partial_bytes(Lt, 3, V));
         BK_TRY(c->spart.ensure(pb));
         partial = c->spart.as<double>();
+        if (method == BK_BICGSTAB) {  // residual norms fused into the R update
+            const size_t nb = (size_t)Lt * genop_norm_blocks(V) * sizeof(double);
+            BK_TRY(c->ynorm.ensure(nb));
+            ynorm = c->ynorm.as<double>();
+            BK_CUDA_TRY(cudaMemsetAsync(ynorm, 0, nb, st));
+        }
 
         // B, X0 into the FP64 device layout
         BK_TRY(launch_pack(BK_FP64, Bc, B64, Lt, st));
@@ -965,7 +978,15 @@ struct Solve {
     // After the new residual R_{k+1} exists: stopping rule, breakdown flags and,
     // in mixed precision, FP64 reliable updates and the cycle guards.
     bk_status check(int k) {
-        BK_TRY(residual_norms());
+        if (norms_fused) {  // the R update left per-block partial sums
+            for (const auto& cr : col_runs(part.active)) {
+                BK_TRY(launch_norm_finish(ynorm, cr.first, cr.second, rn, V, st));
+                launches++;
+            }
+            BK_TRY(readback());
+        } else {
+            BK_TRY(residual_norms());
+        }
         std::vector<int> upd, bad;
         const double delta = prm->reliable_delta > 0 ? prm->reliable_delta : 0.1;
         const int kmax = 50;  // forced FP64 update after this many iterations without one
@@ -1141,8 +1162,7 @@ struct Solve {
                 std::swap(Pb, Ptmp);
             }
             BK_TRY(dslash_active(Pb, Vb, Pb));  // V = A P
-            BK_TRY(gram(Rt, Vb, G_V));
-            BK_TRY(gram(Rt, R, G_RR));
+            BK_TRY(gram2(Rt, Vb, R, G_V, G_RR));  // R~^H V, R~^H R
             BK_TRY(factor(G_V, info_a));  // R~^H V, used for alpha and beta
             BK_TRY(substitute(G_RR, nullptr, nullptr, alpha, info_a));
             {   // T = R - V alpha
@@ -1195,10 +1215,12 @@ struct Solve {
                 g.xa_mult = 1.0;
                 g.xm = 1.0;
                 g.skip = info_a;
-                BK_TRY(genop(g));
+                g.ynorm = ynorm;
+                BK_TRY(genop(g, &norms_fused));
             }
             const unsigned before = part.active;
             BK_TRY(check(k));
+            norms_fused = false;
             part.active &= before;
             if (!part.active) break;
             {   // P = R + (P - zeta V) beta   (into Ptmp, then swap)

@@ -53,6 +53,9 @@ SysPart single_part(int L);
 size_t gram_partial_bytes(const SysPart& p, int V);
 bk_status launch_gram(int prec, Field A, Field B, const SysPart& p, double* G, double* partial, int V,
                       cudaStream_t st);
+// G = A^H B and G2 = A^H B2, reading A once where the small-system kernel applies.
+bk_status launch_gram2(int prec, Field A, Field B, Field B2, const SysPart& p, double* G, double* G2,
+                       double* partial, int V, cudaStream_t st);
 
 // Column dot products: out[k * ldo + j] = (A_k)_j^H (B_k)_j for pairs k < npair
 // (ldo = L when not given).
@@ -93,8 +96,17 @@ struct GenOp {
     double xm;
     const int* skip;
     SysPart p;
+    // optional: squared norms of the Y columns, as per-block partial sums
+    // ynorm[col * genop_norm_blocks(V) + b] (FP64), summed by launch_norm_finish
+    double* ynorm;
 };
-bk_status launch_genop(int prec, const GenOp& g, int V, cudaStream_t st);
+// *ynorm_done = whether the kernel that ran filled g.ynorm (only the
+// small-system FP32 kernel does).
+bk_status launch_genop(int prec, const GenOp& g, int V, cudaStream_t st, bool* ynorm_done = nullptr);
+int genop_norm_blocks(int V);
+// out[2 j] = sum_b ynorm[j * genop_norm_blocks(V) + b], out[2 j + 1] = 0 for
+// columns j in [c0, c0 + n).
+bk_status launch_norm_finish(const double* ynorm, int c0, int n, double* out, int V, cudaStream_t st);
 
 // ---------------------------------------------------------------- force.cu
 size_t force_scratch_bytes(int V);

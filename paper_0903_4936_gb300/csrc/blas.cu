@@ -471,8 +471,9 @@ __global__ void __launch_bounds__(256) k_genop_chunk(const __grid_constant__ Gen
         }
     }
     __syncthreads();
-    const int site = blockIdx.x * blockDim.x + threadIdx.x;
-    if (site >= V) return;
+    const int site0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = site0 < V;
+    const int site = live ? site0 : V - 1;  // dead lanes compute, store nothing
     const int ch = blockIdx.y;
     auto coef = [&](const double* ptr, double mult) -> cx<float> {
         if (!ptr) return mk((float)mult, 0.f);
@@ -515,16 +516,10 @@ __global__ void __launch_bounds__(256) k_genop_chunk(const __grid_constant__ Gen
     for (int t = 0; t < GENOP_MAXE; ++t) ea[t] = coef(g.ea[t], g.ea_mult[t]);
     const cx<float> xa = coef(g.xa, g.xa_mult);
     const float ym = (float)g.ym, xm = (float)g.xm;
-    // X is read and written: load every column of it before the first store,
-    // which the compiler could not otherwise move loads across
-    float4 xold[LS];
-    if (g.hasX) {
-#pragma unroll
-        for (int j = 0; j < LS; ++j)
-            if (j < Ls) xold[j] = *at(g.X, c0 + j);
-    }
+    float nrm[LS];
 #pragma unroll
     for (int j = 0; j < LS; ++j) {
+        nrm[j] = 0.f;
         if (j >= Ls) continue;
         if (g.hasY) {
             cx<float> y[2] = {ym * acc[j][0], ym * acc[j][1]};
@@ -536,11 +531,12 @@ __global__ void __launch_bounds__(256) k_genop_chunk(const __grid_constant__ Gen
                     cmac(y[1], ea[t], mk(q.z, q.w));
                 }
             }
-            *at(g.Y, c0 + j) = make_float4(y[0].r, y[0].i, y[1].r, y[1].i);
+            if (live) *at(g.Y, c0 + j) = make_float4(y[0].r, y[0].i, y[1].r, y[1].i);
+            if (live) nrm[j] = y[0].r * y[0].r + y[0].i * y[0].i + y[1].r * y[1].r + y[1].i * y[1].i;
         }
-        if (g.hasX) {
+        if (g.hasX && live) {
             float4* xp = at(g.X, c0 + j);
-            const float4 x = xold[j];
+            const float4 x = *xp;
             const float4 v = __ldg(at(g.Xin, c0 + j));
             cx<float> x0 = mk(x.x, x.y) + xm * acc[j][0], x1 = mk(x.z, x.w) + xm * acc[j][1];
             cmac(x0, xa, mk(v.x, v.y));
@@ -548,7 +544,56 @@ __global__ void __launch_bounds__(256) k_genop_chunk(const __grid_constant__ Gen
             *xp = make_float4(x0.r, x0.i, x1.r, x1.i);
         }
     }
+    if (g.ynorm) {  // block-uniform: per column, the sum over this block's sites
+        __shared__ float nred[8][LS];
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+        for (int j = 0; j < LS; ++j) {
+            float v = nrm[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) nred[warp][j] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < Ls) {
+            double v = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += (double)nred[w][threadIdx.x];
+            g.ynorm[(size_t)(c0 + threadIdx.x) * (gridDim.x * gridDim.y) + (size_t)ch * gridDim.x + blockIdx.x] = v;
+        }
+    }
 }
+
+}  // namespace
+
+int genop_norm_blocks(int V) { return ((V + 255) / 256) * Prec<BK_FP32>::nchunk; }
+
+namespace {
+
+__global__ void k_norm_finish(const double* __restrict__ part, int c0, int n, int nb, double* __restrict__ out) {
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (j >= n) return;
+    const double* p = part + (size_t)(c0 + j) * nb;
+    double v = 0.0;
+    for (int b = lane; b < nb; b += 32) v += p[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) {
+        out[2 * (size_t)(c0 + j)] = v;
+        out[2 * (size_t)(c0 + j) + 1] = 0.0;
+    }
+}
+
+}  // namespace
+
+bk_status launch_norm_finish(const double* ynorm, int c0, int n, double* out, int V, cudaStream_t st) {
+    if (n <= 0) return BK_OK;
+    k_norm_finish<<<(n + 7) / 8, 256, 0, st>>>(ynorm, c0, n, genop_norm_blocks(V), out);
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}
+
+namespace {
 
 // ---------------------------------------------------------------- fused block update, tiled
 //
@@ -876,7 +921,7 @@ struct RawChunk<BK_FP16> {
 };
 
 template <int P, int T>
-__global__ void __launch_bounds__(GS_THREADS) k_gram_small(Field A, Field B, SysPart p,
+__global__ void __launch_bounds__(GS_THREADS) k_gram_small(Field A, Field B, Field B2, int npair, SysPart p,
                                                            double2* __restrict__ partial, int V) {
     using RC = RawChunk<P>;
     constexpr int nch = Prec<P>::nchunk, cpc = Chunk<P>::cpc;
@@ -888,10 +933,13 @@ __global__ void __launch_bounds__(GS_THREADS) k_gram_small(Field A, Field B, Sys
     if (!((p.active >> s) & 1u)) return;
     const int c0 = p.col0[s], Ls = p.col0[s + 1] - c0;
     const int nt = (Ls + T - 1) / T, ntiles = nt * nt;  // 1 or 4
-    const int G = NW / ntiles;                          // site groups per block
+    const int nwork = ntiles * npair;                   // (pair, tile) per warp: 1, 2, 4 or 8
+    const int G = NW / nwork;                           // site groups per block
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = warp % ntiles, grp = warp / ntiles;
+    const int work = warp % nwork, grp = warp / nwork;
+    const int pq = work / ntiles, tile = work % ntiles;
     const int ti = tile / nt, tj = tile % nt;
+    const Field& Bq = pq ? B2 : B;
     int ca[T], cb[T];
 #pragma unroll
     for (int x = 0; x < T; ++x) {
@@ -923,7 +971,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_gram_small(Field A, Field B, Sys
 #pragma unroll
             for (int x = 0; x < T; ++x) {
                 sa[x] = RC::scale(A, ca[x], site);
-                sb[x] = RC::scale(B, cb[x], site);
+                sb[x] = RC::scale(Bq, cb[x], site);
             }
 #pragma unroll
             for (int ch = 0; ch < nch; ++ch) {
@@ -931,7 +979,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_gram_small(Field A, Field B, Sys
 #pragma unroll
                 for (int x = 0; x < T; ++x) {
                     ra[x] = RC::ld(A, ca[x], site, ch);
-                    rb[x] = RC::ld(B, cb[x], site, ch);
+                    rb[x] = RC::ld(Bq, cb[x], site, ch);
                 }
 #pragma unroll
                 for (int m = 0; m < cpc; ++m) {
@@ -964,23 +1012,27 @@ __global__ void __launch_bounds__(GS_THREADS) k_gram_small(Field A, Field B, Sys
 #pragma unroll
     for (int q = 0; q < NS; ++q) red[warp][q * 32 + lane] = sh[q];
     __syncthreads();
+    const int ne = p.coef_off[p.nsys];
     const int off = p.coef_off[s];
-    for (int e = threadIdx.x; e < ntiles * T * T; e += blockDim.x) {
-        const int tl = e / (T * T), xy = e % (T * T);
+    for (int e = threadIdx.x; e < nwork * T * T; e += blockDim.x) {
+        const int w = e / (T * T), xy = e % (T * T);
+        const int q = w / ntiles, tl = w % ntiles;
         const int i = (tl / nt) * T + xy / T, j = (tl % nt) * T + xy % T;
         double2 v = make_double2(0.0, 0.0);
         for (int g = 0; g < G; ++g) {
-            v.x += red[g * ntiles + tl][2 * xy];
-            v.y += red[g * ntiles + tl][2 * xy + 1];
+            v.x += red[g * nwork + w][2 * xy];
+            v.y += red[g * nwork + w][2 * xy + 1];
         }
-        if (i < Ls && j < Ls) partial[(size_t)blockIdx.x * p.coef_off[p.nsys] + off + i * Ls + j] = v;
+        if (i < Ls && j < Ls) partial[((size_t)blockIdx.x * npair + q) * ne + off + i * Ls + j] = v;
     }
 }
 
 // G[e] = sum over blocks b of partial[b * ne + e]: one warp per entry, lanes
 // stride over the blocks, FP64 throughout (fixed order, so reproducible).
+// With two outputs (G2 != nullptr) entries [ne1, ne) go to G2[e - ne1].
 __global__ void k_gram_finish_warp(const double2* __restrict__ partial, int ne, int nbx,
-                                   double2* __restrict__ G) {
+                                   double2* __restrict__ G, double2* __restrict__ G2 = nullptr,
+                                   int ne1 = 0) {
     const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (e >= ne) return;
@@ -991,7 +1043,10 @@ __global__ void k_gram_finish_warp(const double2* __restrict__ partial, int ne, 
         v.y += w.y;
     }
     v = warp_sum(v);
-    if (lane == 0) G[e] = v;
+    if (lane == 0) {
+        if (G2 && e >= ne1) G2[e - ne1] = v;
+        else G[e] = v;
+    }
 }
 
 // Tile side of k_gram_small for this partition, 0 if it does not apply.
@@ -1005,12 +1060,12 @@ static int gram_small_T(int prec, const SysPart& p) {
     return 0;
 }
 
-static int gram_small_nbx(const SysPart& p, int V, int T, int nthreads) {
+static int gram_small_nbx(const SysPart& p, int V, int T, int nthreads, int npair) {
     int na = 0, maxtiles = 1;
     for (int s = 0; s < p.nsys; ++s) {
         if ((p.active >> s) & 1u) ++na;
         const int nt = (p.col0[s + 1] - p.col0[s] + T - 1) / T;
-        maxtiles = std::max(maxtiles, nt * nt);
+        maxtiles = std::max(maxtiles, nt * nt * npair);
     }
     const int G = (nthreads / 32) / maxtiles;
     const int groups = (V + 31) / 32;
@@ -1280,32 +1335,48 @@ size_t gram_partial_bytes(const SysPart& p, int V) {
     const int nbx = gram_nbx(ntiles, V);
     size_t b = (size_t)ntiles * GT * GT * nbx * sizeof(double2);
     const size_t bt = (size_t)gram_tiled_nbx(p.nsys, V) * p.coef_off[p.nsys] * sizeof(double2);
-    const size_t bs = (size_t)GS_TARGET_BLOCKS * p.coef_off[p.nsys] * sizeof(double2);
+    const size_t bs = (size_t)GS_TARGET_BLOCKS * 2 * p.coef_off[p.nsys] * sizeof(double2);  // up to 2 pairs
     return std::max(std::max(b, bt), bs);
+}
+
+// k_gram_small for npair = 1 (G = A^H B) or 2 (G = A^H B, G2 = A^H B2, one pass
+// over A); requires gram_small_T(prec, p) != 0.
+static bk_status launch_gram_small(int prec, Field A, Field B, Field B2, int npair, const SysPart& p, double* G,
+                                   double* G2, double* partial, int V, cudaStream_t st) {
+    const int T = gram_small_T(prec, p);
+    if (!p.active) return BK_OK;
+    const int nbx = gram_small_nbx(p, V, T, GS_THREADS, npair);
+    dim3 grid(nbx, p.nsys);
+    double2* part = (double2*)partial;
+#define BK_GS(PP, TT) k_gram_small<PP, TT><<<grid, GS_THREADS, 0, st>>>(A, B, B2, npair, p, part, V)
+    if (prec == BK_FP32) {
+        if (T == 3) BK_GS(BK_FP32, 3);
+        else if (T == 4) BK_GS(BK_FP32, 4);
+        else BK_GS(BK_FP32, 6);
+    } else {
+        if (T == 3) BK_GS(BK_FP16, 3);
+        else if (T == 4) BK_GS(BK_FP16, 4);
+        else BK_GS(BK_FP16, 6);
+    }
+#undef BK_GS
+    BK_CUDA_TRY(cudaGetLastError());
+    const int ne = p.coef_off[p.nsys];
+    k_gram_finish_warp<<<(npair * ne + 7) / 8, 256, 0, st>>>(part, npair * ne, nbx, (double2*)G, (double2*)G2, ne);
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}
+
+bk_status launch_gram2(int prec, Field A, Field B, Field B2, const SysPart& p, double* G, double* G2,
+                       double* partial, int V, cudaStream_t st) {
+    if (gram_small_T(prec, p)) return launch_gram_small(prec, A, B, B2, 2, p, G, G2, partial, V, st);
+    const bk_status e = launch_gram(prec, A, B, p, G, partial, V, st);
+    if (e != BK_OK) return e;
+    return launch_gram(prec, A, B2, p, G2, partial, V, st);
 }
 
 bk_status launch_gram(int prec, Field A, Field B, const SysPart& p, double* G, double* partial, int V,
                       cudaStream_t st) {
-    if (const int T = gram_small_T(prec, p)) {
-        if (!p.active) return BK_OK;
-        const int nbx = gram_small_nbx(p, V, T, GS_THREADS);
-        dim3 grid(nbx, p.nsys);
-        double2* part = (double2*)partial;
-        if (prec == BK_FP32) {
-            if (T == 3) k_gram_small<BK_FP32, 3><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
-            else if (T == 4) k_gram_small<BK_FP32, 4><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
-            else k_gram_small<BK_FP32, 6><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
-        } else {
-            if (T == 3) k_gram_small<BK_FP16, 3><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
-            else if (T == 4) k_gram_small<BK_FP16, 4><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
-            else k_gram_small<BK_FP16, 6><<<grid, GS_THREADS, 0, st>>>(A, B, p, part, V);
-        }
-        BK_CUDA_TRY(cudaGetLastError());
-        const int ne = p.coef_off[p.nsys];
-        k_gram_finish_warp<<<(ne + 7) / 8, 256, 0, st>>>(part, ne, nbx, (double2*)G);
-        BK_CUDA_TRY(cudaGetLastError());
-        return BK_OK;
-    }
+    if (gram_small_T(prec, p)) return launch_gram_small(prec, A, B, B, 1, p, G, nullptr, partial, V, st);
     if (gram_tiled_ok(prec, p)) {
         int maxL = 0;
         for (int s = 0; s < p.nsys; ++s) maxL = std::max(maxL, p.col0[s + 1] - p.col0[s]);
@@ -1401,7 +1472,8 @@ bk_status launch_xmy(int prec, Field X, const double* M, const double* c_dev, Fi
 }
 
 // Tiled path: FP32/FP16 blocks with a matrix and every system L <= 96.
-static bk_status launch_genop_tiled(int prec, const GenOp& g, int V, cudaStream_t st, bool& done) {
+static bk_status launch_genop_tiled(int prec, const GenOp& g, int V, cudaStream_t st, bool& done,
+                                    bool* ynorm_done) {
     done = false;
     if (prec == BK_FP64) return BK_OK;
     int maxL = 0;
@@ -1418,6 +1490,7 @@ static bk_status launch_genop_tiled(int prec, const GenOp& g, int V, cudaStream_
         else k_genop_chunk<12><<<grid, 256, 0, st>>>(g, V);
         BK_CUDA_TRY(cudaGetLastError());
         done = true;
+        if (ynorm_done) *ynorm_done = g.ynorm != nullptr;
         return BK_OK;
     }
     if (!g.M) return BK_OK;
@@ -1451,12 +1524,13 @@ static bk_status launch_genop_tiled(int prec, const GenOp& g, int V, cudaStream_
     return BK_OK;
 }
 
-bk_status launch_genop(int prec, const GenOp& g, int V, cudaStream_t st) {
+bk_status launch_genop(int prec, const GenOp& g, int V, cudaStream_t st, bool* ynorm_done) {
+    if (ynorm_done) *ynorm_done = false;
     const int L = g.p.col0[g.p.nsys];
     if (L <= 0) return BK_OK;
     {
         bool done = false;
-        bk_status e = launch_genop_tiled(prec, g, V, st, done);
+        bk_status e = launch_genop_tiled(prec, g, V, st, done, ynorm_done);
         if (e != BK_OK || done) return e;
     }
     // J output columns per thread: each loaded input spinor serves J outputs
