@@ -117,11 +117,13 @@ struct bk_ctx {
     std::vector<cudaEvent_t> events;
     // operator launch shapes chosen by the autotuner, keyed by (prec, residual, ncol)
     struct Shape {
-        int rpt, sx, by;
+        int rpt, sx, by, pipe;
     };
     std::map<long long, Shape> shapes;
     bool autotune = true;
     bool verbose = false;  // BK_VERBOSE=1: one line per solve and per tuning decision on stderr
+    int pipe_only = 0;      // BK_DSLASH_PIPE=1: FP32 operator tuned over the pipelined kernel only
+                            // (default: the plain kernel, faster on every shape measured)
 };
 
 static bool wide(int prec) { return prec == BK_FP64 || prec == BK_DF64; }
@@ -166,6 +168,8 @@ extern "C" bk_status bk_create(const int dims[4], int device, bk_ctx** out) {
         c->autotune = !(e && e[0] == '0');
         const char* v = getenv("BK_VERBOSE");
         c->verbose = v && v[0] == '1';
+        const char* pp = getenv("BK_DSLASH_PIPE");
+        if (pp && pp[0] == '1') c->pipe_only = 1;
     }
     c->device = device;
     bk_status s;
@@ -258,8 +262,22 @@ static bk_status tune_shape(bk_ctx* c, int prec, DslashOp op, cudaStream_t st, b
             for (int threads : {128, 256}) {
                 int by = std::min(threads / sx, ngroups);
                 if (by < 1) by = 1;
-                cands.push_back({rpt, sx, by});
+                cands.push_back({rpt, sx, by, 0});
             }
+        // FP32: the cp.async-pipelined kernel (shared-memory stages per thread)
+        if (prec == BK_FP32 && rpt <= 2)
+            for (int sx : {16, 32})
+                for (int threads : {64, 128}) {
+                    int by = std::min(threads / sx, ngroups);
+                    if (by < 1) by = 1;
+                    cands.push_back({rpt, sx, by, 1});
+                }
+    }
+    if (prec == BK_FP32) {
+        std::vector<bk_ctx::Shape> keep;
+        for (const auto& cd : cands)
+            if (cd.pipe == c->pipe_only) keep.push_back(cd);
+        cands.swap(keep);
     }
     cudaEvent_t e0, e1;
     BK_CUDA_TRY(cudaEventCreate(&e0));
@@ -270,6 +288,7 @@ static bk_status tune_shape(bk_ctx* c, int prec, DslashOp op, cudaStream_t st, b
         op.rpt = cd.rpt;
         op.site_block = cd.sx;
         op.col_block = cd.by;
+        op.pipe = cd.pipe;
         BK_TRY(launch_dslash(prec, op, st));
         BK_CUDA_TRY(cudaEventRecord(e0, st));
         BK_TRY(launch_dslash(prec, op, st));
@@ -305,6 +324,7 @@ static bk_status dslash_fields(bk_ctx* c, int prec, const double* kappa, Field x
     op.site_block = 0;
     op.col_block = 0;
     op.rpt = 0;
+    op.pipe = 0;
     if (c->autotune && ncol <= BK_MAX_COLS) {
         const long long key = ((long long)prec << 40) | ((long long)(residual != 0) << 36) | ncol;
         auto it = c->shapes.find(key);
@@ -313,12 +333,13 @@ static bk_status dslash_fields(bk_ctx* c, int prec, const double* kappa, Field x
             BK_TRY(tune_shape(c, prec, op, st, sh));
             it = c->shapes.emplace(key, sh).first;
             if (c->verbose)
-                fprintf(stderr, "[bkrylov] tuned operator prec=%d residual=%d ncol=%d: rpt=%d sites=%d groups=%d\n", prec,
-                        residual, ncol, sh.rpt, sh.sx, sh.by);
+                fprintf(stderr, "[bkrylov] tuned operator prec=%d residual=%d ncol=%d: rpt=%d sites=%d groups=%d pipe=%d\n",
+                        prec, residual, ncol, sh.rpt, sh.sx, sh.by, sh.pipe);
         }
         op.rpt = it->second.rpt;
         op.site_block = it->second.sx;
         op.col_block = it->second.by;
+        op.pipe = it->second.pipe;
     }
     return launch_dslash(prec, op, st);
 }

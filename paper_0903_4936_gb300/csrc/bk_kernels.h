@@ -24,6 +24,7 @@ struct DslashOp {
     int site_block;        // launch shape: sites per thread block (0 = default)
     int col_block;         // column groups per thread block (0 = default)
     int rpt;               // columns per thread: 1, 2 or 4 (0 = 1; FP64 always 1)
+    int pipe;              // FP32 only: 1 = cp.async-pipelined kernel (rpt 1 or 2)
 };
 bk_status launch_dslash(int prec, const DslashOp& op, cudaStream_t st);
 

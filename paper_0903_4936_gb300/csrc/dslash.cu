@@ -307,6 +307,195 @@ __global__ void __launch_bounds__(dslash_max_threads<P, RPT>()) k_dslash(const _
     }
 }
 
+// ----------------------------------------------------------------- pipelined FP32 variant
+//
+// Same arithmetic as k_dslash<FP32, RPT>, with the memory latency moved off
+// the registers: while a thread computes hop h, its copies for hop h + 1 (the
+// neighbour spinors of its RPT columns and the 3x3 link) are in flight as
+// cp.async transfers into the thread's own shared-memory slots (two stages).
+// Hop 8 is the site's own spinor (clover term and axpy).  Each thread reads
+// only the slots it filled, so the only synchronisation is cp.async.wait_group.
+// Shared memory per thread: 2 stages x (RPT x 96 + 72) bytes.
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int RPT>
+constexpr int pipe_smem_per_thread() { return 2 * (RPT * 96 + 72); }
+
+template <int MU, int S>
+__device__ __forceinline__ void hop_apply(const cx<float> (&u)[9], const cx<float> (&q)[12], cx<float> (&acc)[12]) {
+    cx<float> h[6], w[6];
+    project<MU, S>(q, h);
+    if constexpr (S < 0) {  // forward: U h
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                cx<float> t = u[3 * i] * h[3 * hh];
+                cmac(t, u[3 * i + 1], h[3 * hh + 1]);
+                cmac(t, u[3 * i + 2], h[3 * hh + 2]);
+                w[3 * hh + i] = t;
+            }
+    } else {  // backward: U^+ h
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                cx<float> t = mk(0.f, 0.f);
+                cjmac(t, u[i], h[3 * hh]);
+                cjmac(t, u[3 + i], h[3 * hh + 1]);
+                cjmac(t, u[6 + i], h[3 * hh + 2]);
+                w[3 * hh + i] = t;
+            }
+    }
+    reconstruct<MU, S>(w, acc);
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(256) k_dslash_pipe(const __grid_constant__ DArgs<BK_FP32> a) {
+    extern __shared__ float4 pipe_smem[];
+    const int tid = threadIdx.x, NT = blockDim.x;
+    float4* sp = pipe_smem;                                   // [stage][r][chunk][NT]
+    float2* sl = reinterpret_cast<float2*>(pipe_smem + 2 * RPT * 6 * NT);  // [stage][9][NT]
+    const int sblk = a.groups_fast ? blockIdx.y : blockIdx.x;
+    const int gblk = a.groups_fast ? blockIdx.x : blockIdx.y;
+    const int s = sblk * a.SX + (tid % a.SX);
+    const int g = gblk * (NT / a.SX) + tid / a.SX;
+    const int cl0 = g * RPT;
+    if (s >= a.V || cl0 >= a.ncol) return;
+    const int nr = min(RPT, a.ncol - cl0);
+    const int c0 = a.col0 + cl0;
+    int nb[9];  // hop h: mu = h / 2, forward (even h) or backward; hop 8 = the site itself
+    {
+        int r = s, co[4];
+        co[0] = r % a.L[0];
+        r /= a.L[0];
+        co[1] = r % a.L[1];
+        r /= a.L[1];
+        co[2] = r % a.L[2];
+        co[3] = r / a.L[2];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const int Lm = a.L[mu], sm = a.st[mu];
+            nb[2 * mu] = co[mu] == Lm - 1 ? s - (Lm - 1) * sm : s + sm;
+            nb[2 * mu + 1] = co[mu] == 0 ? s + (Lm - 1) * sm : s - sm;
+        }
+        nb[8] = s;
+    }
+    const float4* X = (const float4*)a.x.data;
+    const long long cs = a.x.cstride;
+    // copies of hop h into stage st: spinors at nb[h]; the link U_mu(n) for a
+    // forward hop, U_mu(n - mu) for a backward one (none for hop 8)
+    auto issue = [&](int h, int stg) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+            if (r < nr)
+#pragma unroll
+                for (int k = 0; k < 6; ++k)
+                    cp_async16(sp + ((stg * RPT + r) * 6 + k) * NT + tid,
+                               X + (size_t)(c0 + r) * cs + (size_t)k * a.V + nb[h]);
+        if (h < 8) {
+            const int mu = h >> 1, ls = (h & 1) ? nb[h] : s;
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                cp_async8(sl + (stg * 9 + k) * NT + tid, a.U + (size_t)(mu * 9 + k) * a.V + ls);
+        }
+        cp_async_commit();
+    };
+    auto spinor = [&](int stg, int r, cx<float> (&q)[12]) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 v = sp[((stg * RPT + r) * 6 + k) * NT + tid];
+            q[2 * k] = mk(v.x, v.y);
+            q[2 * k + 1] = mk(v.z, v.w);
+        }
+    };
+    cx<float> acc[RPT][12];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[r][k] = mk(0.f, 0.f);
+    issue(0, 0);
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+        issue(h + 1, (h + 1) & 1);
+        cp_async_wait<1>();  // this thread's copies of hop h have landed
+        const int stg = h & 1;
+        cx<float> u[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float2 v = sl[(stg * 9 + k) * NT + tid];
+            u[k] = mk(v.x, v.y);
+        }
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            if (r < nr) {
+                cx<float> q[12];
+                spinor(stg, r, q);
+                switch (h) {
+                    case 0: hop_apply<0, -1>(u, q, acc[r]); break;
+                    case 1: hop_apply<0, +1>(u, q, acc[r]); break;
+                    case 2: hop_apply<1, -1>(u, q, acc[r]); break;
+                    case 3: hop_apply<1, +1>(u, q, acc[r]); break;
+                    case 4: hop_apply<2, -1>(u, q, acc[r]); break;
+                    case 5: hop_apply<2, +1>(u, q, acc[r]); break;
+                    case 6: hop_apply<3, -1>(u, q, acc[r]); break;
+                    default: hop_apply<3, +1>(u, q, acc[r]); break;
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();  // hop 8: the site's own spinors, stage 0
+    // clover: the chiral blocks act on u + l (block 0) and u - l (block 1)
+#pragma unroll
+    for (int blk = 0; blk < 2; ++blk) {
+        float m[36];
+        load_clov_block(a.C, blk, s, a.V, m);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            if (r < nr) {
+                cx<float> q[12], v[6], yv[6];
+                spinor(0, r, q);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) v[k] = blk == 0 ? q[k] + q[k + 6] : q[k] - q[k + 6];
+                herm6(m, v, yv);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    acc[r][k] = acc[r][k] + yv[k];
+                    acc[r][k + 6] = blk == 0 ? acc[r][k + 6] + yv[k] : acc[r][k + 6] - yv[k];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        if (r < nr) {
+            cx<float> q[12], out[12];
+            spinor(0, r, q);
+            const float kap = (float)a.kappa[cl0 + r];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) out[k] = q[k] - kap * acc[r][k];
+            if (a.residual) {
+                cx<float> bb[12];
+                load_spinor<BK_FP32>(a.b, c0 + r, s, bb);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) out[k] = bb[k] - out[k];
+            }
+            store_spinor<BK_FP32>(a.y, c0 + r, s, out);
+        }
+    }
+}
+
 template <int P>
 bk_status dslash_impl(const DslashOp& op, cudaStream_t st) {
     if (op.ncol <= 0) return BK_OK;
@@ -358,6 +547,23 @@ bk_status dslash_impl(const DslashOp& op, cudaStream_t st) {
     const int nsb = (op.V + SX - 1) / SX, ngb = (ngroups + BY - 1) / BY;
     a.groups_fast = nsb <= 65535 ? 1 : 0;
     dim3 grid = a.groups_fast ? dim3(ngb, nsb) : dim3(nsb, ngb);
+    if constexpr (P == BK_FP32) {
+        if (op.pipe && rpt <= 2) {
+            const int nt = SX * BY;
+            const size_t smem = (size_t)nt * (rpt == 2 ? pipe_smem_per_thread<2>() : pipe_smem_per_thread<1>());
+            if (rpt == 2) {
+                BK_CUDA_TRY(cudaFuncSetAttribute(k_dslash_pipe<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+                k_dslash_pipe<2><<<grid, nt, smem, st>>>(a);
+            } else {
+                BK_CUDA_TRY(cudaFuncSetAttribute(k_dslash_pipe<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+                k_dslash_pipe<1><<<grid, nt, smem, st>>>(a);
+            }
+            BK_CUDA_TRY(cudaGetLastError());
+            return BK_OK;
+        }
+    }
     if constexpr (P == BK_FP64 || P == BK_DF64) {
         k_dslash<P, 1><<<grid, SX * BY, 0, st>>>(a);
     } else {

@@ -172,3 +172,23 @@ def test_df64_operator_tracks_fp64_where_fp32_cannot():
     assert np.linalg.norm(r64) < 2e-9 * nb
     assert np.linalg.norm(rdd - r64) < 1e-3 * np.linalg.norm(r64)
     assert np.linalg.norm(r32 - r64) > 10 * np.linalg.norm(r64)
+
+
+@pytest.mark.parametrize("dims,L", [((4, 4, 4, 4), 12), ((2, 4, 2, 6), 5), ((3, 5, 4, 6), 1), ((8, 8, 8, 16), 13)])
+def test_dslash_pipelined_kernel(monkeypatch, dims, L):
+    """The cp.async-pipelined FP32 operator (selected for every FP32 launch
+    with BK_DSLASH_PIPE=1) against the oracle, and as the inner operator of a
+    mixed solve; odd L leaves a ragged two-column group."""
+    import paper_0903_4936_gb300 as bk
+    monkeypatch.setenv("BK_DSLASH_PIPE", "1")
+    lat, U = _lat(dims, 0.5, 300 + L)
+    X = synth.gaussian_sources(dims, L, 8)
+    kappa = [0.115 + 0.001 * j for j in range(L)]
+    Y = lat.dslash(torch.from_numpy(X).cuda(), kappa, "fp32").cpu().numpy()
+    assert _rel(Y, dirac.apply_dirac(U, X, np.array(kappa), 1.0)) < TOL["fp32"]
+    if dims == (4, 4, 4, 4):
+        B = torch.from_numpy(synth.z4_noise(dims, L, 9)).cuda()
+        Xs, info = lat.block_solve(B, 0.12, method="bicgstab", prec="fp32", tol=1e-10, maxiter=1000)
+        assert info["converged"] == 1 and info["true_res_max"] <= 1e-10
+        R = B.cpu().numpy() - dirac.apply_dirac(U, Xs.cpu().numpy(), 0.12, 1.0)
+        assert np.linalg.norm(R) <= 1e-10 * np.linalg.norm(B.cpu().numpy()) * np.sqrt(L)
