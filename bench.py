@@ -42,6 +42,16 @@ WORKLOADS = {
                     "with per-iteration Cholesky basis of P, FP64 residual replacement (delta 0.03), FP64 true "
                     "residual <= 1e-10 for every column; FP64 comparison: the paper's plain FP64 block BiCGGR "
                     "per case (one block of L columns), same true residual"),
+    "c4": dict(dims=(24, 24, 24, 48), eps=0.5, csw=1.0, gauge_seed=1004, prec="fp32", method="bicgstab",
+               block=6, delta=0.03, e2e=False, distinct_sources=True,
+               e2e_note="host-buffer pass not run: its staging copies of B and X (2 x 25 GB) do not fit beside "
+                        "the solve's 250 GB on the device",
+               cases=list(zip((0.120, 0.122, 0.124, 0.126, 0.128, 0.130), (4, 12, 12, 24, 48, 96), ["z4"] * 6)),
+               desc="24^3x48 clover Wilson-Dirac, random SU(3) links eps=0.5, c_SW=1.0: 6 systems, kappa "
+                    "{0.120,...,0.130} with L {4,12,12,24,48,96} Z4 noise = 196 right-hand sides; mixed: one "
+                    "batched block BiCGSTAB solve over 33 systems of at most 6 columns, FP32 inner iterations, "
+                    "FP64 residual replacement (delta 0.03), FP64 true residual <= 1e-10 for every column; FP64 "
+                    "comparison: the paper's plain FP64 block BiCGGR per system"),
     "c3-12": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp32", method="bicgstab",
                   cases=[(0.125, 12, "point")],
                   desc="16^3x32, eps=0.5, c_SW=1.0, kappa=0.125, L=12 point sources; block BiCGSTAB, "
@@ -251,25 +261,36 @@ def gb300_arm(args, wl, rank, world, local_rank):
     lat.upload_gauge(U)
     lat.build_clover(wl["csw"])
     V = lat.V
-    cases = []
-    for (kappa, L, kind) in wl["cases"]:
-        B = sources(dims, L, kind, replica_seed(L, rank))
-        cases.append(dict(kappa=kappa, L=L, kind=kind, B=torch.from_numpy(B).to(dev),
-                          Bh=torch.from_numpy(B).pin_memory()))
     del U
-    # batched mode: every case split into systems of at most `block` columns,
-    # all systems solved together
+    with_e2e = wl.get("e2e", True)
+    cases = []
     batch = None
     if wl.get("block"):
+        # batched mode: all cases' sources in one device block (each case a
+        # view of its columns), every case split into systems of at most
+        # `block` columns, all systems solved together.  Sources go to the
+        # device one case at a time, so the host holds at most one case.
         blk = wl["block"]
+        Lt = sum(L for (_, L, _) in wl["cases"])
+        Ball = torch.empty((Lt,) + tuple(reversed(dims)) + (4, 3), dtype=torch.complex128, device=dev)
         kap_s, L_s, owner = [], [], []
-        for ci, c in enumerate(cases):
-            for c0 in range(0, c["L"], blk):
-                kap_s.append(c["kappa"])
-                L_s.append(min(blk, c["L"] - c0))
+        c0 = 0
+        for ci, (kappa, L, kind) in enumerate(wl["cases"]):
+            seed = replica_seed(L, rank) + (100 * ci if wl.get("distinct_sources") else 0)
+            Ball[c0:c0 + L].copy_(torch.from_numpy(sources(dims, L, kind, seed)))
+            cases.append(dict(kappa=kappa, L=L, kind=kind, B=Ball[c0:c0 + L]))
+            for j0 in range(0, L, blk):
+                kap_s.append(kappa)
+                L_s.append(min(blk, L - j0))
                 owner.append(ci)
-        Ball = torch.cat([c["B"] for c in cases], dim=0).contiguous()
-        batch = dict(kappas=kap_s, Ls=L_s, owner=owner, B=Ball, Bh=Ball.cpu().pin_memory())
+            c0 += L
+        batch = dict(kappas=kap_s, Ls=L_s, owner=owner, B=Ball,
+                     Bh=Ball.cpu().pin_memory() if with_e2e else None)
+    else:
+        for (kappa, L, kind) in wl["cases"]:
+            B = sources(dims, L, kind, replica_seed(L, rank))
+            cases.append(dict(kappa=kappa, L=L, kind=kind, B=torch.from_numpy(B).to(dev),
+                              Bh=torch.from_numpy(B).pin_memory()))
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     def step(record, host=False):
@@ -350,17 +371,20 @@ def gb300_arm(args, wl, rank, world, local_rank):
     # B copied in and X copied out inside every call.
     e2e_ms = 0.0
     h2d = d2h = 0
-    for _ in range(max(1, min(args.steps, 3))):
-        flush.fill_(1)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        t = step(False, host=True)
-        torch.cuda.synchronize()
-        e2e_ms += (time.perf_counter() - t0) * 1e3
     n_e2e = max(1, min(args.steps, 3))
-    for c in cases:
-        h2d += c["B"].numel() * 16
-        d2h += c["B"].numel() * 16
+    if with_e2e:
+        for _ in range(n_e2e):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            t = step(False, host=True)
+            torch.cuda.synchronize()
+            e2e_ms += (time.perf_counter() - t0) * 1e3
+        for c in cases:
+            h2d += c["B"].numel() * 16
+            d2h += c["B"].numel() * 16
+    else:
+        e2e_ms = None
     batched = None
     if batch is not None:
         batched = dict(systems=len(batch["Ls"]), block=wl["block"], columns=sum(batch["Ls"]))
@@ -387,7 +411,8 @@ def gb300_arm(args, wl, rank, world, local_rank):
             per[f"k{c['kappa']}_L{c['L']}"] = dict(ms=round(t, 1), iterations=info["iterations"])
         fp64 = dict(method="block BiCGGR, FP64", fp64_rhs_per_s=rhs / (ms / 1e3), cases=per)
 
-    return dict(total_ms=total_ms, per_step_ms=per_step_ms, agg=agg, clocks=clk, e2e_ms=e2e_ms / n_e2e,
+    return dict(total_ms=total_ms, per_step_ms=per_step_ms, agg=agg, clocks=clk,
+                e2e_ms=e2e_ms / n_e2e if e2e_ms is not None else None,
                 h2d=h2d, d2h=d2h, fp64=fp64, V=V, batched=batched,
                 iters={f"k{c['kappa']}_L{c['L']}": c["last_info"]["iterations"] for c in cases},
                 true_res={f"k{c['kappa']}_L{c['L']}": c["last_info"]["true_res_max"] for c in cases},
@@ -470,8 +495,9 @@ def main():
                      "unit": "GB/s", "frac": (achieved / hbm) if achieved else None, "peak_kind": peak_kind,
                      "traffic": traffic, "launches": agg["n_inner"],
                      "avg_launch_us": agg["t_inner"] / agg["n_inner"] * 1e3 if agg["n_inner"] else None},
-        "e2e": {"value": world * total_rhs_per_step / (r["e2e_ms"] / 1e3), "unit": "RHS/s",
-                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+        "e2e": ({"value": world * total_rhs_per_step / (r["e2e_ms"] / 1e3), "unit": "RHS/s",
+                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]} if r["e2e_ms"] is not None else
+                {"value": None, "unit": "RHS/s", "skipped": wl.get("e2e_note")}),
         "gpu_launches": int(agg["launches"]),
         "clocks": r["clocks"],
         "iterations": r["iters"], "reliable_updates": r["rel_updates"], "true_res_max": r["true_res"],
@@ -496,7 +522,7 @@ def main():
 
 # Iteration counts of the GPU solver per workload's first case, used to turn the
 # oracle's seconds per iteration into RHS/s on the reference arm.
-GPU_ITERS_HINT = {"c3": 42, "c3-12": 57, "c3-48": 281, "c2": 122}
+GPU_ITERS_HINT = {"c3": 42, "c4": 45, "c3-12": 57, "c3-48": 281, "c2": 122}
 
 if __name__ == "__main__":
     main()

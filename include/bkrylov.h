@@ -276,7 +276,7 @@ bk_status bk_block_solve(bk_ctx* ctx, const bk_solve_params* params, double kapp
  * multi-RHS operator launch serves every system per step (each link and
  * clover block is read once for all columns); Gram matrices, L x L solves and
  * block updates are block-diagonal per system; converged systems are frozen.
- * info: array of nsys entries.  nsys <= 32.                               */
+ * info: array of nsys entries.  nsys <= 64.                               */
 bk_status bk_block_solve_batched(bk_ctx* ctx, const bk_solve_params* params, int nsys,
                                  const double* kappa, const int* Ls, const double* B, double* X,
                                  bk_solve_info* info, void* stream);

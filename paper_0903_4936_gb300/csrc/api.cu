@@ -621,7 +621,7 @@ struct Solve {
 
     // Column ranges [c0, c0 + n) covered by maximal runs of consecutive
     // systems whose bit is set in mask (systems own consecutive columns).
-    std::vector<std::pair<int, int>> col_runs(unsigned mask) const {
+    std::vector<std::pair<int, int>> col_runs(sysmask mask) const {
         std::vector<std::pair<int, int>> r;
         for (int s = 0; s < nsys;) {
             if (!((mask >> s) & 1u)) {
@@ -714,7 +714,7 @@ struct Solve {
     }
 
     // squared FP64 norms of the columns of f owned by the systems in mask, into rn
-    bk_status norms_runs(int prec, Field f, unsigned mask) {
+    bk_status norms_runs(int prec, Field f, sysmask mask) {
         for (const auto& cr : col_runs(mask)) {
             Field a[1] = {field_cols(f, cr.first)};
             BK_TRY(coldot(prec, 1, a, a, rn + 2 * (size_t)cr.first, cr.second));
@@ -738,9 +738,9 @@ struct Solve {
     // rprec: BK_FP64 or BK_DF64 arithmetic for B - A X; accum = false recomputes
     // the residual of the current X64 (Xlo already folded in).
     bk_status reliable_update(const std::vector<int>& sys, int rprec, bool accum) {
-        unsigned mask = 0;
+        sysmask mask = 0;
         for (int s : sys) {
-            mask |= 1u << s;
+            mask |= 1ull << s;
             mv64[s]++;
             if (accum) nrel[s]++;
         }
@@ -947,9 +947,9 @@ struct Solve {
     }
 
     void update_active() {
-        unsigned a = 0;
+        sysmask a = 0;
         for (int s = 0; s < nsys; ++s)
-            if (done[s] == 0) a |= 1u << s;
+            if (done[s] == 0) a |= 1ull << s;
         part.active = a;
     }
 
@@ -1115,7 +1115,7 @@ struct Solve {
                 g.skip = info_a;
                 BK_TRY(genop(g));
             }
-            const unsigned before = part.active;
+            const sysmask before = part.active;
             BK_TRY(check(k));
             // systems that stopped keep their state; the rest continue
             part.active &= before;
@@ -1239,7 +1239,7 @@ struct Solve {
                 g.ynorm = ynorm;
                 BK_TRY(genop(g, &norms_fused));
             }
-            const unsigned before = part.active;
+            const sysmask before = part.active;
             BK_TRY(check(k));
             norms_fused = false;
             part.active &= before;
@@ -1272,13 +1272,13 @@ struct Solve {
     bk_status finish(double* Xc) {
         // systems whose final FP64 true residual is not known yet: all but those
         // that converged on an FP64 residual replacement (mixed precision)
-        unsigned need = 0;
+        sysmask need = 0;
         for (int s = 0; s < nsys; ++s)
             if (!res_known[s]) {
-                need |= 1u << s;
+                need |= 1ull << s;
                 mv64[s]++;
             }
-        part.active = nsys >= 32 ? 0xffffffffu : ((1u << nsys) - 1u);
+        part.active = all_systems(nsys);
         for (const auto& cr : col_runs(need)) {
             if (mixed) {
                 dim3 grid((V + 127) / 128, cr.second);
@@ -1305,7 +1305,7 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
                             const double* B, double* X, bk_solve_info* info, void* stream) {
     auto t0 = std::chrono::steady_clock::now();
     BK_CHECK_ARG(c && prm && kappa && Ls && B && X && info, "null argument");
-    BK_CHECK_ARG(nsys >= 1 && nsys <= BK_MAX_SYS, "nsys must be in [1, 32]");
+    BK_CHECK_ARG(nsys >= 1 && nsys <= BK_MAX_SYS, "nsys must be in [1, 64]");
     BK_CHECK_ARG(prm->method == BK_BICGSTAB || prm->method == BK_BICGGR, "unknown method");
     BK_CHECK_ARG(valid_prec(prm->prec), "unknown precision");
     BK_CHECK_ARG(prm->tol > 0 && prm->maxiter >= 0, "tol must be > 0 and maxiter >= 0");

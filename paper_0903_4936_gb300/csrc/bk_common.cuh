@@ -243,5 +243,5 @@ void bk_set_error(const char* fmt, ...);
 
 // Maximum columns handled by one operator launch (kernel-argument kappa list).
 #define BK_MAX_COLS 256
-// Maximum number of systems of a batched solve.
-#define BK_MAX_SYS 32
+// Maximum number of systems of a batched solve (one bit each in a 64-bit mask).
+#define BK_MAX_SYS 64

@@ -40,11 +40,16 @@ bk_status launch_gamma5_canon(const double* X, double* Y, long long nsites_cols,
 // Partition of the columns into independent systems: system s owns columns
 // [col0[s], col0[s+1]).  coef_off[s] = offset (in complex entries) of system
 // s's L_s x L_s matrix inside a packed coefficient array.
+// one bit per system of a batched solve (BK_MAX_SYS <= 64)
+typedef unsigned long long sysmask;
+// every system of an nsys-system partition
+inline sysmask all_systems(int nsys) { return nsys >= 64 ? ~0ull : ((1ull << nsys) - 1ull); }
+
 struct SysPart {
     int nsys;
     int col0[BK_MAX_SYS + 1];
     int coef_off[BK_MAX_SYS + 1];
-    unsigned active;       // bit s set: system s is still iterating
+    sysmask active;        // bit s set: system s is still iterating
 };
 SysPart make_part(int nsys, const int* Ls);
 SysPart single_part(int L);

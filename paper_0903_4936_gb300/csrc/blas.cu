@@ -24,7 +24,7 @@ SysPart make_part(int nsys, const int* Ls) {
         p.col0[s] = p.col0[nsys];
         p.coef_off[s] = p.coef_off[nsys];
     }
-    p.active = nsys >= 32 ? 0xffffffffu : ((1u << nsys) - 1u);
+    p.active = all_systems(nsys);
     return p;
 }
 

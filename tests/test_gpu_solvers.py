@@ -75,6 +75,25 @@ def test_fp64_iterates_match_oracle(c1, method):
     assert _dev(X.cpu().numpy(), dense.from_columns(Xo, dims)) < 1e-9
 
 
+def test_fp64_cholesky_basis_keeps_the_papers_iterates(c1):
+    """Block BiCGSTAB with P replaced by P T^-1 (P^H P = T^H T) before every
+    V = A P, forced on in FP64: alpha and beta absorb T, so the residual
+    history is the oracle's plain block BiCGSTAB (the paper's algorithm)
+    iterate for iterate."""
+    dims, lat, U, B, Xd, A = c1
+    Bg = synth.gaussian_sources(dims, 6, 51)
+    Rt = synth.gaussian_sources(dims, 6, 52)
+    X, info = lat.block_solve(torch.from_numpy(Bg).cuda(), 0.12, method="bicgstab", prec="fp64", tol=1e-12,
+                              maxiter=500, history=True, rtilde=torch.from_numpy(Rt).cuda(), orth=True)
+    Xo, io = solvers.block_bicgstab(A, dense.to_columns(Bg), 1e-12, 500, Rt=dense.to_columns(Rt))
+    assert abs(info["iterations"] - io["iterations"]) <= 2
+    ho = np.asarray(io["history"])
+    n = int(np.argmax(ho < 1e-8)) if np.any(ho < 1e-8) else len(ho)
+    assert n >= 10
+    assert np.allclose(np.array(info["history"][:n]), ho[:n], rtol=1e-6)
+    assert _dev(X.cpu().numpy(), dense.from_columns(Xo, dims)) < 1e-9
+
+
 @pytest.mark.parametrize("prec", ["fp32"])
 @pytest.mark.parametrize("method", ["bicggr", "bicgstab"])
 def test_mixed_solve_matches_dense_lu(c1, prec, method):
@@ -147,6 +166,26 @@ def test_batched_systems_match_individual(c1, kappas, Ls):
         D = dense.dense_matrix(U, k, 1.0)
         ref = dense.from_columns(np.linalg.solve(D, dense.to_columns(Bs[c0:c0 + L])), dims)
         assert infos[s]["converged"] == 1 and infos[s]["true_res_max"] <= 1e-10
+        assert _dev(X[c0:c0 + L], ref) <= 1e-8
+        c0 += L
+
+
+def test_batched_more_than_32_systems(c1):
+    """36 systems (24 of one column, 12 of two) in one mixed-precision solve:
+    the 64-bit system mask, systems converging at different steps, each
+    system against its dense solution."""
+    dims, lat, U, B, Xd, A = c1
+    Ls = [1] * 24 + [2] * 12
+    kappas = [0.11 if s % 2 else 0.12 for s in range(len(Ls))]
+    Bs = synth.z4_noise(dims, sum(Ls), 78)
+    X, infos = lat.block_solve_batched(torch.from_numpy(Bs).cuda(), kappas, Ls, method="bicgstab", prec="fp32",
+                                       tol=1e-10, maxiter=1000)
+    X = X.cpu().numpy()
+    lu = {k: np.linalg.inv(dense.dense_matrix(U, k, 1.0)) for k in set(kappas)}
+    c0 = 0
+    for s, (k, L) in enumerate(zip(kappas, Ls)):
+        assert infos[s]["converged"] == 1 and infos[s]["true_res_max"] <= 1e-10
+        ref = dense.from_columns(lu[k] @ dense.to_columns(Bs[c0:c0 + L]), dims)
         assert _dev(X[c0:c0 + L], ref) <= 1e-8
         c0 += L
 
