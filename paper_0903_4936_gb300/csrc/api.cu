@@ -459,6 +459,7 @@ namespace {
 //   mode 0 (BiCGGR):   zeta = sum_j d0_j / sum_j d1_j  (d0 = W^H R, d1 = W^H W)
 //   mode 1 (BiCGSTAB): zeta = sum_j d0_j / sum_j d1_j  (d0 = Z^H T, d1 = Z^H Z)
 // writes zeta, -zeta, 1/zeta; zbad[s] = 1 when zeta is not finite or zero.
+// one thread per system: launched with BK_MAX_SYS threads
 __global__ void k_scalars(const double2* __restrict__ dots, int Lt, SysPart p, double2* zeta, double2* mzeta,
                           double2* izeta, int* zbad) {
     const int s = threadIdx.x;
@@ -679,7 +680,7 @@ struct Solve {
     }
     bk_status scalars() {
         launches += 1;
-        k_scalars<<<1, 32, 0, st>>>((const double2*)dots, Lt, part, (double2*)zeta, (double2*)mzeta,
+        k_scalars<<<1, BK_MAX_SYS, 0, st>>>((const double2*)dots, Lt, part, (double2*)zeta, (double2*)mzeta,
                                     (double2*)izeta, zbad);
         BK_CUDA_TRY(cudaGetLastError());
         return BK_OK;
