@@ -93,6 +93,10 @@ bk_status bk_upload_gauge(bk_ctx* ctx, const double* U, int U_on_device, void* s
  * csw = 0 gives the plain Wilson operator.  Errors: NO_GAUGE, CUDA.        */
 bk_status bk_build_clover(bk_ctx* ctx, double csw, void* stream);
 
+/* bk_build_clover on the legacy default stream, returning once the clover
+ * term is built.                                                          */
+bk_status bk_set_clover(bk_ctx* ctx, double csw);
+
 /* Bytes of an L-column device-layout block of precision prec.             */
 size_t bk_field_bytes(const bk_ctx* ctx, int L, bk_prec prec);
 
@@ -111,9 +115,23 @@ bk_status bk_dslash_dev(bk_ctx* ctx, const double* kappa, const void* Xd, void* 
                         bk_prec prec, void* stream);
 
 /* Same operator on canonical FP64 device blocks X -> Y, computed in prec:
- * packs X, applies the operator, unpacks into Y (library workspace).      */
+ * packs X, applies the operator, unpacks into Y (library workspace).
+ * Both operator calls accept BK_DF64 (blocks in the BK_FP64 layout).      */
 bk_status bk_dslash(bk_ctx* ctx, const double* kappa, const double* X, double* Y, int L,
                     bk_prec prec, void* stream);
+
+/* Which layout the blocks of bk_dslash_multi are in.                      */
+typedef enum bk_layout {
+    BK_LAYOUT_CANONICAL = 0, /* canonical FP64 device blocks (as bk_dslash)   */
+    BK_LAYOUT_DEVICE = 1     /* device-layout blocks in prec (as bk_dslash_dev) */
+} bk_layout;
+
+/* The multi-RHS operator of Eq. (wd-op) with one hopping parameter for all L
+ * columns: Y_i = X_i - kappa (H X_i + C X_i).  Equivalent to bk_dslash
+ * (layout CANONICAL) or bk_dslash_dev (layout DEVICE) with kappa repeated.
+ * Errors: NO_GAUGE, INVALID_ARG, CUDA.                                    */
+bk_status bk_dslash_multi(bk_ctx* ctx, double kappa, const void* X, void* Y, int L, bk_prec prec,
+                          bk_layout layout, void* stream);
 
 /* gamma_5 (as printed in Section 2) applied to every column of a canonical
  * FP64 device block, out of place (Y may equal X).                        */
@@ -122,9 +140,10 @@ bk_status bk_gamma5(bk_ctx* ctx, const double* X, double* Y, int L, void* stream
 /* Block inner product (Section 3, the L x L matrices R~_0^H V_k etc.):
  *     G[i][j] = sum_{n, alpha, a} conj(A_i(n,alpha,a)) B_j(n,alpha,a)
  * for device-layout blocks A, B of L columns in prec.  G: device array of
- * L*L complex FP64 {re, im}, row-major.  Products and per-thread partial sums
- * are in the arithmetic precision of prec; the sum across threads and blocks
- * is FP64.  Uses library workspace for the per-block partial sums.
+ * L*L complex FP64 {re, im}, row-major.  Products, per-thread partial sums
+ * and the sum across one warp are in the arithmetic precision of prec; sums
+ * across warps and thread blocks are FP64.  Uses library workspace for the
+ * per-block partial sums.
  * Errors: INVALID_ARG, CUDA.                                              */
 bk_status bk_block_gram(bk_ctx* ctx, const void* A, const void* B, int L, bk_prec prec,
                         double* G, void* stream);
@@ -238,7 +257,7 @@ typedef struct bk_solve_info {
     int matvecs;           /* operator applications in the inner precision    */
     int matvecs_fp64;      /* FP64-class operator applications (residuals, in
                               FP64 or double-float arithmetic)                */
-    int reliable_updates;  /* FP64 residual replacements                      */
+    int reliable_updates;  /* residual replacements (mixed precision)         */
     int restarts;          /* mixed precision: low-precision cycles discarded
                               and restarted from the last FP64 residual
                               (breakdown, non-finite or runaway residual)     */
@@ -273,10 +292,11 @@ bk_status bk_block_solve(bk_ctx* ctx, const bk_solve_params* params, double kapp
 /* Several independent systems on the same gauge field, solved together:
  * system s has hopping parameter kappa[s] and Ls[s] columns; their columns
  * are concatenated in B and X (canonical layout, sum(Ls) columns).  One
- * multi-RHS operator launch serves every system per step (each link and
- * clover block is read once for all columns); Gram matrices, L x L solves and
- * block updates are block-diagonal per system; converged systems are frozen.
- * info: array of nsys entries.  nsys <= 64.                               */
+ * multi-RHS operator launch per step serves every consecutive run of systems
+ * still iterating (one launch while all are; each link and clover block is
+ * read once for all of its columns); Gram matrices, L x L solves and block
+ * updates are block-diagonal per system; converged systems drop out of every
+ * launch.  info: array of nsys entries.  nsys <= 64.                      */
 bk_status bk_block_solve_batched(bk_ctx* ctx, const bk_solve_params* params, int nsys,
                                  const double* kappa, const int* Ls, const double* B, double* X,
                                  bk_solve_info* info, void* stream);

@@ -99,6 +99,11 @@ class Lattice:
         check(lib().bk_build_clover(self._h, float(csw), _stream_ptr(self.device)), "bk_build_clover")
         self.csw = float(csw)
 
+    def set_clover(self, csw: float):
+        """build_clover on the default stream, synchronously (bk_set_clover)."""
+        check(lib().bk_set_clover(self._h, float(csw)), "bk_set_clover")
+        self.csw = float(csw)
+
     # ------------------------------------------------------------ operator
     def _kappas(self, kappa, L):
         if isinstance(kappa, (int, float)):
@@ -116,6 +121,25 @@ class Lattice:
         Y = torch.empty_like(X) if out is None else out
         check(lib().bk_dslash(self._h, self._kappas(kappa, L), _ptr(X), _ptr(Y), L, _prec(prec),
                               _stream_ptr(self.device)), "bk_dslash")
+        return Y
+
+    def dslash_multi(self, X: torch.Tensor, kappa: float, L: int | None = None, prec="fp64", layout="canonical",
+                     out: torch.Tensor | None = None) -> torch.Tensor:
+        """Y = D_W X with one kappa for every column (bk_dslash_multi).  layout
+        "canonical": X a canonical block (L from its shape); "device": X a
+        device-layout block of L columns in prec."""
+        if layout == "canonical":
+            self._check_block(X, "X")
+            L = X.shape[0]
+            Y = torch.empty_like(X) if out is None else out
+        elif layout == "device":
+            if L is None:
+                raise ValueError("device layout needs L")
+            Y = self.empty_field(L, "fp64" if prec == "df64" else prec) if out is None else out
+        else:
+            raise ValueError("layout must be 'canonical' or 'device'")
+        check(lib().bk_dslash_multi(self._h, float(kappa), _ptr(X), _ptr(Y), int(L), _prec(prec),
+                                    _lib.LAYOUT[layout], _stream_ptr(self.device)), "bk_dslash_multi")
         return Y
 
     def gamma5(self, X: torch.Tensor) -> torch.Tensor:

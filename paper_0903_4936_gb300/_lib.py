@@ -24,8 +24,10 @@ EXPORTED = [
     "bk_status_string", "bk_last_error", "bk_create", "bk_destroy", "bk_upload_gauge",
     "bk_build_clover", "bk_field_bytes", "bk_pack", "bk_unpack", "bk_dslash_dev", "bk_dslash",
     "bk_gamma5", "bk_block_gram", "bk_block_xmy", "bk_small_solve", "bk_block_solve",
-    "bk_block_solve_batched", "bk_dot", "bk_gauge_force", "bk_block_gram_noalloc",
+    "bk_block_solve_batched", "bk_dot", "bk_gauge_force", "bk_block_gram_noalloc", "bk_dslash_multi",
+    "bk_set_clover",
 ]
+LAYOUT = {"canonical": 0, "device": 1}
 
 
 class SolveParams(C.Structure):
@@ -94,6 +96,8 @@ def lib():
         "bk_dot": (C.c_int, [vp, vp, vp, C.c_int, dp, vp]),
         "bk_block_gram_noalloc": (C.c_int, [C.c_int, vp, vp, C.c_int, C.c_int, vp, vp]),
         "bk_gauge_force": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, vp, vp]),
+        "bk_dslash_multi": (C.c_int, [vp, C.c_double, vp, vp, C.c_int, C.c_int, C.c_int, vp]),
+        "bk_set_clover": (C.c_int, [vp, C.c_double]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -376,6 +376,21 @@ extern "C" bk_status bk_dslash(bk_ctx* c, const double* kappa, const double* X, 
     return launch_unpack(sp, y, Y, L, st);
 }
 
+extern "C" bk_status bk_dslash_multi(bk_ctx* c, double kappa, const void* X, void* Y, int L, bk_prec prec,
+                                     bk_layout layout, void* stream) {
+    BK_CHECK_ARG(c && X && Y && L >= 1, "bad argument to bk_dslash_multi");
+    BK_CHECK_ARG(layout == BK_LAYOUT_CANONICAL || layout == BK_LAYOUT_DEVICE, "unknown layout");
+    std::vector<double> k((size_t)L, kappa);
+    if (layout == BK_LAYOUT_DEVICE) return bk_dslash_dev(c, k.data(), X, Y, L, prec, stream);
+    return bk_dslash(c, k.data(), (const double*)X, (double*)Y, L, prec, stream);
+}
+
+extern "C" bk_status bk_set_clover(bk_ctx* c, double csw) {
+    BK_TRY(bk_build_clover(c, csw, nullptr));
+    BK_CUDA_TRY(cudaStreamSynchronize(nullptr));
+    return BK_OK;
+}
+
 extern "C" bk_status bk_gamma5(bk_ctx* c, const double* X, double* Y, int L, void* stream) {
     BK_CHECK_ARG(c && X && Y && L >= 1, "bad argument to bk_gamma5");
     BK_CUDA_TRY(cudaSetDevice(c->device));

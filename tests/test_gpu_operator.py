@@ -192,3 +192,24 @@ def test_dslash_pipelined_kernel(monkeypatch, dims, L):
         assert info["converged"] == 1 and info["true_res_max"] <= 1e-10
         R = B.cpu().numpy() - dirac.apply_dirac(U, Xs.cpu().numpy(), 0.12, 1.0)
         assert np.linalg.norm(R) <= 1e-10 * np.linalg.norm(B.cpu().numpy()) * np.sqrt(L)
+
+
+def test_dslash_multi_and_set_clover():
+    """bk_set_clover builds the clover term (FP64 operator against the oracle)
+    and bk_dslash_multi (one kappa for all columns) gives bit for bit what
+    bk_dslash and bk_dslash_dev give with kappa repeated, in both layouts."""
+    import paper_0903_4936_gb300 as bk
+    dims = (4, 4, 4, 6)
+    U = synth.random_su3_field(dims, 0.5, 61)
+    lat = bk.Lattice(dims)
+    lat.upload_gauge(U)
+    lat.set_clover(1.0)
+    X = synth.gaussian_sources(dims, 5, 62)
+    Xt = torch.from_numpy(X).cuda()
+    Y1 = lat.dslash_multi(Xt, 0.121, prec="fp64").cpu().numpy()
+    assert _rel(Y1, dirac.apply_dirac(U, X, 0.121, 1.0)) < TOL["fp64"]
+    np.testing.assert_array_equal(Y1, lat.dslash(Xt, 0.121, "fp64").cpu().numpy())
+    F = lat.pack(Xt, "fp32")
+    G1 = lat.unpack(lat.dslash_multi(F, 0.121, L=5, prec="fp32", layout="device"), 5, "fp32").cpu().numpy()
+    G2 = lat.unpack(lat.dslash_dev(F, 5, 0.121, "fp32"), 5, "fp32").cpu().numpy()
+    np.testing.assert_array_equal(G1, G2)
