@@ -37,14 +37,14 @@ bk_status launch_cast(int pin, Field in, int pout, Field out, int L, cudaStream_
 bk_status launch_gamma5_canon(const double* X, double* Y, long long nsites_cols, cudaStream_t st);
 
 // ---------------------------------------------------------------- blas.cu
-// Partition of the columns into independent systems: system s owns columns
-// [col0[s], col0[s+1]).  coef_off[s] = offset (in complex entries) of system
-// s's L_s x L_s matrix inside a packed coefficient array.
 // one bit per system of a batched solve (BK_MAX_SYS <= 64)
 typedef unsigned long long sysmask;
 // every system of an nsys-system partition
 inline sysmask all_systems(int nsys) { return nsys >= 64 ? ~0ull : ((1ull << nsys) - 1ull); }
 
+// Partition of the columns into independent systems: system s owns columns
+// [col0[s], col0[s+1]).  coef_off[s] = offset (in complex entries) of system
+// s's L_s x L_s matrix inside a packed coefficient array.
 struct SysPart {
     int nsys;
     int col0[BK_MAX_SYS + 1];
