@@ -279,9 +279,17 @@ static bk_status tune_shape(bk_ctx* c, int prec, DslashOp op, cudaStream_t st, b
             if (cd.pipe == c->pipe_only) keep.push_back(cd);
         cands.swap(keep);
     }
-    cudaEvent_t e0, e1;
-    BK_CUDA_TRY(cudaEventCreate(&e0));
-    BK_CUDA_TRY(cudaEventCreate(&e1));
+    // events released on every return path
+    struct EventPair {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~EventPair() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    BK_CUDA_TRY(cudaEventCreate(&ev.a));
+    BK_CUDA_TRY(cudaEventCreate(&ev.b));
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     float best_ms = 1e30f;
     best = cands[0];
     for (const auto& cd : cands) {
@@ -302,8 +310,6 @@ static bk_status tune_shape(bk_ctx* c, int prec, DslashOp op, cudaStream_t st, b
             best = cd;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     return BK_OK;
 }
 
