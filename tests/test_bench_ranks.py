@@ -60,3 +60,30 @@ def test_replicas_draw_different_sources():
     s1 = synth.z2_noise(dims, 4, b.replica_seed(4, 1))
     assert not np.array_equal(s0, s1)
     assert b.replica_seed(48, 0) == 2048
+
+
+def test_reference_arm_runs_on_cpu():
+    """bench.py --impl reference: the FP64 oracle timed on the host, one JSON
+    line with the contract's keys (8^3 x 16 workload, one short step)."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "c2",
+                          "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=600, check=True)
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "RHS/s"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["higher_is_better"] is True
+
+
+def test_roofline_traffic_scales_the_capture(tmp_path, monkeypatch):
+    """roofline.traffic = captured DRAM / algorithmic bytes x this run's bytes
+    per launch, and None once the operator sources differ from the capture's."""
+    import json
+    b = _bench()
+    d = json.load(open(os.path.join(ROOT, "profiles", "dslash_traffic.json")))
+    c = d["captures"]["fp32"]
+    if d["source_hash"] == b.source_hash():
+        assert b.ncu_traffic("fp32", 2e9) == pytest.approx(c["dram_bytes"] / c["alg_bytes"] * 2e9)
+    monkeypatch.setattr(b, "source_hash", lambda: "0000")
+    assert b.ncu_traffic("fp32", 2e9) is None
