@@ -1,18 +1,25 @@
 #!/usr/bin/env python
-"""Benchmark: right-hand sides solved per second to true relative residual 1e-10
-with the mixed-precision block BiCGGR solver, on a synthetic 16^3 x 32 clover
-Wilson-Dirac problem, plus the multi-RHS operator's HBM roofline.
+"""Benchmark: right-hand sides solved per second to FP64 true relative residual
+1e-10 on a synthetic clover Wilson-Dirac problem, plus the multi-RHS operator's
+HBM roofline.
 
-One step = every case of the workload solved once through the C ABI (block
-BiCGGR, FP16-stored / FP32-arithmetic inner iterations, FP64 reliable updates
-and FP64 true residual).  Each solve must reach a FP64 true residual <= 1e-10,
-else the run fails.  Prints ONE JSON line on rank 0.
+Default workload (`--workload c4`): 24^3 x 48, random SU(3) links eps = 0.5,
+c_SW = 1, six systems kappa in {0.120, ..., 0.130} with L = {4, 12, 12, 24, 48,
+96} Z4 noise sources (196 right-hand sides).  One step = the whole workload
+solved once through the C ABI as one batched solve: every system split into
+block systems of at most 6 columns, block BiCGSTAB with FP32 inner iterations
+and FP64 residual replacement, each column to an FP64 true residual <= 1e-10
+(the run fails otherwise).  Prints ONE JSON line on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload c3|c3-12|c3-48|c2] [--no-fp64] [--no-cpu-baseline]
+                  [--workload c4|c3|c2|...] [--no-fp64] [--fp64-full] [--no-cpu-baseline]
+
+Comparisons on the same GPU (after the timed steps): the plain FP64 method at
+the same 6-column split (isolates precision) and, with --fp64-full, the
+paper's FP64 block BiCGGR with every system as one block of all its columns.
 
 --impl reference times the FP64 CPU oracle (test infrastructure, written from
-the paper) on a bounded sample of the same workload.
+the paper) on bounded samples of the same workload on the host cores.
 """
 from __future__ import annotations
 
@@ -20,6 +27,7 @@ import argparse
 import hashlib
 import json
 import math
+import multiprocessing
 import os
 import subprocess
 import sys
@@ -31,40 +39,33 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RHS solved/s to rel resid 1e-10 (mixed vs FP64); multi-RHS dslash HBM GB/s"
 
+_C4_CASES = list(zip((0.120, 0.122, 0.124, 0.126, 0.128, 0.130), (4, 12, 12, 24, 48, 96), ["z4"] * 6))
+_C3_CASES = [(k, L, src) for k in (0.120, 0.125, 0.130) for (L, src) in ((12, "point"), (48, "z2"))]
+
 # Workloads: (Lx, Ly, Lz, Lt), link spread eps, c_SW, cases (kappa, L, source kind).
 WORKLOADS = {
+    "c4": dict(dims=(24, 24, 24, 48), eps=0.5, csw=1.0, gauge_seed=1004, prec="fp32", method="bicgstab",
+               block=6, delta=0.03, distinct_sources=True, cases=_C4_CASES,
+               desc="24^3x48 clover Wilson-Dirac, random SU(3) links eps=0.5, c_SW=1.0: 6 systems, kappa "
+                    "{0.120,...,0.130} with L {4,12,12,24,48,96} Z4 noise = 196 right-hand sides; one batched "
+                    "block BiCGSTAB solve over 33 block systems of at most 6 columns, FP32 inner iterations, FP64 "
+                    "residual replacement (delta 0.03), FP64 true residual <= 1e-10 for every column"),
     "c3": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp32", method="bicgstab",
-               block=6, delta=0.03,
-               cases=[(k, L, src) for k in (0.120, 0.125, 0.130) for (L, src) in ((12, "point"), (48, "z2"))],
+               block=6, delta=0.03, cases=_C3_CASES,
                desc="16^3x32 clover Wilson-Dirac, random SU(3) links eps=0.5, c_SW=1.0, kappa in "
                     "{0.120,0.125,0.130} x (L=12 point sources, L=48 complex-Z2 noise) = 180 right-hand sides; "
-                    "mixed: one batched block BiCGSTAB solve over 30 systems of 6 columns, FP32 inner iterations "
-                    "with per-iteration Cholesky basis of P, FP64 residual replacement (delta 0.03), FP64 true "
-                    "residual <= 1e-10 for every column; FP64 comparison: the paper's plain FP64 block BiCGGR "
-                    "per case (one block of L columns), same true residual"),
-    "c4": dict(dims=(24, 24, 24, 48), eps=0.5, csw=1.0, gauge_seed=1004, prec="fp32", method="bicgstab",
-               block=6, delta=0.03, e2e=False, distinct_sources=True,
-               e2e_note="host-buffer pass not run: its staging copies of B and X (2 x 25 GB) do not fit beside "
-                        "the solve's 250 GB on the device",
-               cases=list(zip((0.120, 0.122, 0.124, 0.126, 0.128, 0.130), (4, 12, 12, 24, 48, 96), ["z4"] * 6)),
-               desc="24^3x48 clover Wilson-Dirac, random SU(3) links eps=0.5, c_SW=1.0: 6 systems, kappa "
-                    "{0.120,...,0.130} with L {4,12,12,24,48,96} Z4 noise = 196 right-hand sides; mixed: one "
-                    "batched block BiCGSTAB solve over 33 systems of at most 6 columns, FP32 inner iterations, "
-                    "FP64 residual replacement (delta 0.03), FP64 true residual <= 1e-10 for every column; FP64 "
-                    "comparison: the paper's plain FP64 block BiCGGR per system"),
+                    "one batched block BiCGSTAB solve over 30 systems of 6 columns, FP32 inner iterations, FP64 "
+                    "residual replacement (delta 0.03), FP64 true residual <= 1e-10 for every column"),
+    "c2": dict(dims=(8, 8, 8, 16), eps=0.5, csw=1.0, gauge_seed=1002, prec="fp32", method="bicggr",
+               cases=[(0.125, 12, "point")],
+               desc="8^3x16, eps=0.5, c_SW=1.0, kappa=0.125, L=12 point sources; block BiCGGR with FP32 inner "
+                    "iterations (Cholesky basis of P) and FP64 residual replacement, tol 1e-10"),
     "c3-12": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp32", method="bicgstab",
                   cases=[(0.125, 12, "point")],
                   desc="16^3x32, eps=0.5, c_SW=1.0, kappa=0.125, L=12 point sources; block BiCGSTAB, "
                        "FP32 inner iterations, FP64 residual replacement, tol 1e-10"),
-    "c3-48": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp32", method="bicgstab",
-                  cases=[(0.125, 48, "z2")],
-                  desc="16^3x32, eps=0.5, c_SW=1.0, kappa=0.125, L=48 complex-Z2 noise; block BiCGSTAB, "
-                       "FP32 inner iterations, FP64 residual replacement, tol 1e-10"),
-    "c2": dict(dims=(8, 8, 8, 16), eps=0.5, csw=1.0, gauge_seed=1002, prec="fp32", method="bicgstab",
-               cases=[(0.125, 12, "point")],
-               desc="8^3x16, eps=0.5, c_SW=1.0, kappa=0.125, L=12 point sources; block BiCGSTAB FP32 inner + "
-                    "FP64 residual replacement, tol 1e-10"),
 }
+DEFAULT_WORKLOAD = "c4"
 TOL = 1e-10
 MAXITER = 5000
 
@@ -94,8 +95,23 @@ def sources(dims, L, kind, seed):
     return synth.gaussian_sources(dims, L, seed)
 
 
-# sources that define the operator kernel k_dslash (its own file and the
-# headers it includes)
+def case_seed(wl, ci, L, rank):
+    """Source seed of case ci: each rank (replica) solves its own noise vectors."""
+    return replica_seed(L, rank) + (100 * ci if wl.get("distinct_sources") else 0)
+
+
+def systems(wl):
+    """The block systems of the batched solve: (kappa, columns, case index)."""
+    out = []
+    blk = wl.get("block")
+    for ci, (kappa, L, _) in enumerate(wl["cases"]):
+        step = blk or L
+        for j0 in range(0, L, step):
+            out.append((kappa, min(step, L - j0), ci))
+    return out
+
+
+# sources that define the inner operator kernel (its own file and the headers it includes)
 OPERATOR_SOURCES = ["paper_0903_4936_gb300/csrc/dslash.cu", "paper_0903_4936_gb300/csrc/bk_common.cuh",
                     "paper_0903_4936_gb300/csrc/dd.cuh", "paper_0903_4936_gb300/csrc/bk_kernels.h",
                     "include/bkrylov.h"]
@@ -183,43 +199,109 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ oracle baseline
+#
+# The FP64 numpy oracle as it stands, on the host cores.  A full oracle solve
+# of the benchmark's lattice takes hours, so a sample is one oracle
+# application of D_W to the first block system's columns: the oracle block
+# BiCGGR spends 2 such applications per iteration (plus one at set-up and one
+# for the true residual) and its block algebra on top, which the sample leaves
+# out (so the CPU figure is an upper bound).  RHS/s = columns / (seconds per
+# application x (2 iterations + 2)), with the iteration count of the same
+# FP64 block BiCGGR on the GPU for that system (iterate for iterate the
+# oracle's recursion in the parity tests).  Every host core runs its own
+# sample concurrently (one process each); the figure is their sum.
 
-ORACLE_SNIPPET = r"""
-import os, sys, time, json
-sys.path.insert(0, {root!r})
-import numpy as np, synth
-from oracle import clover, dense, dirac, solvers
-dims = {dims!r}; kappa = {kappa!r}; L = {L}; kind = {kind!r}
-U = synth.random_su3_field(dims, {eps!r}, {gseed!r})
-B = synth.point_sources(dims)[:L].copy() if kind == "point" else synth.z2_noise(dims, L, {sseed!r})
-t0 = time.perf_counter()
-F = clover.field_strength(U)
-A = lambda M: dense.to_columns(dirac.apply_dirac(U, dense.from_columns(M, dims), kappa, {csw!r}, F=F))
-Bc = dense.to_columns(B)
-t1 = time.perf_counter()
-A(Bc)  # one operator application: the set-up product W_0 = A R_0 of the solve below
-t2 = time.perf_counter()
-X, info = solvers.block_bicggr(A, Bc, 1e-300, {iters})
-t3 = time.perf_counter()
-it = max(1, info["iterations"])
-print(json.dumps(dict(setup_s=t1 - t0, apply_s=t2 - t1, iter_s=((t3 - t2) - (t2 - t1)) / it, iterations=it)))
-"""
-
-
-def run_oracle_sample(wl, case, iters=1):
-    """Time `iters` iterations of the oracle's block BiCGGR (plus the initial
-    operator application) on one case, single-threaded, in a fresh process."""
-    kappa, L, kind = case
-    code = ORACLE_SNIPPET.format(root=ROOT, dims=wl["dims"], kappa=kappa, L=L, kind=kind, eps=wl["eps"],
-                                 gseed=wl["gauge_seed"], sseed=2000 + L, csw=wl["csw"], iters=iters)
-    env = dict(os.environ)
+def _oracle_worker(args):
+    """One process: load the shared gauge field and clover field strength,
+    build the system's sources, time `reps` oracle operator applications."""
+    root, dims, eps, gpath, fpath, csw, kappa, L, kind, seed, reps = args
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[v] = "1"
-    env["CUDA_VISIBLE_DEVICES"] = ""
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
-    if out.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+        os.environ[v] = "1"
+    sys.path.insert(0, root)
+    import numpy as np
+
+    import synth  # noqa: F401
+    from oracle import dense, dirac
+    U = np.load(gpath, mmap_mode="r")
+    F = np.load(fpath, mmap_mode="r")
+    B = sources(dims, L, kind, seed)[:L]
+    Bc = dense.to_columns(B)
+    out = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        dense.to_columns(dirac.apply_dirac(U, dense.from_columns(Bc, dims), kappa, csw, F=F))
+        out.append(time.perf_counter() - t0)
+    return out
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _mem_available_gb():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) / 1024 / 1024
+    except OSError:
+        pass
+    return 16.0
+
+
+def oracle_samples(wl, nsamples, rank=0):
+    """Run nsamples timed oracle applications spread over the host cores
+    (one process per core, spawned, no GPU).  Returns (per-sample seconds,
+    processes used, the sampled system's (kappa, L))."""
+    import numpy as np
+
+    import synth
+    from oracle import clover
+    dims = wl["dims"]
+    kappa, L, ci = systems(wl)[0]
+    kind = wl["cases"][ci][2]
+    Lcase = wl["cases"][ci][1]
+    seed = case_seed(wl, ci, Lcase, rank)
+    tmp = tempfile.mkdtemp(prefix="bk_oracle_")
+    gpath, fpath = os.path.join(tmp, "U.npy"), os.path.join(tmp, "F.npy")
+    U = synth.random_su3_field(dims, wl["eps"], wl["gauge_seed"])
+    np.save(gpath, U)
+    np.save(fpath, clover.field_strength(U))
+    del U
+    V = synth.lattice_volume(dims)
+    per_proc_gb = 2.5 + V * L * 12 * 16 * 8 / 2**30  # the application's temporaries
+    procs = max(1, min(_host_cores(), nsamples, int(_mem_available_gb() * 0.7 / per_proc_gb)))
+    reps = [nsamples // procs + (1 if i < nsamples % procs else 0) for i in range(procs)]
+    jobs = [(ROOT, dims, wl["eps"], gpath, fpath, wl["csw"], kappa, Lcase, kind, seed, r) for r in reps if r > 0]
+    try:
+        ctx = multiprocessing.get_context("spawn")
+        with ctx.Pool(len(jobs)) as pool:
+            res = pool.map(_oracle_worker, jobs)
+    finally:
+        for f in (gpath, fpath):
+            try:
+                os.remove(f)
+            except OSError:
+                pass
+        os.rmdir(tmp)
+    secs = [t for r in res for t in r]
+    return secs, len(jobs), (kappa, L)
+
+
+def oracle_rhs_per_s(secs, procs, L, iters):
+    """Whole-host RHS/s: procs concurrent samples, each an L-column operator
+    application, (2 iterations + 2) applications per solve."""
+    mean = sum(secs) / len(secs)
+    return procs * L / (mean * (2 * iters + 2)), mean
+
+
+# Iteration count of the FP64 block BiCGGR on the first block system of each
+# workload (kappa 0.120, L <= 6), as measured by this benchmark's FP64
+# comparison on a GB300; the reference arm, which has no GPU, uses it to turn
+# the oracle's seconds per application into RHS/s.
+FP64_ITERS_FIRST_SYSTEM = {"c4": 45, "c3": 45, "c2": 50, "c3-12": 54}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -247,7 +329,6 @@ def replica_seed(L, rank):
 
 
 def gb300_arm(args, wl, rank, world, local_rank):
-    import numpy as np
     import torch
 
     import paper_0903_4936_gb300 as bk
@@ -262,76 +343,45 @@ def gb300_arm(args, wl, rank, world, local_rank):
     lat.build_clover(wl["csw"])
     V = lat.V
     del U
-    with_e2e = wl.get("e2e", True)
+    # All cases' sources in one device block (each case a view of its columns);
+    # the host copy is pinned for the end-to-end pass.
+    Lt = sum(L for (_, L, _) in wl["cases"])
+    Ball = torch.empty((Lt,) + tuple(reversed(dims)) + (4, 3), dtype=torch.complex128, device=dev)
     cases = []
-    batch = None
-    if wl.get("block"):
-        # batched mode: all cases' sources in one device block (each case a
-        # view of its columns), every case split into systems of at most
-        # `block` columns, all systems solved together.  Sources go to the
-        # device one case at a time, so the host holds at most one case.
-        blk = wl["block"]
-        Lt = sum(L for (_, L, _) in wl["cases"])
-        Ball = torch.empty((Lt,) + tuple(reversed(dims)) + (4, 3), dtype=torch.complex128, device=dev)
-        kap_s, L_s, owner = [], [], []
-        c0 = 0
-        for ci, (kappa, L, kind) in enumerate(wl["cases"]):
-            seed = replica_seed(L, rank) + (100 * ci if wl.get("distinct_sources") else 0)
-            Ball[c0:c0 + L].copy_(torch.from_numpy(sources(dims, L, kind, seed)))
-            cases.append(dict(kappa=kappa, L=L, kind=kind, B=Ball[c0:c0 + L]))
-            for j0 in range(0, L, blk):
-                kap_s.append(kappa)
-                L_s.append(min(blk, L - j0))
-                owner.append(ci)
-            c0 += L
-        batch = dict(kappas=kap_s, Ls=L_s, owner=owner, B=Ball,
-                     Bh=Ball.cpu().pin_memory() if with_e2e else None)
-    else:
-        for (kappa, L, kind) in wl["cases"]:
-            B = sources(dims, L, kind, replica_seed(L, rank))
-            cases.append(dict(kappa=kappa, L=L, kind=kind, B=torch.from_numpy(B).to(dev),
-                              Bh=torch.from_numpy(B).pin_memory()))
+    c0 = 0
+    for ci, (kappa, L, kind) in enumerate(wl["cases"]):
+        Ball[c0:c0 + L].copy_(torch.from_numpy(sources(dims, L, kind, case_seed(wl, ci, L, rank))))
+        cases.append(dict(kappa=kappa, L=L, kind=kind, c0=c0))
+        c0 += L
+    sysl = systems(wl)
+    kap_s, L_s, owner = [s[0] for s in sysl], [s[1] for s in sysl], [s[2] for s in sysl]
+    Xdev = torch.empty_like(Ball)
+    Bh = Ball.cpu().pin_memory()
+    Xh = torch.empty_like(Bh).pin_memory()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
-    def step(record, host=False):
-        tot = dict(rhs=0, launches=0, t_inner=0.0, n_inner=0, bytes_inner=0.0)
-        if batch is not None:
-            B = batch["Bh"] if host else batch["B"]
-            X, infos = lat.block_solve_batched(B, batch["kappas"], batch["Ls"], method=wl["method"],
-                                               prec=wl["prec"], tol=TOL, maxiter=MAXITER, timing=record,
-                                               delta=wl.get("delta", 0.0))
-            for si, info in enumerate(infos):
-                if not (info["converged"] and info["true_res_max"] <= TOL):
-                    raise RuntimeError(f"system {si} did not reach {TOL}: {info}")
-            ltot = sum(batch["Ls"])
-            info = infos[0]
-            tot["rhs"] = ltot
-            tot["launches"] = info["n_launches"]
-            tot["t_inner"] = info["time_dslash_inner_ms"]
-            tot["n_inner"] = info["n_dslash_inner"]
-            tot["bytes_inner"] = dslash_bytes(V, info["cols_dslash_inner"], wl["prec"], info["n_dslash_inner"])
-            for ci, c in enumerate(cases):
-                mine = [infos[si] for si in range(len(infos)) if batch["owner"][si] == ci]
-                c["last_info"] = dict(iterations=max(i["iterations"] for i in mine),
-                                      reliable_updates=max(i["reliable_updates"] for i in mine),
-                                      true_res_max=max(i["true_res_max"] for i in mine))
-            return tot
-        for c in cases:
-            B = c["Bh"] if host else c["B"]
-            X, info = lat.block_solve(B, c["kappa"], method=wl["method"], prec=wl["prec"], tol=TOL,
-                                      maxiter=MAXITER, timing=record)
-            if not (info["converged"] and info["true_res_max"] <= TOL):
-                raise RuntimeError(f"solve did not reach {TOL}: {info}")
-            tot["rhs"] += c["L"]
-            tot["launches"] += info["n_launches"]
-            tot["t_inner"] += info["time_dslash_inner_ms"]
-            tot["n_inner"] += info["n_dslash_inner"]
-            tot["bytes_inner"] += dslash_bytes(V, info["cols_dslash_inner"], wl["prec"], info["n_dslash_inner"])
-            c["last_info"] = info
-        return tot
+    def solve(B, X, record, prec=None, method=None):
+        return lat.block_solve_batched(B, kap_s, L_s, method=method or wl["method"], prec=prec or wl["prec"],
+                                       tol=TOL, maxiter=MAXITER, timing=record, delta=wl.get("delta", 0.0),
+                                       out=X, raise_on_fail=False)
 
+    def check(infos, what):
+        for si, info in enumerate(infos):
+            if not (info["converged"] and info["true_res_max"] <= TOL):
+                raise RuntimeError(f"{what}: system {si} did not reach {TOL}: {info}")
+
+    def step(record, host=False):
+        X, infos = solve(Bh if host else Ball, Xh if host else Xdev, record)
+        check(infos, "mixed solve")
+        info = infos[0]
+        return dict(launches=info["n_launches"], t_inner=info["time_dslash_inner_ms"],
+                    n_inner=info["n_dslash_inner"],
+                    bytes_inner=dslash_bytes(V, info["cols_dslash_inner"], wl["prec"], info["n_dslash_inner"]),
+                    infos=infos)
+
+    last = None
     for _ in range(args.warmup):
-        step(False)
+        last = step(False)
         flush.fill_(1)
     torch.cuda.synchronize()
 
@@ -339,7 +389,7 @@ def gb300_arm(args, wl, rank, world, local_rank):
     if rank == 0:
         clocks.start()
     per_step_ms = []
-    agg = dict(rhs=0, launches=0, t_inner=0.0, n_inner=0, bytes_inner=0.0)
+    agg = dict(launches=0, t_inner=0.0, n_inner=0, bytes_inner=0.0)
     stream = torch.cuda.current_stream(dev)
     if world > 1:
         import torch.distributed as dist
@@ -361,62 +411,92 @@ def gb300_arm(args, wl, rank, world, local_rank):
         total_ms += ms
         for k in agg:
             agg[k] += t[k]
+        last = t
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     if world > 1:
         dist.barrier()
     clk = clocks.stop() if rank == 0 else None
 
-    # e2e: the same metric through the public API with host (pinned) buffers:
-    # B copied in and X copied out inside every call.
-    e2e_ms = 0.0
-    h2d = d2h = 0
+    # e2e: the same metric through the public API with pinned host buffers: B
+    # is copied in and X copied out (through a bounded device staging buffer,
+    # a chunk of columns at a time) inside every call.
     n_e2e = max(1, min(args.steps, 3))
-    if with_e2e:
-        for _ in range(n_e2e):
-            flush.fill_(1)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            t = step(False, host=True)
-            torch.cuda.synchronize()
-            e2e_ms += (time.perf_counter() - t0) * 1e3
-        for c in cases:
-            h2d += c["B"].numel() * 16
-            d2h += c["B"].numel() * 16
-    else:
-        e2e_ms = None
-    batched = None
-    if batch is not None:
-        batched = dict(systems=len(batch["Ls"]), block=wl["block"], columns=sum(batch["Ls"]))
+    e2e_ms = 0.0
+    for _ in range(n_e2e):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(False, host=True)
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    h2d = d2h = Ball.numel() * 16
+
+    infos = last["infos"]
+    per_case = {}
+    for ci, c in enumerate(cases):
+        mine = [infos[si] for si in range(len(infos)) if owner[si] == ci]
+        per_case[f"k{c['kappa']}_L{c['L']}"] = dict(
+            iterations=max(i["iterations"] for i in mine), reliable_updates=max(i["reliable_updates"] for i in mine),
+            true_res_max=max(i["true_res_max"] for i in mine))
 
     fp64 = None
     if not args.no_fp64 and rank == 0:
-        # plain FP64 block BiCGGR (the paper's method) on every case, to the same
-        # FP64 true residual, timed with CUDA events outside the timed loop
-        rhs, ms = 0, 0.0
-        per = {}
-        for c in cases:
+        fp64 = {}
+
+        def timed(fn):
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            X, info = lat.block_solve(c["B"], c["kappa"], method="bicggr", prec="fp64", tol=TOL, maxiter=MAXITER)
+            out = fn()
             e1.record()
             e1.synchronize()
-            if info["true_res_max"] > TOL:
-                raise RuntimeError(f"FP64 solve did not reach {TOL}: {info}")
-            t = e0.elapsed_time(e1)
-            ms += t
-            rhs += c["L"]
-            per[f"k{c['kappa']}_L{c['L']}"] = dict(ms=round(t, 1), iterations=info["iterations"])
-        fp64 = dict(method="block BiCGGR, FP64", fp64_rhs_per_s=rhs / (ms / 1e3), cases=per)
+            return out, e0.elapsed_time(e1)
 
-    return dict(total_ms=total_ms, per_step_ms=per_step_ms, agg=agg, clocks=clk,
-                e2e_ms=e2e_ms / n_e2e if e2e_ms is not None else None,
-                h2d=h2d, d2h=d2h, fp64=fp64, V=V, batched=batched,
-                iters={f"k{c['kappa']}_L{c['L']}": c["last_info"]["iterations"] for c in cases},
-                true_res={f"k{c['kappa']}_L{c['L']}": c["last_info"]["true_res_max"] for c in cases},
-                rel_updates={f"k{c['kappa']}_L{c['L']}": c["last_info"]["reliable_updates"] for c in cases})
+        # the plain FP64 block BiCGGR at the same split: precision alone.  One
+        # batched solve per case (all cases at once would need seven FP64
+        # blocks of every column beside the benchmark's buffers); a short
+        # untimed solve first tunes the FP64 operator's launch shape.
+        tot, its, first = 0.0, [], None
+        for ci, c in enumerate(cases):
+            idx = [si for si in range(len(L_s)) if owner[si] == ci]
+            Bc = Ball[c["c0"]:c["c0"] + c["L"]]
+            Xc = Xdev[c["c0"]:c["c0"] + c["L"]]
+            ks, ls = [kap_s[si] for si in idx], [L_s[si] for si in idx]
+            lat.block_solve_batched(Bc, ks, ls, method="bicggr", prec="fp64", tol=TOL, maxiter=1, out=Xc,
+                                    raise_on_fail=False)
+            (X, inf64), ms = timed(lambda: lat.block_solve_batched(Bc, ks, ls, method="bicggr", prec="fp64",
+                                                                   tol=TOL, maxiter=MAXITER, out=Xc,
+                                                                   raise_on_fail=False))
+            check(inf64, "FP64 solve at the same split")
+            tot += ms
+            its += [i["iterations"] for i in inf64]
+            if first is None:
+                first = inf64[0]["iterations"]
+        fp64["same_split"] = dict(method="block BiCGGR, FP64, the same block systems (one batched solve per case)",
+                                  rhs_per_s=Lt / (tot / 1e3), ms=round(tot, 1), iterations_first_system=first,
+                                  iterations_max=max(its))
+        if args.fp64_full:
+            # the paper's method as printed: every case one block of all its columns
+            tot, per = 0.0, {}
+            for c in cases:
+                Bc = Ball[c["c0"]:c["c0"] + c["L"]].contiguous()
+                lat.block_solve(Bc, c["kappa"], method="bicggr", prec="fp64", tol=TOL, maxiter=1,
+                                raise_on_fail=False)
+                (X, info), ms = timed(lambda: lat.block_solve(Bc, c["kappa"], method="bicggr", prec="fp64", tol=TOL,
+                                                              maxiter=MAXITER))
+                if info["true_res_max"] > TOL:
+                    raise RuntimeError(f"FP64 solve did not reach {TOL}: {info}")
+                tot += ms
+                per[f"k{c['kappa']}_L{c['L']}"] = dict(ms=round(ms, 1), iterations=info["iterations"])
+                del Bc
+            fp64["full_blocks"] = dict(method="block BiCGGR, FP64, each case one block (the paper's method)",
+                                       rhs_per_s=Lt / (tot / 1e3), cases=per)
+
+    return dict(total_ms=total_ms, per_step_ms=per_step_ms, agg=agg, clocks=clk, e2e_ms=e2e_ms / n_e2e,
+                h2d=h2d, d2h=d2h, fp64=fp64, V=V, per_case=per_case,
+                batched=dict(systems=len(L_s), block=wl.get("block"), columns=Lt))
 
 
 def main():
@@ -425,8 +505,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--fp64-full", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
@@ -438,24 +519,24 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        # Reference arm: the CPU oracle as it stands, one process, one thread.
-        first = wl["cases"][0]
-        samples = []
-        for _ in range(args.warmup + args.steps):
-            samples.append(run_oracle_sample(wl, first, iters=1))
-        timed = samples[args.warmup:]
-        iter_s = sum(s["iter_s"] for s in timed) / len(timed)
-        n_it = GPU_ITERS_HINT.get(args.workload, 100)
-        value = first[1] / (iter_s * n_it)
+        # Reference arm: the CPU oracle as it stands.  Each step is one sample
+        # (an oracle operator application on the first block system); the
+        # steps run concurrently, one process per host core.
+        secs, procs, (kappa, L) = oracle_samples(wl, args.warmup + args.steps)
+        timed = secs[args.warmup:] if len(secs) > args.warmup else secs
+        iters = FP64_ITERS_FIRST_SYSTEM[args.workload]
+        value, mean = oracle_rhs_per_s(timed, procs, L, iters)
+        sample = (f"one FP64 numpy-oracle application of D_W to the first block system's {L} columns (kappa={kappa}) "
+                  f"per step ({mean:.1f} s), {procs} processes on the host cores at once; RHS/s = processes x L / "
+                  f"(s x (2 x {iters} + 2)), {iters} = the FP64 block BiCGGR iteration count of that system; the "
+                  f"oracle's block algebra is left out")
         line = {
             "impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": iter_s * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["desc"], "parallelism": "none (CPU oracle)"},
-            "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": 1, "kind": "oracle",
-                             "sample": f"one block BiCGGR iteration of the FP64 numpy oracle per step on the case "
-                                       f"kappa={first[0]}, L={first[1]} {first[2]}; RHS/s = L / (seconds per "
-                                       f"iteration x {n_it} iterations, the GPU solver's count for this case)"},
+            "config": {"workload": wl["desc"], "lattice": "x".join(map(str, wl["dims"])),
+                       "parallelism": f"CPU oracle, {procs} processes"},
+            "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": procs, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }
         print(json.dumps(line))
@@ -467,11 +548,10 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
-    # The oracle baseline runs in a spawned process before any GPU work.
+    # The oracle baseline runs in spawned processes before any GPU work.
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu_case = wl["cases"][0]
-        cpu = run_oracle_sample(wl, cpu_case, iters=1)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_samples(wl, _host_cores())
 
     r = gb300_arm(args, wl, rank, world, local_rank)
 
@@ -490,39 +570,39 @@ def main():
         "config": {"workload": wl["desc"], "lattice": "x".join(map(str, wl["dims"])),
                    "rhs_per_step": total_rhs_per_step, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 and a 256 MB L2 flush before every timed step"},
-        "roofline": {"bound": "hbm", "kernel": f"k_dslash<{wl['prec'].upper()}> (inner operator, all columns)",
+        "roofline": {"bound": "hbm", "kernel": f"k_dslash_pair<{wl['prec'].upper()}> (inner operator, all columns)",
                      "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": (achieved / hbm) if achieved else None, "peak_kind": peak_kind,
                      "traffic": traffic, "launches": agg["n_inner"],
                      "avg_launch_us": agg["t_inner"] / agg["n_inner"] * 1e3 if agg["n_inner"] else None},
-        "e2e": ({"value": world * total_rhs_per_step / (r["e2e_ms"] / 1e3), "unit": "RHS/s",
-                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]} if r["e2e_ms"] is not None else
-                {"value": None, "unit": "RHS/s", "skipped": wl.get("e2e_note")}),
+        "e2e": {"value": world * total_rhs_per_step / (r["e2e_ms"] / 1e3), "unit": "RHS/s",
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
         "gpu_launches": int(agg["launches"]),
         "clocks": r["clocks"],
-        "iterations": r["iters"], "reliable_updates": r["rel_updates"], "true_res_max": r["true_res"],
+        "per_case": r["per_case"],
         "batched": r["batched"],
     }
     if r["fp64"]:
-        r["fp64"]["mixed_over_fp64"] = (value / world) / r["fp64"]["fp64_rhs_per_s"]
+        for k, v in r["fp64"].items():
+            v["mixed_over_fp64"] = (value / world) / v["rhs_per_s"]
         line["fp64_comparison"] = r["fp64"]
     if cpu is not None:
-        its = r["iters"].get(f"k{wl['cases'][0][0]}_L{wl['cases'][0][1]}", 100)
-        cv = wl["cases"][0][1] / (cpu["iter_s"] * its)
-        line["cpu_baseline"] = {"value": cv, "unit": "RHS/s", "cores": 1, "kind": "oracle",
-                                "sample": f"one FP64 numpy-oracle block BiCGGR iteration ({cpu['iter_s']:.1f} s) on "
-                                          f"kappa={wl['cases'][0][0]}, L={wl['cases'][0][1]}; RHS/s = L / (s/iter x "
-                                          f"{its} iterations, the GPU solver's count for that case)"}
+        secs, procs, (kappa, L) = cpu
+        iters = (r["fp64"] or {}).get("same_split", {}).get("iterations_first_system") or \
+            FP64_ITERS_FIRST_SYSTEM[args.workload]
+        cv, mean = oracle_rhs_per_s(secs, procs, L, iters)
+        line["cpu_baseline"] = {
+            "value": cv, "unit": "RHS/s", "cores": procs, "kind": "oracle",
+            "sample": f"one FP64 numpy-oracle application of D_W to the first block system's {L} columns "
+                      f"(kappa={kappa}, {mean:.1f} s) on each of {procs} host processes at once; RHS/s = processes x "
+                      f"L / (s x (2 x {iters} + 2)), {iters} = this run's FP64 block BiCGGR iteration count for that "
+                      f"system; the oracle's block algebra is left out"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 
-
-# Iteration counts of the GPU solver per workload's first case, used to turn the
-# oracle's seconds per iteration into RHS/s on the reference arm.
-GPU_ITERS_HINT = {"c3": 42, "c4": 45, "c3-12": 57, "c3-48": 281, "c2": 122}
 
 if __name__ == "__main__":
     main()

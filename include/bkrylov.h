@@ -17,12 +17,18 @@
  *    contiguous array of N complex FP64 numbers ordered [site][spin][colour]
  *    {re, im}; component index 3*spin + colour (Section 2 point-source
  *    convention, 0-based).  Total 16*N*L bytes.
- *  - Device spinor block ("device layout"): opaque, precision-specific,
+ *  - Device spinor block ("device layout"): precision-specific,
  *    bk_field_bytes() bytes, produced by bk_pack() and read by bk_unpack().
- *    Columns are stored one after another, each as 16-byte chunks in
- *    [chunk][site] order (FP64: 12 chunks, FP32: 6, FP16: 3 plus one FP32
- *    scale per site and column).  Any device allocation with 256-byte
- *    alignment may hold it.
+ *    RHS-interleaved: the columns are grouped in pairs (2p, 2p + 1) and, for
+ *    site n and spinor component k = 3*spin + colour, element
+ *    (n * 12 + k) * ceil(L/2) + p holds the pair's real parts, then its
+ *    imaginary parts: FP64 {re, re}, {im, im} as two double2 (32 bytes),
+ *    FP32 {re, re, im, im} (16 bytes), FP16 {re, re}, {im, im} as two half2
+ *    (8 bytes) followed, after all elements, by one FP32 scale per site and
+ *    column (float2 per site and pair; FP16 values are stored divided by the
+ *    column's largest component at that site).  An odd L leaves the last
+ *    pair's second column as padding (zero after bk_pack).  Any device
+ *    allocation with 256-byte alignment may hold it.
  *  - Pointers documented as "device" must be CUDA device memory of the
  *    context's device; "host" pointers are ordinary (or pinned) host memory.
  *    The caller owns every buffer it passes; the library copies what it keeps.
@@ -161,9 +167,11 @@ bk_status bk_block_gram(bk_ctx* ctx, const void* A, const void* B, int L, bk_pre
  *     (L <= 360); larger L returns BK_ERR_INVALID_ARG and bk_block_gram must
  *     be used.  Fewer thread blocks are used when the array would not hold
  *     the usual number; the result is the same sum in a different order.
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress)
+ *     with the caller's device current, so the address always belongs to
+ *     the current context.  The first call on a device also loads the
+ *     library's device code there: make that first call before any stream
+ *     capture.
  *   - Every call shares the one array and overwrites it; each slot a call
  *     reads is written earlier in the same call, so nothing needs clearing,
  *     but calls whose work overlaps on the GPU (other streams, other host
@@ -211,6 +219,30 @@ bk_status bk_dot(bk_ctx* ctx, const double* A, const double* B, int L, double re
  * Uses library workspace (10 V * 9 complex).  Errors: NO_GAUGE, INVALID_ARG, CUDA. */
 bk_status bk_gauge_force(bk_ctx* ctx, const double* X, const double* Lam, int L, int mode, double scale,
                          double* out, void* stream);
+
+/* Derivative of the loss with respect to the hopping parameter for the
+ * adjoint of a solve.  Eq. (wd-op) writes D_W = 1 - kappa M with M the
+ * hopping plus clover term, so dD_W/dkappa = -M = (D_W - 1)/kappa and, for
+ * X = D_W^-1 B and lam = D_W^-H eta (the gradient of a real loss with
+ * respect to X),
+ *     *grad = -Re <lam, (dD_W/dkappa) X> = Re sum conj(lam) (X - B) / kappa.
+ * Lam, X, B: canonical FP64 device blocks of L columns.  grad: host double.
+ * FP64 partial sums per thread block, summed in a fixed order; synchronises
+ * the stream.  Uses library workspace.
+ * Errors: INVALID_ARG (null pointer, L < 1, kappa zero or not finite), CUDA. */
+bk_status bk_kappa_grad(bk_ctx* ctx, double kappa, const double* Lam, const double* X, const double* B, int L,
+                        double* grad, void* stream);
+
+/* ----------------------------------------------------------- measurement */
+
+/* Arithmetic peak of device `device` (no paper counterpart: the roofline
+ * denominators of the operator kernels).  kind 0: FP32 fused multiply-add,
+ * 1: packed FP32x2 fused multiply-add (fma.rn.f32x2), 2: FP64 fused
+ * multiply-add.  *tflops (host) = 2 flops per FMA lane / kernel time, best
+ * of 3 timed launches of 8 blocks of 256 threads per SM, 8 independent
+ * chains per thread.  Allocates 2 KB of device memory for the call.
+ * Errors: INVALID_ARG, CUDA.                                              */
+bk_status bk_probe_peak(int kind, int device, double* tflops);
 
 /* ---------------------------------------------------------------- solves */
 

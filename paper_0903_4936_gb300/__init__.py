@@ -21,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import BKError, PREC, METHOD, SolveInfo, SolveParams, check, lib
 
-__all__ = ["Lattice", "BKError", "PREC", "METHOD", "load", "block_solve_autograd", "small_solve"]
+__all__ = ["Lattice", "BKError", "PREC", "METHOD", "load", "block_solve_autograd", "small_solve", "probe_peak"]
 
 
 def load():
@@ -197,6 +197,16 @@ class Lattice:
         check(lib().bk_dot(self._h, _ptr(A), _ptr(B), A.shape[0], r, _stream_ptr(self.device)), "bk_dot")
         return complex(r[0], r[1])
 
+    def kappa_grad(self, Lam: torch.Tensor, X: torch.Tensor, B: torch.Tensor, kappa: float) -> float:
+        """Re sum conj(Lam) (X - B) / kappa (bk_kappa_grad): dLoss/dkappa for
+        X = D_W^-1 B and Lam the adjoint solution."""
+        for t, n in ((Lam, "Lam"), (X, "X"), (B, "B")):
+            self._check_block(t, n)
+        r = C.c_double()
+        check(lib().bk_kappa_grad(self._h, float(kappa), _ptr(Lam), _ptr(X), _ptr(B), X.shape[0], C.byref(r),
+                                  _stream_ptr(self.device)), "bk_kappa_grad")
+        return r.value
+
     def gauge_force(self, X: torch.Tensor, Lam: torch.Tensor, mode=0, scale=1.0) -> torch.Tensor:
         """Link derivative of Re sum <Lam, (H + C) X> (see bk_gauge_force).
         mode 0/1: complex128 [4, V, 3, 3] (Sigma / Sigma^+); mode 2: float64 [4, V, 8]."""
@@ -271,14 +281,23 @@ class Lattice:
 
     def block_solve_batched(self, B: torch.Tensor, kappas: Sequence[float], Ls: Sequence[int], method="bicggr",
                             prec="fp64", tol=1e-10, maxiter=2000, delta=0.0, rtilde=None, seed=0, history=False,
-                            timing=False, raise_on_fail=True, restart=False, orth=None, update="fp64"):
-        """Several systems (kappa_s, L_s columns each, concatenated in B)."""
+                            timing=False, raise_on_fail=True, restart=False, orth=None, update="fp64",
+                            out: torch.Tensor | None = None):
+        """Several systems (kappa_s, L_s columns each, concatenated in B).  X is
+        returned where B lives, in `out` if given (same shape and location as
+        B; pinned host memory for host blocks)."""
         self._check_block(B, "B")
         nsys = len(Ls)
         if sum(Ls) != B.shape[0] or len(kappas) != nsys:
             raise ValueError("B must hold sum(Ls) columns and one kappa per system")
         on_host = not B.is_cuda
-        X = torch.empty_like(B, pin_memory=on_host) if on_host else torch.empty_like(B)
+        if out is not None:
+            self._check_block(out, "out")
+            if out.shape != B.shape or out.is_cuda != B.is_cuda:
+                raise ValueError("out must have B's shape and location")
+            X = out
+        else:
+            X = torch.empty_like(B, pin_memory=on_host) if on_host else torch.empty_like(B)
         prm = self._params(method, prec, tol, maxiter, delta, False, on_host, rtilde, seed, history, timing,
                            restart, orth, update)
         infos = (SolveInfo * nsys)()
@@ -309,8 +328,8 @@ class _BlockSolve(torch.autograd.Function):
     """X = D_W(U, kappa)^-1 B with the adjoint of Section 3's solve.
 
     backward: lam = D^-H g = gamma_5 D^-1 gamma_5 g (gamma_5-hermiticity of
-    D_W), grad_B = lam, grad_kappa = Re <lam, X - B> / kappa (D = 1 - kappa M,
-    M X = (X - B) / kappa), grad_U = kappa Sigma^+ from bk_gauge_force.  The
+    D_W), grad_B = lam, grad_kappa from bk_kappa_grad (Re <lam, X - B> / kappa,
+    since D = 1 - kappa M), grad_U = kappa Sigma^+ from bk_gauge_force.  The
     adjoint solve recomputes, it stores no Krylov history."""
 
     @staticmethod
@@ -335,8 +354,7 @@ class _BlockSolve(torch.autograd.Function):
         gB = lam if ctx.needs_input_grad[0] else None
         gk = None
         if ctx.needs_input_grad[1]:
-            d = lat.dot(lam, X) - lat.dot(lam, B)
-            gk = torch.tensor(d.real / k, dtype=torch.float64, device=X.device)
+            gk = torch.tensor(lat.kappa_grad(lam, X, B, k), dtype=torch.float64, device=X.device)
         gU = None
         if ctx.needs_input_grad[2]:
             gU = lat.gauge_force(X, lam, mode=1, scale=k).reshape(U.shape)
@@ -361,3 +379,12 @@ def small_solve(G: torch.Tensor, H: torch.Tensor, scale=1.0):
     check(lib().bk_small_solve(L, _ptr(G), _ptr(H), cc, _ptr(Xs), _ptr(info), _stream_ptr(G.device)),
           "bk_small_solve")
     return Xs, int(info.item())
+
+
+def probe_peak(kind: str = "fp32", device: int = 0) -> float:
+    """Measured arithmetic peak of the GPU in TFLOP/s (bk_probe_peak):
+    kind "fp32" (FMA), "fp32x2" (packed FMA) or "fp64" (FMA)."""
+    k = {"fp32": 0, "fp32x2": 1, "fp64": 2}[kind]
+    r = C.c_double()
+    check(lib().bk_probe_peak(k, int(device), C.byref(r)), "bk_probe_peak")
+    return r.value

@@ -25,7 +25,7 @@ EXPORTED = [
     "bk_build_clover", "bk_field_bytes", "bk_pack", "bk_unpack", "bk_dslash_dev", "bk_dslash",
     "bk_gamma5", "bk_block_gram", "bk_block_xmy", "bk_small_solve", "bk_block_solve",
     "bk_block_solve_batched", "bk_dot", "bk_gauge_force", "bk_block_gram_noalloc", "bk_dslash_multi",
-    "bk_set_clover",
+    "bk_set_clover", "bk_probe_peak", "bk_kappa_grad",
 ]
 LAYOUT = {"canonical": 0, "device": 1}
 
@@ -98,6 +98,8 @@ def lib():
         "bk_gauge_force": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, vp, vp]),
         "bk_dslash_multi": (C.c_int, [vp, C.c_double, vp, vp, C.c_int, C.c_int, C.c_int, vp]),
         "bk_set_clover": (C.c_int, [vp, C.c_double]),
+        "bk_probe_peak": (C.c_int, [C.c_int, C.c_int, dp]),
+        "bk_kappa_grad": (C.c_int, [vp, C.c_double, vp, vp, vp, C.c_int, dp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

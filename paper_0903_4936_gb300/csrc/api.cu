@@ -32,12 +32,6 @@ void bk_set_error(const char* fmt, ...) {
     va_end(ap);
 }
 
-#define BK_TRY(expr)                        \
-    do {                                    \
-        bk_status _s = (expr);              \
-        if (_s != BK_OK) return _s;         \
-    } while (0)
-
 #define BK_CHECK_ARG(cond, msg)             \
     do {                                    \
         if (!(cond)) {                      \
@@ -112,18 +106,18 @@ struct bk_ctx {
     // scratch of the single-operation entry points
     DevBuf s1, s2, part, scal;
     // solver workspace
-    DevBuf B64, X64, R64, Xlo, blk[8], small, spart, canonB, canonX, canonRt, fscratch, ynorm;
+    DevBuf B64, X64, R64, Xlo, blk[8], small, spart, stage, colmap, fscratch, ynorm;
     HostBuf rb_host;
     std::vector<cudaEvent_t> events;
     // operator launch shapes chosen by the autotuner, keyed by (prec, residual, ncol)
     struct Shape {
-        int rpt, sx, by, pipe;
+        int threads, variant;
     };
     std::map<long long, Shape> shapes;
     bool autotune = true;
     bool verbose = false;  // BK_VERBOSE=1: one line per solve and per tuning decision on stderr
-    int pipe_only = 0;      // BK_DSLASH_PIPE=1: FP32 operator tuned over the pipelined kernel only
-                            // (default: the plain kernel, faster on every shape measured)
+    int force_variant = 0;  // BK_DSLASH_VARIANT=1..7: FP32/FP16 operator variant (thread mapping and
+                            // register cap), 128 threads, no tuning (tests every variant the tuner may pick)
 };
 
 static bool wide(int prec) { return prec == BK_FP64 || prec == BK_DF64; }
@@ -168,15 +162,15 @@ extern "C" bk_status bk_create(const int dims[4], int device, bk_ctx** out) {
         c->autotune = !(e && e[0] == '0');
         const char* v = getenv("BK_VERBOSE");
         c->verbose = v && v[0] == '1';
-        const char* pp = getenv("BK_DSLASH_PIPE");
-        if (pp && pp[0] == '1') c->pipe_only = 1;
+        const char* fv = getenv("BK_DSLASH_VARIANT");
+        if (fv && fv[0] >= '1' && fv[0] <= '7') c->force_variant = fv[0] - '0';
     }
     c->device = device;
     bk_status s;
     if ((s = c->U64.ensure((size_t)36 * V * sizeof(double2))) != BK_OK ||
-        (s = c->U32.ensure((size_t)36 * V * sizeof(float2))) != BK_OK ||
+        (s = c->U32.ensure((size_t)4 * V * BK_LINK32_F4 * sizeof(float4))) != BK_OK ||
         (s = c->C64.ensure((size_t)36 * V * sizeof(double2))) != BK_OK ||
-        (s = c->C32.ensure((size_t)18 * V * sizeof(float4))) != BK_OK) {
+        (s = c->C32.ensure((size_t)V * BK_CLOV32_F4 * sizeof(float4))) != BK_OK) {
         bk_destroy(c);
         return s;
     }
@@ -188,8 +182,8 @@ extern "C" bk_status bk_destroy(bk_ctx* c) {
     if (!c) return BK_OK;
     cudaSetDevice(c->device);
     DevBuf* bufs[] = {&c->U64, &c->U32, &c->C64, &c->C32, &c->Utmp, &c->s1, &c->s2, &c->part, &c->scal,
-                      &c->B64, &c->X64, &c->R64, &c->Xlo, &c->small, &c->spart, &c->canonB,
-                      &c->canonX, &c->canonRt, &c->fscratch, &c->ynorm};
+                      &c->B64, &c->X64, &c->R64, &c->Xlo, &c->small, &c->spart, &c->stage,
+                      &c->colmap, &c->fscratch, &c->ynorm};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : c->blk) b.release();
     c->rb_host.release();
@@ -208,7 +202,7 @@ extern "C" bk_status bk_upload_gauge(bk_ctx* c, const double* U, int on_device, 
         BK_CUDA_TRY(cudaMemcpyAsync(c->Utmp.p, U, (size_t)36 * c->V * sizeof(double2), cudaMemcpyHostToDevice, st));
         src = c->Utmp.as<double>();
     }
-    BK_TRY(launch_gauge_convert(src, c->U64.as<double2>(), c->U32.as<float2>(), c->V, st));
+    BK_TRY(launch_gauge_convert(src, c->U64.as<double2>(), c->U32.as<float4>(), c->V, st));
     if (!on_device) BK_CUDA_TRY(cudaStreamSynchronize(st));
     c->has_gauge = true;
     c->has_clover = false;
@@ -234,50 +228,44 @@ extern "C" size_t bk_field_bytes(const bk_ctx* c, int L, bk_prec prec) {
     return field_bytes(L, c->V, storage_prec(prec));
 }
 
+// canonical L columns -> device block (an odd L gets a zero padding column)
+static bk_status pack_block(int prec, const double* X, Field f, int L, cudaStream_t st) {
+    BK_TRY(launch_pack(prec, X, L, nullptr, 0, f, st));
+    if (L & 1) BK_TRY(launch_zero_col(prec, f, L, st));
+    return BK_OK;
+}
+
 extern "C" bk_status bk_pack(bk_ctx* c, const double* X, void* Xd, int L, bk_prec prec, void* stream) {
     BK_CHECK_ARG(c && X && Xd && L >= 1 && valid_prec(prec), "bad argument to bk_pack");
     BK_CUDA_TRY(cudaSetDevice(c->device));
-    return launch_pack(prec, X, make_field(Xd, L, c->V, prec), L, (cudaStream_t)stream);
+    return pack_block(prec, X, make_field(Xd, L, c->V, prec), L, (cudaStream_t)stream);
 }
 
 extern "C" bk_status bk_unpack(bk_ctx* c, const void* Xd, double* X, int L, bk_prec prec, void* stream) {
     BK_CHECK_ARG(c && X && Xd && L >= 1 && valid_prec(prec), "bad argument to bk_unpack");
     BK_CUDA_TRY(cudaSetDevice(c->device));
-    return launch_unpack(prec, make_field((void*)Xd, L, c->V, prec), X, L, (cudaStream_t)stream);
+    return launch_unpack(prec, make_field((void*)Xd, L, c->V, prec), nullptr, 0, X, L, (cudaStream_t)stream);
 }
 
-// Pick the operator's launch shape (columns per thread, sites and column
-// groups per block) for this context: on first use of a (precision, mode,
+// Pick the operator's launch shape (threads per block and, for FP32 / FP16,
+// the register cap) for this context: on first use of a (precision, mode,
 // column count) every candidate runs on the caller's data and the fastest
 // (CUDA events, 2 timed launches after 1 warm-up) is kept.  Every candidate
 // computes the same result.
 static bk_status tune_shape(bk_ctx* c, int prec, DslashOp op, cudaStream_t st, bk_ctx::Shape& best) {
     std::vector<bk_ctx::Shape> cands;
-    const int rpts[3] = {1, 2, 4};
-    for (int ri = 0; ri < (wide(prec) ? 1 : 3); ++ri) {
-        const int rpt = rpts[ri];
-        if (rpt > 1 && rpt > op.ncol) continue;
-        const int ngroups = (op.ncol + rpt - 1) / rpt;
-        for (int sx : {16, 32})
-            for (int threads : {128, 256}) {
-                int by = std::min(threads / sx, ngroups);
-                if (by < 1) by = 1;
-                cands.push_back({rpt, sx, by, 0});
-            }
-        // FP32: the cp.async-pipelined kernel (shared-memory stages per thread)
-        if (prec == BK_FP32 && rpt <= 2)
-            for (int sx : {16, 32})
-                for (int threads : {64, 128}) {
-                    int by = std::min(threads / sx, ngroups);
-                    if (by < 1) by = 1;
-                    cands.push_back({rpt, sx, by, 1});
-                }
-    }
-    if (prec == BK_FP32) {
-        std::vector<bk_ctx::Shape> keep;
-        for (const auto& cd : cands)
-            if (cd.pipe == c->pipe_only) keep.push_back(cd);
-        cands.swap(keep);
+    if (wide(prec)) {
+        for (int t : {64, 128}) cands.push_back({t, 0});
+    } else {
+        // one thread per (site, pair), register caps 255 (variant 1), 170 (2),
+        // 128 (3); colour-split, three threads per (site, pair): caps 128 (4),
+        // 85 (5), 64 (6), 255 (7)
+        for (int t : {128, 256}) cands.push_back({t, 1});
+        for (int v : {2, 3})
+            for (int t : {64, 128}) cands.push_back({t, v});
+        for (int v : {4, 7})
+            for (int t : {128, 256}) cands.push_back({t, v});
+        cands.push_back({256, 5});
     }
     // events released on every return path
     struct EventPair {
@@ -293,10 +281,8 @@ static bk_status tune_shape(bk_ctx* c, int prec, DslashOp op, cudaStream_t st, b
     float best_ms = 1e30f;
     best = cands[0];
     for (const auto& cd : cands) {
-        op.rpt = cd.rpt;
-        op.site_block = cd.sx;
-        op.col_block = cd.by;
-        op.pipe = cd.pipe;
+        op.threads = cd.threads;
+        op.variant = cd.variant;
         BK_TRY(launch_dslash(prec, op, st));
         BK_CUDA_TRY(cudaEventRecord(e0, st));
         BK_TRY(launch_dslash(prec, op, st));
@@ -327,25 +313,27 @@ static bk_status dslash_fields(bk_ctx* c, int prec, const double* kappa, Field x
     op.ncol = ncol;
     op.residual = residual;
     op.kappa = kappa;
-    op.site_block = 0;
-    op.col_block = 0;
-    op.rpt = 0;
-    op.pipe = 0;
-    if (c->autotune && ncol <= BK_MAX_COLS) {
-        const long long key = ((long long)prec << 40) | ((long long)(residual != 0) << 36) | ncol;
+    op.threads = 0;
+    op.variant = 0;
+    if (c->force_variant && !wide(prec)) {
+        op.threads = 128;
+        op.variant = c->force_variant;
+    } else if (c->autotune && ncol <= BK_MAX_COLS) {
+        // FP64-class launches are bound by the FP64 pipe whatever their width:
+        // one shape per mode, tuned at first use
+        const long long key =
+            ((long long)prec << 40) | ((long long)(residual != 0) << 36) | (wide(prec) ? 0 : ncol);
         auto it = c->shapes.find(key);
         if (it == c->shapes.end()) {
             bk_ctx::Shape sh;
             BK_TRY(tune_shape(c, prec, op, st, sh));
             it = c->shapes.emplace(key, sh).first;
             if (c->verbose)
-                fprintf(stderr, "[bkrylov] tuned operator prec=%d residual=%d ncol=%d: rpt=%d sites=%d groups=%d pipe=%d\n",
-                        prec, residual, ncol, sh.rpt, sh.sx, sh.by, sh.pipe);
+                fprintf(stderr, "[bkrylov] tuned operator prec=%d residual=%d ncol=%d: threads=%d variant=%d\n",
+                        prec, residual, ncol, sh.threads, sh.variant);
         }
-        op.rpt = it->second.rpt;
-        op.site_block = it->second.sx;
-        op.col_block = it->second.by;
-        op.pipe = it->second.pipe;
+        op.threads = it->second.threads;
+        op.variant = it->second.variant;
     }
     return launch_dslash(prec, op, st);
 }
@@ -377,9 +365,11 @@ extern "C" bk_status bk_dslash(bk_ctx* c, const double* kappa, const double* X, 
     BK_TRY(c->s1.ensure(nb));
     BK_TRY(c->s2.ensure(nb));
     Field x = make_field(c->s1.p, L, c->V, sp), y = make_field(c->s2.p, L, c->V, sp);
-    BK_TRY(launch_pack(sp, X, x, L, st));
-    BK_TRY(dslash_fields(c, prec, kappa, x, y, x, 0, L, 0, st));
-    return launch_unpack(sp, y, Y, L, st);
+    BK_TRY(pack_block(sp, X, x, L, st));
+    std::vector<double> k((size_t)L + 1, 0.0);
+    for (int j = 0; j < L; ++j) k[j] = kappa[j];
+    BK_TRY(dslash_fields(c, prec, k.data(), x, y, x, 0, L, 0, st));
+    return launch_unpack(sp, y, nullptr, 0, Y, L, st);
 }
 
 extern "C" bk_status bk_dslash_multi(bk_ctx* c, double kappa, const void* X, void* Y, int L, bk_prec prec,
@@ -472,6 +462,23 @@ extern "C" bk_status bk_dot(bk_ctx* c, const double* A, const double* B, int L, 
     return BK_OK;
 }
 
+extern "C" bk_status bk_kappa_grad(bk_ctx* c, double kappa, const double* Lam, const double* X, const double* B,
+                                   int L, double* grad, void* stream) {
+    BK_CHECK_ARG(c && Lam && X && B && grad && L >= 1, "bad argument to bk_kappa_grad");
+    BK_CHECK_ARG(kappa != 0.0 && std::isfinite(kappa), "bk_kappa_grad: kappa must be finite and non-zero");
+    BK_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    BK_TRY(c->fscratch.ensure(force_scratch_bytes(c->V)));
+    BK_TRY(c->scal.ensure(2 * sizeof(double)));
+    BK_TRY(launch_canon_dot_diff(Lam, X, B, (long long)L * c->V * 12, 1.0 / kappa, c->scal.as<double>(),
+                                 c->fscratch.p, st));
+    double r[2];
+    BK_CUDA_TRY(cudaMemcpyAsync(r, c->scal.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    BK_CUDA_TRY(cudaStreamSynchronize(st));
+    *grad = r[0];
+    return BK_OK;
+}
+
 // ================================================================= solver
 
 namespace {
@@ -487,7 +494,7 @@ __global__ void k_scalars(const double2* __restrict__ dots, int Lt, SysPart p, d
     if (s >= p.nsys) return;
     if (!((p.active >> s) & 1u)) return;
     double2 num = make_double2(0, 0), den = make_double2(0, 0);
-    for (int j = p.col0[s]; j < p.col0[s + 1]; ++j) {
+    for (int j = p.col0[s]; j < p.col0[s] + p.L[s]; ++j) {
         num.x += dots[j].x;
         num.y += dots[j].y;
         den.x += dots[Lt + j].x;
@@ -502,66 +509,17 @@ __global__ void k_scalars(const double2* __restrict__ dots, int Lt, SysPart p, d
     zbad[s] = (isfinite(zr) && isfinite(zi) && m > 0.0) ? 0 : 1;
 }
 
-// X64[cols] += Xlo[cols]; Xlo[cols] = 0
-__global__ void k_accum(Field x64, Field xlo, int V) {
-    const int site = blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = blockIdx.y;
-    if (site >= V) return;
-    cx<double> a[12];
-    cx<float> b[12];
-    load_spinor<BK_FP64>(x64, c, site, a);
-    load_spinor<BK_FP32>(xlo, c, site, b);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        a[k] = a[k] + mk((double)b[k].r, (double)b[k].i);
-        b[k] = mk(0.f, 0.f);
-    }
-    store_spinor<BK_FP64>(x64, c, site, a);
-    store_spinor<BK_FP32>(xlo, c, site, b);
-}
-
-// Seeded Gaussian shadow residual: SplitMix64 of (seed, index), Box-Muller.
-__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
-    z += 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-template <int P>
-__global__ void k_random(Field f, int V, uint64_t seed) {
-    using R = typename Prec<P>::real;
-    const int site = blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = blockIdx.y;
-    if (site >= V) return;
-    cx<R> v[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        const uint64_t idx = (((uint64_t)c * V + site) * 12 + k);
-        const uint64_t a = splitmix64(seed ^ (2 * idx)), b = splitmix64(seed ^ (2 * idx + 1));
-        if (P == BK_FP64) {
-            const double u1 = ((a >> 11) + 1) * (1.0 / 9007199254740993.0);
-            const double u2 = (b >> 11) * (1.0 / 9007199254740992.0);
-            const double r = sqrt(-log(u1));  // |z| of a complex Gaussian with E|z|^2 = 1
-            v[k] = mk((R)(r * cospi(2 * u2)), (R)(r * sinpi(2 * u2)));
-        } else {  // a low-precision shadow block needs no FP64 transcendentals
-            const float u1 = (float)((a >> 40) + 1) * (1.0f / 16777217.0f);
-            const float u2 = (float)(b >> 40) * (1.0f / 16777216.0f);
-            const float r = sqrtf(-logf(u1));
-            float sn, cs;
-            sincospif(2.0f * u2, &sn, &cs);
-            v[k] = mk((R)(r * cs), (R)(r * sn));
-        }
-    }
-    store_spinor<P>(f, c, site, v);
-}
-
 struct Solve {
     bk_ctx* c;
     const bk_solve_params* prm;
     cudaStream_t st;
-    int nsys, Lt, V, P, method;
+    int nsys, Lt, V, P, method;  // Lt: device columns (systems padded to even widths)
+    int Lu;                       // the caller's columns
     bool mixed;
     SysPart part;
+    std::vector<int> dcol_h;      // device column of each caller column
+    int ucol0[BK_MAX_SYS];        // first caller column of each system
+    int* dcol = nullptr;          // the same, on the device
     std::vector<double> kcol;        // kappa per column
     std::vector<double> bnorm;       // ||b_j||
     std::vector<int> done;           // per system: 0 active, 1 converged, 2 breakdown, 3 not converged
@@ -673,21 +631,14 @@ struct Solve {
         launches += 2;
         return launch_gram2(P, A, B, B2, part, G, G2, partial, V, st);
     }
-    bk_status coldot(int prec, int npair, const Field* A, const Field* B, double* out, int ncol = -1) {
+    // column dots over columns [c0, c0 + n): out[k * Lt + c0 + j]
+    bk_status coldot(int prec, int npair, const Field* A, const Field* B, double* out, int c0, int n) {
         launches += 2;
-        return launch_coldot(prec, npair, A, B, ncol < 0 ? Lt : ncol, out, partial, V, st);
+        return launch_coldot(prec, npair, A, B, c0, n, out, Lt, partial, V, st);
     }
     // pairs of column dots over the active systems' columns: out[k * Lt + j]
     bk_status coldot_active(int npair, const Field* A, const Field* B, double* out) {
-        for (const auto& cr : col_runs(part.active)) {
-            Field a[2], b[2];
-            for (int k = 0; k < npair; ++k) {
-                a[k] = field_cols(A[k], cr.first);
-                b[k] = field_cols(B[k], cr.first);
-            }
-            launches += 2;
-            BK_TRY(launch_coldot(P, npair, a, b, cr.second, out + 2 * (size_t)cr.first, partial, V, st, Lt));
-        }
+        for (const auto& cr : col_runs(part.active)) BK_TRY(coldot(P, npair, A, B, out, cr.first, cr.second));
         return BK_OK;
     }
     // L x L solves in two steps: factor G once, substitute for each right-hand side
@@ -738,8 +689,8 @@ struct Solve {
     // squared FP64 norms of the columns of f owned by the systems in mask, into rn
     bk_status norms_runs(int prec, Field f, sysmask mask) {
         for (const auto& cr : col_runs(mask)) {
-            Field a[1] = {field_cols(f, cr.first)};
-            BK_TRY(coldot(prec, 1, a, a, rn + 2 * (size_t)cr.first, cr.second));
+            Field a[1] = {f};
+            BK_TRY(coldot(prec, 1, a, a, rn, cr.first, cr.second));
         }
         return BK_OK;
     }
@@ -747,7 +698,7 @@ struct Solve {
     double rel(int j) const { return std::sqrt(std::max(rn_h[2 * j], 0.0)) / bnorm[j]; }
     double sys_max(int s) const {
         double m = 0;
-        for (int j = part.col0[s]; j < part.col0[s + 1]; ++j) {
+        for (int j = part.col0[s]; j < part.col0[s] + part.L[s]; ++j) {
             const double r = rel(j);
             m = (std::isnan(r) || r > m) ? r : m;
             if (std::isnan(m)) return m;
@@ -769,19 +720,11 @@ struct Solve {
         for (const auto& cr : col_runs(mask)) {
             const int c0 = cr.first, n = cr.second;
             if (mixed && accum) {
-                dim3 grid((V + 127) / 128, n);
-                k_accum<<<grid, 128, 0, st>>>(field_cols(X64, c0), field_cols(Xlo, c0), V);
-                BK_CUDA_TRY(cudaGetLastError());
+                BK_TRY(launch_accum(X64, Xlo, c0 / 2, n / 2, st));
                 launches++;
             }
             BK_TRY(dslash(rprec, X64, R64, B64, c0, n, 1));
-            if (P != BK_FP64) {
-                BK_TRY(launch_cast(BK_FP64, field_cols(R64, c0), P, field_cols(R, c0), n, st));
-            } else {
-                BK_CUDA_TRY(cudaMemcpyAsync((char*)R.data + (size_t)c0 * R.cstride * 16,
-                                            (char*)R64.data + (size_t)c0 * R64.cstride * 16,
-                                            (size_t)n * R.cstride * 16, cudaMemcpyDeviceToDevice, st));
-            }
+            BK_TRY(cast_cols(R64, BK_FP64, R, P, c0, n));
             launches++;
         }
         BK_TRY(norms_runs(BK_FP64, R64, mask));
@@ -796,9 +739,12 @@ struct Solve {
         B64 = make_field(c->B64.p, Lt, V, BK_FP64);
         X64 = make_field(c->X64.p, Lt, V, BK_FP64);
         R64 = make_field(c->R64.p, Lt, V, BK_FP64);
-        orth = method == BK_BICGSTAB && (prm->orth_mode == 1 || (prm->orth_mode == 0 && mixed));
+        // Cholesky basis of P: block BiCGSTAB (any precision when forced on);
+        // block BiCGGR only in mixed precision, where V = A P is formed
+        // explicitly after the basis change
+        orth = (prm->orth_mode == 1 || (prm->orth_mode == 0 && mixed)) && (method == BK_BICGSTAB || mixed);
         upd_prec = (mixed && prm->update_prec == 1) ? BK_DF64 : BK_FP64;
-        const int nblk = 7;
+        const int nblk = (method == BK_BICGGR && orth) ? 8 : 7;
         for (int i = 0; i < nblk; ++i) BK_TRY(c->blk[i].ensure(fbp));
         Field f[8];
         for (int i = 0; i < nblk; ++i) f[i] = make_field(c->blk[i].p, Lt, V, P);
@@ -810,6 +756,7 @@ struct Solve {
             Wb = f[4];
             Ub = f[5];
             Yb = f[6];
+            if (orth) Ptmp = f[7];
         } else {
             Tb = f[4];
             Zb = f[5];
@@ -819,6 +766,10 @@ struct Solve {
             BK_TRY(c->Xlo.ensure(field_bytes(Lt, V, BK_FP32)));
             Xlo = make_field(c->Xlo.p, Lt, V, BK_FP32);
         }
+        // caller column -> device column
+        BK_TRY(c->colmap.ensure((size_t)Lu * sizeof(int)));
+        dcol = c->colmap.as<int>();
+        BK_CUDA_TRY(cudaMemcpyAsync(dcol, dcol_h.data(), (size_t)Lu * sizeof(int), cudaMemcpyHostToDevice, st));
         // small arrays (complex FP64 unless noted)
         const int nc = ncoef();
         const size_t nsmall = (size_t)7 * nc + 3 * Lt + Lt + 3 * nsys;
@@ -867,69 +818,52 @@ struct Solve {
         BK_TRY(c->spart.ensure(pb));
         partial = c->spart.as<double>();
         if (method == BK_BICGSTAB) {  // residual norms fused into the R update
-            const size_t nb = (size_t)Lt * genop_norm_blocks(V) * sizeof(double);
+            const size_t nb = (size_t)Lt * genop_norm_rows(V) * sizeof(double);
             BK_TRY(c->ynorm.ensure(nb));
             ynorm = c->ynorm.as<double>();
             BK_CUDA_TRY(cudaMemsetAsync(ynorm, 0, nb, st));
         }
 
-        // B, X0 into the FP64 device layout
-        BK_TRY(launch_pack(BK_FP64, Bc, B64, Lt, st));
-        launches++;
+        // B, X0 into the FP64 device layout (padding columns zero)
+        BK_TRY(put_caller_block(Bc, B64));
         {
             Field a[1] = {B64}, b[1] = {B64};
-            BK_TRY(coldot(BK_FP64, 1, a, b, rn));
+            BK_TRY(coldot(BK_FP64, 1, a, b, rn, 0, Lt));
             BK_TRY(readback());
-            for (int j = 0; j < Lt; ++j) {
-                const double n2 = rn_h[2 * j];
-                if (!std::isfinite(n2)) {
-                    bk_set_error("right-hand side column %d is not finite", j);
-                    return BK_ERR_NONFINITE;
+            for (int s = 0; s < nsys; ++s)
+                for (int j = part.col0[s]; j < part.col0[s] + part.L[s]; ++j) {
+                    const double n2 = rn_h[2 * j];
+                    const int ju = j - part.col0[s] + ucol0[s];
+                    if (!std::isfinite(n2)) {
+                        bk_set_error("right-hand side column %d is not finite", ju);
+                        return BK_ERR_NONFINITE;
+                    }
+                    if (n2 <= 0.0) {
+                        bk_set_error("right-hand side column %d is zero", ju);
+                        return BK_ERR_INVALID_ARG;
+                    }
+                    bnorm[j] = std::sqrt(n2);
                 }
-                if (n2 <= 0.0) {
-                    bk_set_error("right-hand side column %d is zero", j);
-                    return BK_ERR_INVALID_ARG;
-                }
-                bnorm[j] = std::sqrt(n2);
-            }
         }
         if (prm->rtilde_mode == 2) {
-            const double* rt = prm->rtilde;
-            if (prm->buffers_on_host) {
-                BK_TRY(c->canonRt.ensure((size_t)Lt * V * 12 * sizeof(double2)));
-                BK_CUDA_TRY(cudaMemcpyAsync(c->canonRt.p, rt, (size_t)Lt * V * 12 * sizeof(double2),
-                                            cudaMemcpyHostToDevice, st));
-                rt = c->canonRt.as<double>();
-            }
-            if (P == BK_FP64) {
-                BK_TRY(launch_pack(BK_FP64, rt, Rt, Lt, st));
-            } else {
-                BK_TRY(launch_pack(BK_FP64, rt, R64, Lt, st));  // R64 is rebuilt below
-                BK_TRY(launch_cast(BK_FP64, R64, P, Rt, Lt, st));
-                launches++;
-            }
+            BK_TRY(put_caller_block(prm->rtilde, R64));  // R64 is rebuilt below
+            BK_TRY(cast_cols(R64, BK_FP64, Rt, P, 0, Lt));
             launches++;
         } else if (prm->rtilde_mode == 0) {
-            dim3 grid((V + 127) / 128, Lt);
-            switch (P) {
-                case BK_FP64: k_random<BK_FP64><<<grid, 128, 0, st>>>(Rt, V, prm->seed); break;
-                case BK_FP32: k_random<BK_FP32><<<grid, 128, 0, st>>>(Rt, V, prm->seed); break;
-                default: k_random<BK_FP16><<<grid, 128, 0, st>>>(Rt, V, prm->seed); break;
-            }
-            BK_CUDA_TRY(cudaGetLastError());
+            BK_TRY(launch_random(P, Rt, Lt, prm->seed, st));
             launches++;
         }
         if (prm->x0_given) {
-            BK_TRY(launch_pack(BK_FP64, Xc, X64, Lt, st));
-            launches++;
+            BK_TRY(put_caller_block(Xc, X64));
             Field a[1] = {X64}, b[1] = {X64};
-            BK_TRY(coldot(BK_FP64, 1, a, b, rn));
+            BK_TRY(coldot(BK_FP64, 1, a, b, rn, 0, Lt));
             BK_TRY(readback());
-            for (int j = 0; j < Lt; ++j)
-                if (!std::isfinite(rn_h[2 * j])) {
-                    bk_set_error("initial guess column %d is not finite", j);
-                    return BK_ERR_NONFINITE;
-                }
+            for (int s = 0; s < nsys; ++s)
+                for (int j = part.col0[s]; j < part.col0[s] + part.L[s]; ++j)
+                    if (!std::isfinite(rn_h[2 * j])) {
+                        bk_set_error("initial guess column %d is not finite", j - part.col0[s] + ucol0[s]);
+                        return BK_ERR_NONFINITE;
+                    }
             BK_TRY(dslash(BK_FP64, X64, R64, B64, 0, Lt, 1));
             for (int s = 0; s < nsys; ++s) mv64[s]++;
         } else {
@@ -938,7 +872,7 @@ struct Solve {
         }
 
         if (mixed) BK_CUDA_TRY(cudaMemsetAsync(Xlo.data, 0, field_bytes(Lt, V, BK_FP32), st));
-        BK_TRY(launch_cast(BK_FP64, R64, P, R, Lt, st));
+        BK_TRY(cast_cols(R64, BK_FP64, R, P, 0, Lt));
         launches++;
         if (prm->rtilde_mode == 1)
             BK_CUDA_TRY(cudaMemcpyAsync(Rt.data, R.data, fbp, cudaMemcpyDeviceToDevice, st));
@@ -965,7 +899,7 @@ struct Solve {
     void converged_fp64(int s) {
         done[s] = 1;
         res_known[s] = 1;
-        for (int j = part.col0[s]; j < part.col0[s + 1]; ++j) true_res[j] = rel(j);
+        for (int j = part.col0[s]; j < part.col0[s] + part.L[s]; ++j) true_res[j] = rel(j);
     }
 
     void update_active() {
@@ -975,16 +909,75 @@ struct Solve {
         part.active = a;
     }
 
-    // Copy columns [c0, c0 + n) of src into dst (same precision and layout).
+    // Copy columns [c0, c0 + n) (whole pairs) of src into dst (same precision
+    // and layout): one strided segment per (site, component) row.
     bk_status copy_cols(Field dst, Field src, int c0, int n, int prec) {
-        const size_t bytes = (size_t)n * src.cstride * 16;
-        BK_CUDA_TRY(cudaMemcpyAsync((char*)dst.data + (size_t)c0 * src.cstride * 16,
-                                    (char*)src.data + (size_t)c0 * src.cstride * 16, bytes,
-                                    cudaMemcpyDeviceToDevice, st));
+        const size_t eb = prec_ebytes(prec), pitch = (size_t)src.np * eb;
+        BK_CUDA_TRY(cudaMemcpy2DAsync((char*)dst.data + (size_t)(c0 / 2) * eb, pitch,
+                                      (const char*)src.data + (size_t)(c0 / 2) * eb, pitch, (size_t)(n / 2) * eb,
+                                      (size_t)V * 12, cudaMemcpyDeviceToDevice, st));
         if (prec == BK_FP16)
-            BK_CUDA_TRY(cudaMemcpyAsync(dst.norm + (size_t)c0 * V, src.norm + (size_t)c0 * V,
-                                        (size_t)n * V * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            BK_CUDA_TRY(cudaMemcpy2DAsync(dst.norm + c0 / 2, (size_t)src.np * sizeof(float2), src.norm + c0 / 2,
+                                          (size_t)src.np * sizeof(float2), (size_t)(n / 2) * sizeof(float2),
+                                          (size_t)V, cudaMemcpyDeviceToDevice, st));
         return BK_OK;
+    }
+
+    // dst[cols] = src[cols] converted between precisions (whole pairs)
+    bk_status cast_cols(Field src, int psrc, Field dst, int pdst, int c0, int n) {
+        if (psrc == pdst) return copy_cols(dst, src, c0, n, psrc);
+        return launch_cast(psrc, field_pairs(src, c0 / 2, psrc), pdst, field_pairs(dst, c0 / 2, pdst), n / 2, st);
+    }
+
+    // The caller's canonical FP64 block (Lu columns, device or host memory)
+    // into an FP64 device-layout block: caller column j goes to device column
+    // dcol_h[j]; padding columns are zeroed.  Host blocks are staged through
+    // a bounded device buffer, a chunk of columns at a time.
+    bk_status put_caller_block(const double* src, Field dst) {
+        const size_t colb = (size_t)V * 12 * sizeof(double2);
+        if (!prm->buffers_on_host) {
+            BK_TRY(launch_pack(BK_FP64, src, Lu, dcol, 0, dst, st));
+            launches++;
+        } else {
+            const int ch = stage_cols();
+            BK_TRY(c->stage.ensure((size_t)ch * colb));
+            for (int j0 = 0; j0 < Lu; j0 += ch) {
+                const int nj = std::min(ch, Lu - j0);
+                BK_CUDA_TRY(cudaMemcpyAsync(c->stage.p, (const char*)src + (size_t)j0 * colb, (size_t)nj * colb,
+                                            cudaMemcpyHostToDevice, st));
+                BK_TRY(launch_pack(BK_FP64, c->stage.as<double>(), nj, dcol + j0, 0, dst, st));
+                launches++;
+            }
+        }
+        for (int s = 0; s < nsys; ++s)
+            if (part.L[s] & 1) {
+                BK_TRY(launch_zero_col(BK_FP64, dst, part.col0[s] + part.L[s], st));
+                launches++;
+            }
+        return BK_OK;
+    }
+    // The solution into the caller's canonical block (device or host).
+    bk_status get_caller_block(Field src, double* dst) {
+        const size_t colb = (size_t)V * 12 * sizeof(double2);
+        if (!prm->buffers_on_host) {
+            launches++;
+            return launch_unpack(BK_FP64, src, dcol, 0, dst, Lu, st);
+        }
+        const int ch = stage_cols();
+        BK_TRY(c->stage.ensure((size_t)ch * colb));
+        for (int j0 = 0; j0 < Lu; j0 += ch) {
+            const int nj = std::min(ch, Lu - j0);
+            BK_TRY(launch_unpack(BK_FP64, src, dcol + j0, 0, c->stage.as<double>(), nj, st));
+            launches++;
+            BK_CUDA_TRY(cudaMemcpyAsync((char*)dst + (size_t)j0 * colb, c->stage.p, (size_t)nj * colb,
+                                        cudaMemcpyDeviceToHost, st));
+        }
+        return BK_OK;
+    }
+    // staging chunk: columns of at most 1 GiB in all
+    int stage_cols() const {
+        const size_t colb = (size_t)V * 12 * sizeof(double2);
+        return (int)std::max<size_t>(1, std::min<size_t>((size_t)Lu, ((size_t)1 << 30) / colb));
     }
 
     // Mixed precision guard: the low-precision cycle of system s went wrong
@@ -993,9 +986,9 @@ struct Solve {
     // FP64 true residual (R64 still holds it).
     bk_status discard_cycle(int s) {
         const int c0 = part.col0[s], n = part.col0[s + 1] - c0;
-        BK_CUDA_TRY(cudaMemsetAsync((char*)Xlo.data + (size_t)c0 * Xlo.cstride * 16, 0,
-                                    (size_t)n * Xlo.cstride * 16, st));
-        BK_TRY(launch_cast(BK_FP64, field_cols(R64, c0), P, field_cols(R, c0), n, st));
+        BK_CUDA_TRY(cudaMemset2DAsync((char*)Xlo.data + (size_t)(c0 / 2) * 16, (size_t)Xlo.np * 16, 0,
+                                      (size_t)(n / 2) * 16, (size_t)V * 12, st));
+        BK_TRY(cast_cols(R64, BK_FP64, R, P, c0, n));
         launches++;
         restart_now[s] = 1;
         nrestart[s]++;
@@ -1023,7 +1016,7 @@ struct Solve {
     bk_status check(int k) {
         if (norms_fused) {  // the R update left per-block partial sums
             for (const auto& cr : col_runs(part.active)) {
-                BK_TRY(launch_norm_finish(ynorm, cr.first, cr.second, rn, V, st));
+                BK_TRY(launch_norm_finish(ynorm, Lt, cr.first, cr.second, rn, V, st));
                 launches++;
             }
             BK_TRY(readback());
@@ -1088,8 +1081,42 @@ struct Solve {
         return BK_OK;
     }
 
+    // P <- P T^-1 with P^H P = T^H T (FP64 Cholesky of the Gram matrix): the
+    // iterates of both methods are unchanged in exact arithmetic (alpha and
+    // the later coefficients absorb T); in low precision R~^H V = R~^H A P
+    // stays well conditioned.
+    bk_status cholesky_basis() {
+        BK_TRY(gram(Pb, Pb, G_Z));
+        launches += 1;
+        BK_TRY(launch_chol_inv(G_Z, gam, part, st));
+        GenOp g = genop0();
+        g.nmi = 1;
+        g.Mi[0] = Pb;
+        g.ma_mult[0] = 1.0;
+        g.M = gam;
+        g.hasY = 1;
+        g.Y = Ptmp;
+        g.ym = 1.0;
+        BK_TRY(genop(g));
+        std::swap(Pb, Ptmp);
+        return BK_OK;
+    }
+
     bk_status iterate_bicggr() {
         for (int k = 0; k < prm->maxiter && part.active; ++k) {
+            if (mixed) {
+                // Low-precision inner iterations: V = A P formed explicitly
+                // (after the optional basis change).  It equals W + Y gamma in
+                // exact arithmetic; the recursion drifts from A P under FP32
+                // rounding and the L x L systems built on V then lose the
+                // iteration.
+                if (orth) BK_TRY(cholesky_basis());
+                if (k > 0 || orth) {  // at k = 0 without the basis change V_0 = W_0 = A P_0 already
+                    BK_TRY(dslash_active(Pb, Vb, Pb));
+                    for (int s = 0; s < nsys; ++s)
+                        if ((part.active >> s) & 1u) mv[s]++;
+                }
+            }
             {   // G_V = R~^H V; traces Tr(W^H R), Tr(W^H W)
                 BK_TRY(gram(Rt, Vb, G_V));
                 Field a[2] = {Wb, Wb}, b[2] = {R, Wb};
@@ -1170,15 +1197,6 @@ struct Solve {
                 }
             }
             BK_TRY(apply_restarts());
-            if (mixed) {
-                // Low-precision inner iterations: V = A P formed explicitly.  It
-                // equals W + Y gamma in exact arithmetic; the recursion drifts
-                // from A P under FP32 rounding and the L x L systems built on V
-                // then lose the iteration.
-                BK_TRY(dslash_active(Pb, Vb, Pb));
-                for (int s = 0; s < nsys; ++s)
-                    if ((part.active >> s) & 1u) mv[s]++;
-            }
             std::swap(G_RR, G_RRn);
         }
         return BK_OK;
@@ -1186,24 +1204,7 @@ struct Solve {
 
     bk_status iterate_bicgstab() {
         for (int k = 0; k < prm->maxiter && part.active; ++k) {
-            if (orth) {
-                // P <- P T^-1 with P^H P = T^H T before V = A P: the iterates are
-                // unchanged in exact arithmetic (alpha, beta absorb T), V = A P stays
-                // exact, and R~^H V stays well conditioned in low precision.
-                BK_TRY(gram(Pb, Pb, G_Z));
-                launches += 1;
-                BK_TRY(launch_chol_inv(G_Z, gam, part, st));
-                GenOp g = genop0();
-                g.nmi = 1;
-                g.Mi[0] = Pb;
-                g.ma_mult[0] = 1.0;
-                g.M = gam;
-                g.hasY = 1;
-                g.Y = Ptmp;
-                g.ym = 1.0;
-                BK_TRY(genop(g));
-                std::swap(Pb, Ptmp);
-            }
+            if (orth) BK_TRY(cholesky_basis());  // before V = A P
             BK_TRY(dslash_active(Pb, Vb, Pb));  // V = A P
             BK_TRY(gram2(Rt, Vb, R, G_V, G_RR));  // R~^H V, R~^H R
             BK_TRY(factor(G_V, info_a));  // R~^H V, used for alpha and beta
@@ -1303,20 +1304,17 @@ struct Solve {
         part.active = all_systems(nsys);
         for (const auto& cr : col_runs(need)) {
             if (mixed) {
-                dim3 grid((V + 127) / 128, cr.second);
-                k_accum<<<grid, 128, 0, st>>>(field_cols(X64, cr.first), field_cols(Xlo, cr.first), V);
-                BK_CUDA_TRY(cudaGetLastError());
+                BK_TRY(launch_accum(X64, Xlo, cr.first / 2, cr.second / 2, st));
                 launches++;
             }
             BK_TRY(dslash(BK_FP64, X64, R64, B64, cr.first, cr.second, 1));
         }
         BK_TRY(norms_runs(BK_FP64, R64, need));
-        BK_TRY(launch_unpack(BK_FP64, X64, Xc, Lt, st));
-        launches++;
+        BK_TRY(get_caller_block(X64, Xc));
         BK_TRY(readback());
         for (int s = 0; s < nsys; ++s)
             if ((need >> s) & 1u)
-                for (int j = part.col0[s]; j < part.col0[s + 1]; ++j) true_res[j] = rel(j);
+                for (int j = part.col0[s]; j < part.col0[s] + part.L[s]; ++j) true_res[j] = rel(j);
         return BK_OK;
     }
 };
@@ -1333,10 +1331,10 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
     BK_CHECK_ARG(prm->tol > 0 && prm->maxiter >= 0, "tol must be > 0 and maxiter >= 0");
     BK_CHECK_ARG(prm->rtilde_mode >= 0 && prm->rtilde_mode <= 2, "rtilde_mode must be 0, 1 or 2");
     BK_CHECK_ARG(prm->rtilde_mode != 2 || prm->rtilde, "rtilde_mode 2 needs the rtilde block");
-    int Lt = 0;
+    int Lu = 0;
     for (int s = 0; s < nsys; ++s) {
-        BK_CHECK_ARG(Ls[s] >= 1, "every system needs L >= 1");
-        Lt += Ls[s];
+        BK_CHECK_ARG(Ls[s] >= 1 && Ls[s] <= 128, "every system needs 1 <= L <= 128");
+        Lu += Ls[s];
     }
     if (!c->has_gauge || !c->has_clover) {
         bk_set_error("solve needs bk_upload_gauge and bk_build_clover first");
@@ -1350,15 +1348,23 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
     S.prm = prm;
     S.st = st;
     S.nsys = nsys;
-    S.Lt = Lt;
     S.V = c->V;
     S.P = prm->prec;
     S.method = prm->method;
     S.mixed = prm->prec != BK_FP64;
     S.part = make_part(nsys, Ls);
-    S.kcol.resize(Lt);
-    for (int s = 0; s < nsys; ++s)
-        for (int j = S.part.col0[s]; j < S.part.col0[s + 1]; ++j) S.kcol[j] = kappa[s];
+    const int Lt = S.part.col0[nsys];  // device columns: every system padded to an even width
+    S.Lt = Lt;
+    S.Lu = Lu;
+    S.kcol.assign(Lt, 0.0);
+    S.dcol_h.resize(Lu);
+    for (int s = 0, ju = 0; s < nsys; ++s) {
+        S.ucol0[s] = ju;
+        for (int j = 0; j < Ls[s]; ++j, ++ju) {
+            S.kcol[S.part.col0[s] + j] = kappa[s];
+            S.dcol_h[ju] = S.part.col0[s] + j;
+        }
+    }
     S.bnorm.assign(Lt, 1.0);
     S.done.assign(nsys, 0);
     S.rmax_since.assign(nsys, 0.0);
@@ -1374,28 +1380,15 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
     S.true_res.assign(Lt, 0.0);
     S.res_known.assign(nsys, 0);
 
-    const size_t canon_bytes = (size_t)Lt * c->V * 12 * sizeof(double2);
-    const double* Bd = B;
-    double* Xd = X;
-    if (prm->buffers_on_host) {
-        BK_TRY(c->canonB.ensure(canon_bytes));
-        BK_TRY(c->canonX.ensure(canon_bytes));
-        BK_CUDA_TRY(cudaMemcpyAsync(c->canonB.p, B, canon_bytes, cudaMemcpyHostToDevice, st));
-        if (prm->x0_given) BK_CUDA_TRY(cudaMemcpyAsync(c->canonX.p, X, canon_bytes, cudaMemcpyHostToDevice, st));
-        Bd = c->canonB.as<double>();
-        Xd = c->canonX.as<double>();
-    }
-
-    BK_TRY(S.setup(Bd, Xd));
+    // host buffers (buffers_on_host) are copied in and out a chunk of
+    // columns at a time inside setup() and finish()
+    BK_TRY(S.setup(B, X));
     if (prm->method == BK_BICGGR)
         BK_TRY(S.iterate_bicggr());
     else
         BK_TRY(S.iterate_bicgstab());
-    BK_TRY(S.finish(Xd));
-    if (prm->buffers_on_host) {
-        BK_CUDA_TRY(cudaMemcpyAsync(X, Xd, canon_bytes, cudaMemcpyDeviceToHost, st));
-        BK_CUDA_TRY(cudaStreamSynchronize(st));
-    }
+    BK_TRY(S.finish(X));
+    BK_CUDA_TRY(cudaStreamSynchronize(st));
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (c->verbose)
         fprintf(stderr, "[bkrylov] solve: %.1f ms wall, %d syncs waiting %.1f ms, %lld launches, %d dslash (%.1f ms events)\n",
@@ -1411,7 +1404,7 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
         in.reliable_updates = S.nrel[s];
         in.breakdown = S.done[s] == 2;
         double tm = 0, rm = 0;
-        for (int j = S.part.col0[s]; j < S.part.col0[s + 1]; ++j) {
+        for (int j = S.part.col0[s]; j < S.part.col0[s] + S.part.L[s]; ++j) {
             tm = std::max(tm, S.true_res[j]);
             if (in.true_res) in.true_res[j - S.part.col0[s]] = S.true_res[j];
         }

@@ -7,32 +7,35 @@
 #include "bk_common.cuh"
 
 // ---------------------------------------------------------------- gauge.cu
-bk_status launch_gauge_convert(const double* Uin_dev, double2* U64, float2* U32, int V, cudaStream_t st);
+bk_status launch_gauge_convert(const double* Uin_dev, double2* U64, float4* U32, int V, cudaStream_t st);
 bk_status launch_clover_build(const double2* U64, double2* C64, float4* C32, const int dims[4], double csw,
                               cudaStream_t st);
 
 // ---------------------------------------------------------------- dslash.cu
 struct DslashOp {
     Field x, y, b;         // y = D x, or y = b - D x when residual != 0
-    const void* U;         // gauge [4][9][V], double2 (FP64) or float2
-    const void* clov;      // packed clover, double2 [36][V] or float4 [18][V]
+    const void* U;         // FP64: [4][9][V] double2; FP32/FP16: packed-pair links (gauge.cu)
+    const void* clov;      // FP64: [36][V] double2; FP32/FP16: packed-pair clover (gauge.cu)
     int dims[4];
     int V;
-    int col0, ncol;        // columns [col0, col0 + ncol) of x, y, b
+    int col0, ncol;        // columns [col0, col0 + ncol) of x, y, b (FP32/FP16: col0 even,
+                           // the launch covers whole pairs)
     int residual;
     const double* kappa;   // host array, ncol entries (kappa of column col0 + j)
-    int site_block;        // launch shape: sites per thread block (0 = default)
-    int col_block;         // column groups per thread block (0 = default)
-    int rpt;               // columns per thread: 1, 2 or 4 (0 = 1; FP64 always 1)
-    int pipe;              // FP32 only: 1 = cp.async-pipelined kernel (rpt 1 or 2)
+    int threads;           // launch shape: threads per block (0 = default)
+    int variant;           // FP32/FP16: 1 = register cap for 1 block of 256 per SM, else 2
 };
 bk_status launch_dslash(int prec, const DslashOp& op, cudaStream_t st);
 
-// canonical FP64 [col][site][12] complex <-> device layout
-bk_status launch_pack(int prec, const double* canon, Field f, int L, cudaStream_t st);
-bk_status launch_unpack(int prec, Field f, double* canon, int L, cudaStream_t st);
-// device layout conversion between precisions (same column count)
-bk_status launch_cast(int pin, Field in, int pout, Field out, int L, cudaStream_t st);
+// canonical FP64 columns <-> device layout.  Canonical column j of the chunk
+// (ncan columns starting at canon) is device column dcol[j] (dcol a device
+// array) or dbase + j (dcol == nullptr).
+bk_status launch_pack(int prec, const double* canon, int ncan, const int* dcol, int dbase, Field f, cudaStream_t st);
+bk_status launch_unpack(int prec, Field f, const int* dcol, int dbase, double* canon, int ncan, cudaStream_t st);
+// zero device column c of f
+bk_status launch_zero_col(int prec, Field f, int c, cudaStream_t st);
+// device layout conversion between precisions over pairs [0, np) of two views
+bk_status launch_cast(int pin, Field in, int pout, Field out, int np, cudaStream_t st);
 // canonical gamma_5
 bk_status launch_gamma5_canon(const double* X, double* Y, long long nsites_cols, cudaStream_t st);
 
@@ -42,34 +45,46 @@ typedef unsigned long long sysmask;
 // every system of an nsys-system partition
 inline sysmask all_systems(int nsys) { return nsys >= 64 ? ~0ull : ((1ull << nsys) - 1ull); }
 
-// Partition of the columns into independent systems: system s owns columns
-// [col0[s], col0[s+1]).  coef_off[s] = offset (in complex entries) of system
-// s's L_s x L_s matrix inside a packed coefficient array.
+// Partition of the columns into independent systems.  System s has L[s]
+// columns, stored at device columns [col0[s], col0[s] + L[s]); col0[s] is
+// even (a system starts on a column pair) and col0[s + 1] = col0[s] +
+// L[s] rounded up to even, so an odd system leaves its last pair's second
+// column as padding that belongs to no system.  coef_off[s] = offset (in
+// complex entries) of system s's L[s] x L[s] matrix inside a packed
+// coefficient array.
 struct SysPart {
     int nsys;
     int col0[BK_MAX_SYS + 1];
+    int L[BK_MAX_SYS];
     int coef_off[BK_MAX_SYS + 1];
     sysmask active;        // bit s set: system s is still iterating
 };
 SysPart make_part(int nsys, const int* Ls);
 SysPart single_part(int L);
+inline int part_pairs(const SysPart& p) { return p.col0[p.nsys] / 2; }
 
-// Block-diagonal Gram matrices G_s = A_s^H B_s (packed by coef_off, complex FP64).
-// `partial` is scratch of gram_partial_bytes() bytes.
+// Block-diagonal Gram matrices G_s = A_s^H B_s (packed by coef_off, complex
+// FP64) over the active systems.  `partial` is scratch of
+// gram_partial_bytes() bytes.
 size_t gram_partial_bytes(const SysPart& p, int V);
 bk_status launch_gram(int prec, Field A, Field B, const SysPart& p, double* G, double* partial, int V,
                       cudaStream_t st);
-// G = A^H B and G2 = A^H B2, reading A once where the small-system kernel applies.
+// G = A^H B and G2 = A^H B2 in one pass over A.
 bk_status launch_gram2(int prec, Field A, Field B, Field B2, const SysPart& p, double* G, double* G2,
                        double* partial, int V, cudaStream_t st);
+// The Gram reduction with caller-provided partial-sum storage of `slots`
+// complex FP64 entries (fewer thread blocks when it holds fewer than the
+// usual number).  Returns INVALID_ARG if one block's entries do not fit.
+bk_status launch_gram_slots(int prec, Field A, Field B, const SysPart& p, double* G, double* partial,
+                            long long slots, int V, cudaStream_t st);
 
-// Column dot products: out[k * ldo + j] = (A_k)_j^H (B_k)_j for pairs k < npair
-// (ldo = L when not given).
+// Column dot products over columns [c0, c0 + n) (c0 even):
+// out[k * ldo + j] = (A_k)_j^H (B_k)_j, j relative to c0, for pairs k < npair.
 size_t coldot_partial_bytes(int L, int npair, int V);
-bk_status launch_coldot(int prec, int npair, const Field* A, const Field* B, int L, double* out,
-                        double* partial, int V, cudaStream_t st, int ldo = 0);
+bk_status launch_coldot(int prec, int npair, const Field* A, const Field* B, int c0, int n, double* out,
+                        int ldo, double* partial, int V, cudaStream_t st);
 
-// Y_j = Z_j + c_s * sum_{i in s} X_i M_s[i][j]  (Z may be null; c per system, complex FP64)
+// Y_j = Z_j + c_s * sum_{i in s} X_i M_s[i][j]  (Z may be absent; c per system, complex FP64)
 bk_status launch_xmy(int prec, Field X, const double* M, const double* c_dev, Field Z, bool hasZ, Field Y,
                      const SysPart& p, int V, cudaStream_t st);
 
@@ -103,16 +118,19 @@ struct GenOp {
     const int* skip;
     SysPart p;
     // optional: squared norms of the Y columns, as per-block partial sums
-    // ynorm[col * genop_norm_blocks(V) + b] (FP64), summed by launch_norm_finish
+    // ynorm[b * ncols + col] (FP64), summed by launch_norm_finish
     double* ynorm;
 };
-// *ynorm_done = whether the kernel that ran filled g.ynorm (only the
-// small-system FP32 kernel does).
+// *ynorm_done = whether the kernel filled g.ynorm
 bk_status launch_genop(int prec, const GenOp& g, int V, cudaStream_t st, bool* ynorm_done = nullptr);
-int genop_norm_blocks(int V);
-// out[2 j] = sum_b ynorm[j * genop_norm_blocks(V) + b], out[2 j + 1] = 0 for
-// columns j in [c0, c0 + n).
-bk_status launch_norm_finish(const double* ynorm, int c0, int n, double* out, int V, cudaStream_t st);
+// partial-sum rows of the fused norms (size of g.ynorm: rows * padded columns doubles)
+int genop_norm_rows(int V);
+// out[2 j] = sum_b ynorm[b * ncols + j], out[2 j + 1] = 0 for columns j in [c0, c0 + n).
+bk_status launch_norm_finish(const double* ynorm, int ncols, int c0, int n, double* out, int V, cudaStream_t st);
+// X64[cols] += Xlo[cols], Xlo[cols] = 0 over pairs [p0, p0 + np)
+bk_status launch_accum(Field X64, Field Xlo, int p0, int np, cudaStream_t st);
+// seeded complex Gaussian block (counter-based, independent of the layout)
+bk_status launch_random(int prec, Field f, int L, uint64_t seed, cudaStream_t st);
 
 // ---------------------------------------------------------------- force.cu
 size_t force_scratch_bytes(int V);
@@ -124,6 +142,9 @@ bk_status launch_gauge_force(const double2* U64, const double* X, const double* 
 // result_dev (complex FP64, device) = sum conj(A) B over ncomplex entries
 bk_status launch_canon_dot(const double* A, const double* B, long long ncomplex, double* result_dev,
                            void* scratch, cudaStream_t st);
+// result_dev = scale * sum conj(A) (B - Cm) over ncomplex entries
+bk_status launch_canon_dot_diff(const double* A, const double* B, const double* Cm, long long ncomplex, double scale,
+                                double* result_dev, void* scratch, cudaStream_t st);
 
 // L x L solves split in two: factor G_s once (LU: complex FP64 per system at
 // coef_off, piv: int per column), then solve any number of right-hand sides

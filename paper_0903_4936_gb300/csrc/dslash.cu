@@ -1,16 +1,28 @@
 // Multi-RHS O(a)-improved Wilson-Dirac operator, Eq. (wd-op) of arXiv:0903.4936,
 // and the layout-conversion kernels around it.
 //
-// One thread computes one (site, column) output spinor:
 //     y = x - kappa_c * ( sum_mu [(1 - gamma_mu) U_mu(n) x(n+mu)
 //                                 + (1 + gamma_mu) U_mu(n-mu)^+ x(n-mu)] + C(n) x(n) )
-// The threads of a block cover `SX` consecutive sites times `BY` columns, so
-// every gauge link and clover block a block needs is fetched from DRAM once
-// and served to all of its columns from L1 (the multi-vector reuse the paper
-// exploits on its CPU, Section 4.3).  Each (1 -+ gamma_mu) has rank two: the
-// neighbour spinor is projected to two colour vectors, multiplied by the 3x3
-// link, and expanded again.  With the printed gamma matrices, for projector
-// (1 + s gamma_mu) (s = -1 forward, +1 backward) and h = (h0, h1):
+//
+// FP32 / FP16 storage (k_dslash_pair): one thread per site and column pair.
+// Blocks are RHS-interleaved (all columns of a site in one row), so the
+// lanes of a warp read one contiguous line per spinor component and share
+// every gauge link and clover entry of their site (one transaction for the
+// warp).  All arithmetic is on pairs {column 2p, column 2p + 1} with the
+// packed FP32x2 multiply-add of sm_100+, against links and clover entries
+// stored as duplicated pairs {u_r, u_r}, {u_i, u_i}, {-u_i, -u_i}, so that
+// a complex product costs four packed instructions for two columns.  The
+// clover term is applied first (out = x - kappa C x needs x(n) only once);
+// each of the eight hops then adds -kappa times its term directly.
+//
+// FP64 / double-float (k_dslash_col): one thread per site and column, FP64
+// links and clover in [element][site] order (the FP64 pipe, not memory,
+// bounds this kernel on GB300).
+//
+// Each (1 -+ gamma_mu) has rank two: the neighbour spinor is projected to two
+// colour vectors, multiplied by the 3x3 link, and expanded again.  With the
+// printed gamma matrices, for projector (1 + s gamma_mu) (s = -1 forward,
+// +1 backward) and h = (h0, h1):
 //   mu=x: h0 = q0 - i s q3, h1 = q1 - i s q2;  out = (h0, h1,  i s h1,  i s h0)
 //   mu=y: h0 = q0 -   s q3, h1 = q1 +   s q2;  out = (h0, h1,    s h1,   -s h0)
 //   mu=z: h0 = q0 - i s q2, h1 = q1 + i s q3;  out = (h0, h1,  i s h0, -i s h1)
@@ -22,14 +34,633 @@
 
 namespace {
 
-template <int P>
-struct DArgs {
+// ================================================================= FP32 / FP16: packed pairs
+
+struct DPairArgs {
     Field x, y, b;
-    const typename Prec<P>::link* __restrict__ U;
-    const typename Prec<P>::clov* __restrict__ C;
+    const float4* __restrict__ U;  // packed-pair links, BK_LINK32_F4 float4 per (mu, site)
+    const float4* __restrict__ C;  // packed-pair clover, BK_CLOV32_F4 float4 per site
     int L[4], st[4];
-    int V, col0, ncol, residual, SX;
-    int groups_fast;  // 1: blockIdx.x = column-group block, blockIdx.y = site block
+    int V, p0, npl, residual;
+    float2 nk[BK_MAX_COLS / 2];  // {-kappa_2p, -kappa_2p+1} of launch pair p - p0
+};
+
+struct Hop {
+    float2 r[6], i[6];  // projected half spinor: colour a of h0 at a, of h1 at 3 + a
+};
+
+// projection (1 + S gamma_mu) x -> h for one column pair and colour a
+template <int MU, int S>
+__device__ __forceinline__ void project_pair(const float2 (&qr)[12], const float2 (&qi)[12], Hop& h, int a) {
+    {
+        const int c0 = a, c1 = 3 + a, c2 = 6 + a, c3 = 9 + a;
+        if constexpr (MU == 0) {
+            if constexpr (S > 0) {  // h0 = q0 - i q3, h1 = q1 - i q2
+                h.r[a] = padd(qr[c0], qi[c3]);
+                h.i[a] = psub(qi[c0], qr[c3]);
+                h.r[3 + a] = padd(qr[c1], qi[c2]);
+                h.i[3 + a] = psub(qi[c1], qr[c2]);
+            } else {  // h0 = q0 + i q3, h1 = q1 + i q2
+                h.r[a] = psub(qr[c0], qi[c3]);
+                h.i[a] = padd(qi[c0], qr[c3]);
+                h.r[3 + a] = psub(qr[c1], qi[c2]);
+                h.i[3 + a] = padd(qi[c1], qr[c2]);
+            }
+        } else if constexpr (MU == 1) {
+            if constexpr (S > 0) {  // h0 = q0 - q3, h1 = q1 + q2
+                h.r[a] = psub(qr[c0], qr[c3]);
+                h.i[a] = psub(qi[c0], qi[c3]);
+                h.r[3 + a] = padd(qr[c1], qr[c2]);
+                h.i[3 + a] = padd(qi[c1], qi[c2]);
+            } else {  // h0 = q0 + q3, h1 = q1 - q2
+                h.r[a] = padd(qr[c0], qr[c3]);
+                h.i[a] = padd(qi[c0], qi[c3]);
+                h.r[3 + a] = psub(qr[c1], qr[c2]);
+                h.i[3 + a] = psub(qi[c1], qi[c2]);
+            }
+        } else if constexpr (MU == 2) {
+            if constexpr (S > 0) {  // h0 = q0 - i q2, h1 = q1 + i q3
+                h.r[a] = padd(qr[c0], qi[c2]);
+                h.i[a] = psub(qi[c0], qr[c2]);
+                h.r[3 + a] = psub(qr[c1], qi[c3]);
+                h.i[3 + a] = padd(qi[c1], qr[c3]);
+            } else {  // h0 = q0 + i q2, h1 = q1 - i q3
+                h.r[a] = psub(qr[c0], qi[c2]);
+                h.i[a] = padd(qi[c0], qr[c2]);
+                h.r[3 + a] = padd(qr[c1], qi[c3]);
+                h.i[3 + a] = psub(qi[c1], qr[c3]);
+            }
+        } else {
+            if constexpr (S > 0) {
+                h.r[a] = qr[c0];
+                h.i[a] = qi[c0];
+                h.r[3 + a] = qr[c1];
+                h.i[3 + a] = qi[c1];
+            } else {
+                h.r[a] = qr[c2];
+                h.i[a] = qi[c2];
+                h.r[3 + a] = qr[c3];
+                h.i[3 + a] = qi[c3];
+            }
+        }
+    }
+}
+
+// acc += -kappa * expand(w) for projector (1 + S gamma_mu); nk = {-kappa}, pk = {+kappa}
+template <int MU, int S>
+__device__ __forceinline__ void reconstruct_pair(const Hop& w, float2 nk, float2 pk, float2 (&ar)[12],
+                                                 float2 (&ai)[12]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int c0 = a, c1 = 3 + a, c2 = 6 + a, c3 = 9 + a;
+        const float2 w0r = w.r[a], w0i = w.i[a], w1r = w.r[3 + a], w1i = w.i[3 + a];
+        if constexpr (MU == 3) {
+            const float2 n2 = padd(nk, nk);
+            if constexpr (S > 0) {
+                ar[c0] = pfma(n2, w0r, ar[c0]);
+                ai[c0] = pfma(n2, w0i, ai[c0]);
+                ar[c1] = pfma(n2, w1r, ar[c1]);
+                ai[c1] = pfma(n2, w1i, ai[c1]);
+            } else {
+                ar[c2] = pfma(n2, w0r, ar[c2]);
+                ai[c2] = pfma(n2, w0i, ai[c2]);
+                ar[c3] = pfma(n2, w1r, ar[c3]);
+                ai[c3] = pfma(n2, w1i, ai[c3]);
+            }
+        } else {
+            ar[c0] = pfma(nk, w0r, ar[c0]);
+            ai[c0] = pfma(nk, w0i, ai[c0]);
+            ar[c1] = pfma(nk, w1r, ar[c1]);
+            ai[c1] = pfma(nk, w1i, ai[c1]);
+            if constexpr (MU == 0) {
+                // lower = (i S w1, i S w0); i w = (-w_i, w_r)
+                if constexpr (S > 0) {
+                    ar[c2] = pfma(pk, w1i, ar[c2]);
+                    ai[c2] = pfma(nk, w1r, ai[c2]);
+                    ar[c3] = pfma(pk, w0i, ar[c3]);
+                    ai[c3] = pfma(nk, w0r, ai[c3]);
+                } else {
+                    ar[c2] = pfma(nk, w1i, ar[c2]);
+                    ai[c2] = pfma(pk, w1r, ai[c2]);
+                    ar[c3] = pfma(nk, w0i, ar[c3]);
+                    ai[c3] = pfma(pk, w0r, ai[c3]);
+                }
+            } else if constexpr (MU == 1) {
+                // lower = (S w1, -S w0)
+                if constexpr (S > 0) {
+                    ar[c2] = pfma(nk, w1r, ar[c2]);
+                    ai[c2] = pfma(nk, w1i, ai[c2]);
+                    ar[c3] = pfma(pk, w0r, ar[c3]);
+                    ai[c3] = pfma(pk, w0i, ai[c3]);
+                } else {
+                    ar[c2] = pfma(pk, w1r, ar[c2]);
+                    ai[c2] = pfma(pk, w1i, ai[c2]);
+                    ar[c3] = pfma(nk, w0r, ar[c3]);
+                    ai[c3] = pfma(nk, w0i, ai[c3]);
+                }
+            } else {
+                // MU == 2: lower = (i S w0, -i S w1)
+                if constexpr (S > 0) {
+                    ar[c2] = pfma(pk, w0i, ar[c2]);
+                    ai[c2] = pfma(nk, w0r, ai[c2]);
+                    ar[c3] = pfma(nk, w1i, ar[c3]);
+                    ai[c3] = pfma(pk, w1r, ai[c3]);
+                } else {
+                    ar[c2] = pfma(nk, w0i, ar[c2]);
+                    ai[c2] = pfma(pk, w0r, ai[c2]);
+                    ar[c3] = pfma(pk, w1i, ar[c3]);
+                    ai[c3] = pfma(nk, w1r, ai[c3]);
+                }
+            }
+        }
+    }
+}
+
+// w = U h (forward) or U^+ h (backward) for both half-spinor vectors.  Link
+// element e = 3 row + col: {u_r, u_r, u_i, u_i} at float4 e, {-u_i, -u_i} at
+// float2 18 + e.  One output row at a time: three link elements are live.
+template <bool DAG>
+__device__ __forceinline__ void link_mul(const float4* __restrict__ u4, const Hop& h, Hop& w) {
+    const float2* u2 = reinterpret_cast<const float2*>(u4);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float2 ur[3], ui[3], un[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int e = DAG ? 3 * j + i : 3 * i + j;
+            const float4 q = __ldg(u4 + e);
+            ur[j] = make_float2(q.x, q.y);
+            ui[j] = make_float2(q.z, q.w);
+            un[j] = __ldg(u2 + 18 + e);
+        }
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            float2 wr = make_float2(0.f, 0.f), wi = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float2 hr = h.r[3 * hh + j], hi = h.i[3 * hh + j];
+                if constexpr (!DAG) {  // U_ij h_j: (u_r h_r - u_i h_i, u_r h_i + u_i h_r)
+                    wr = pfma(ur[j], hr, wr);
+                    wr = pfma(un[j], hi, wr);
+                    wi = pfma(ur[j], hi, wi);
+                    wi = pfma(ui[j], hr, wi);
+                } else {  // conj(U_ji) h_j: (u_r h_r + u_i h_i, u_r h_i - u_i h_r)
+                    wr = pfma(ur[j], hr, wr);
+                    wr = pfma(ui[j], hi, wr);
+                    wi = pfma(ur[j], hi, wi);
+                    wi = pfma(un[j], hr, wi);
+                }
+            }
+            w.r[3 * hh + i] = wr;
+            w.i[3 * hh + i] = wi;
+        }
+    }
+}
+
+template <int P, int MU, int S>
+__device__ __forceinline__ void hop_pair(const DPairArgs& a, int nb, int p, const float4* __restrict__ link,
+                                         float2 nk, float2 pk, float2 (&ar)[12], float2 (&ai)[12]) {
+    Hop h, w;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {  // the four spin components of colour c
+        float2 qr[12], qi[12];
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) {
+            // the t projector reads only two of the four spins
+            if (MU == 3 && ((S > 0) != (sp < 2))) continue;
+            load_elem<P>(a.x, nb, 3 * sp + c, p, qr[3 * sp + c], qi[3 * sp + c]);
+        }
+        Hop hc;
+        project_pair<MU, S>(qr, qi, hc, c);
+        h.r[c] = hc.r[c];
+        h.i[c] = hc.i[c];
+        h.r[3 + c] = hc.r[3 + c];
+        h.i[3 + c] = hc.i[3 + c];
+    }
+    if constexpr (P == BK_FP16) {  // the projection is linear: scale the 12 projected pairs
+        const float2 sc = pair_scale<P>(a.x, nb, p);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            h.r[k] = pmul(h.r[k], sc);
+            h.i[k] = pmul(h.i[k], sc);
+        }
+    }
+    link_mul<(S > 0)>(link, h, w);
+    reconstruct_pair<MU, S>(w, nk, pk, ar, ai);
+}
+
+template <int P, int MU>
+__device__ __forceinline__ void hop_dir_pair(const DPairArgs& a, const int (&co)[4], int n, int p, float2 nk,
+                                             float2 pk, float2 (&ar)[12], float2 (&ai)[12]) {
+    const int Lm = a.L[MU], sm = a.st[MU];
+    const int nf = co[MU] == Lm - 1 ? n - (Lm - 1) * sm : n + sm;
+    const int nb = co[MU] == 0 ? n + (Lm - 1) * sm : n - sm;
+    // forward: (1 - gamma_mu) U_mu(n) x(n + mu)
+    hop_pair<P, MU, -1>(a, nf, p, a.U + ((size_t)MU * a.V + n) * BK_LINK32_F4, nk, pk, ar, ai);
+    // backward: (1 + gamma_mu) U_mu(n - mu)^+ x(n - mu)
+    hop_pair<P, MU, +1>(a, nb, p, a.U + ((size_t)MU * a.V + nb) * BK_LINK32_F4, nk, pk, ar, ai);
+}
+
+// out = q - kappa C q for one chiral 6x6 Hermitian block pair (see gauge.cu
+// for the packed-pair clover order); the blocks act on u + l and u - l.
+__device__ __forceinline__ void clover_pair(const float4* __restrict__ c4, const float2 (&qr)[12],
+                                            const float2 (&qi)[12], float2 nk, float2 (&ar)[12], float2 (&ai)[12]) {
+    float2 yr[2][6], yi[2][6];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        float2 vr[6], vi[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            vr[k] = b == 0 ? padd(qr[k], qr[k + 6]) : psub(qr[k], qr[k + 6]);
+            vi[k] = b == 0 ? padd(qi[k], qi[k + 6]) : psub(qi[k], qi[k + 6]);
+        }
+        const float2* c2 = reinterpret_cast<const float2*>(c4);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const float2 d = __ldg(c2 + 90 + 6 * b + i);
+            yr[b][i] = pmul(d, vr[i]);
+            yi[b][i] = pmul(d, vi[i]);
+        }
+        int q = 0;
+#pragma unroll
+        for (int i = 1; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j < i; ++j, ++q) {
+                const float4 A = __ldg(c4 + 15 * b + q);
+                const float2 AR = make_float2(A.x, A.y), AI = make_float2(A.z, A.w);
+                const float2 NAI = __ldg(c2 + 60 + 15 * b + q);
+                // y_i += A v_j
+                yr[b][i] = pfma(AR, vr[j], yr[b][i]);
+                yr[b][i] = pfma(NAI, vi[j], yr[b][i]);
+                yi[b][i] = pfma(AR, vi[j], yi[b][i]);
+                yi[b][i] = pfma(AI, vr[j], yi[b][i]);
+                // y_j += conj(A) v_i
+                yr[b][j] = pfma(AR, vr[i], yr[b][j]);
+                yr[b][j] = pfma(AI, vi[i], yr[b][j]);
+                yi[b][j] = pfma(AR, vi[i], yi[b][j]);
+                yi[b][j] = pfma(NAI, vr[i], yi[b][j]);
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        ar[k] = pfma(nk, padd(yr[0][k], yr[1][k]), qr[k]);
+        ai[k] = pfma(nk, padd(yi[0][k], yi[1][k]), qi[k]);
+        ar[k + 6] = pfma(nk, psub(yr[0][k], yr[1][k]), qr[k + 6]);
+        ai[k + 6] = pfma(nk, psub(yi[0][k], yi[1][k]), qi[k + 6]);
+    }
+}
+
+template <int P, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_dslash_pair(const __grid_constant__ DPairArgs a) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long long)a.V * a.npl) return;
+    const int n = (int)(g / a.npl);
+    const int pl = (int)(g - (long long)n * a.npl);
+    const int p = a.p0 + pl;
+    int co[4];
+    {
+        int r = n;
+        co[0] = r % a.L[0];
+        r /= a.L[0];
+        co[1] = r % a.L[1];
+        r /= a.L[1];
+        co[2] = r % a.L[2];
+        co[3] = r / a.L[2];
+    }
+    const float2 nk = a.nk[pl];
+    const float2 pk = make_float2(-nk.x, -nk.y);
+    float2 ar[12], ai[12];
+    {   // out = x - kappa C x
+        float2 qr[12], qi[12];
+        load_pair<P>(a.x, n, p, qr, qi);
+        clover_pair(a.C + (size_t)n * BK_CLOV32_F4, qr, qi, nk, ar, ai);
+    }
+    hop_dir_pair<P, 0>(a, co, n, p, nk, pk, ar, ai);
+    hop_dir_pair<P, 1>(a, co, n, p, nk, pk, ar, ai);
+    hop_dir_pair<P, 2>(a, co, n, p, nk, pk, ar, ai);
+    hop_dir_pair<P, 3>(a, co, n, p, nk, pk, ar, ai);
+    if (a.residual) {  // b - D x
+        float2 br[12], bi[12];
+        load_pair<P>(a.b, n, p, br, bi);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            ar[k] = psub(br[k], ar[k]);
+            ai[k] = psub(bi[k], ai[k]);
+        }
+    }
+    store_pair<P>(a.y, n, p, ar, ai);
+}
+
+// ----------------------------------------------------------------- colour-split form
+//
+// The same operator with three threads per (site, column pair), one per
+// colour c: each keeps only the four spin components of its colour (a
+// quarter of the accumulators), loads only its colour's spin components of
+// each neighbour, projects them, and receives the other two colours'
+// projected half spinors from its two partner lanes by warp shuffles; it
+// then multiplies row c of the link (column c for U^+) and expands into its
+// own components.  Lanes 3 j + c (j < 10) of a warp serve ten (site, pair)
+// slots; lanes 30 and 31 repeat slot 9 and store nothing.  Fewer registers
+// per thread and three times the threads per site give the memory system
+// more independent warps to overlap.
+
+template <int MU, int S>
+__device__ __forceinline__ void project_colour(const float2 (&qr)[4], const float2 (&qi)[4], float2& h0r,
+                                               float2& h0i, float2& h1r, float2& h1i) {
+    // qr/qi[s] = spin s of the thread's colour
+    if constexpr (MU == 0) {
+        if constexpr (S > 0) {
+            h0r = padd(qr[0], qi[3]); h0i = psub(qi[0], qr[3]);
+            h1r = padd(qr[1], qi[2]); h1i = psub(qi[1], qr[2]);
+        } else {
+            h0r = psub(qr[0], qi[3]); h0i = padd(qi[0], qr[3]);
+            h1r = psub(qr[1], qi[2]); h1i = padd(qi[1], qr[2]);
+        }
+    } else if constexpr (MU == 1) {
+        if constexpr (S > 0) {
+            h0r = psub(qr[0], qr[3]); h0i = psub(qi[0], qi[3]);
+            h1r = padd(qr[1], qr[2]); h1i = padd(qi[1], qi[2]);
+        } else {
+            h0r = padd(qr[0], qr[3]); h0i = padd(qi[0], qi[3]);
+            h1r = psub(qr[1], qr[2]); h1i = psub(qi[1], qi[2]);
+        }
+    } else if constexpr (MU == 2) {
+        if constexpr (S > 0) {
+            h0r = padd(qr[0], qi[2]); h0i = psub(qi[0], qr[2]);
+            h1r = psub(qr[1], qi[3]); h1i = padd(qi[1], qr[3]);
+        } else {
+            h0r = psub(qr[0], qi[2]); h0i = padd(qi[0], qr[2]);
+            h1r = padd(qr[1], qi[3]); h1i = psub(qi[1], qr[3]);
+        }
+    } else {
+        if constexpr (S > 0) {
+            h0r = qr[0]; h0i = qi[0]; h1r = qr[1]; h1i = qi[1];
+        } else {
+            h0r = qr[2]; h0i = qi[2]; h1r = qr[3]; h1i = qi[3];
+        }
+    }
+}
+
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// acc (spins 0..3 of the thread's colour) += -kappa expand(w0, w1)
+template <int MU, int S>
+__device__ __forceinline__ void reconstruct_colour(float2 w0r, float2 w0i, float2 w1r, float2 w1i, float2 nk,
+                                                   float2 pk, float2 (&ar)[4], float2 (&ai)[4]) {
+    if constexpr (MU == 3) {
+        const float2 n2 = padd(nk, nk);
+        const int s0 = S > 0 ? 0 : 2;
+        ar[s0] = pfma(n2, w0r, ar[s0]);
+        ai[s0] = pfma(n2, w0i, ai[s0]);
+        ar[s0 + 1] = pfma(n2, w1r, ar[s0 + 1]);
+        ai[s0 + 1] = pfma(n2, w1i, ai[s0 + 1]);
+    } else {
+        ar[0] = pfma(nk, w0r, ar[0]);
+        ai[0] = pfma(nk, w0i, ai[0]);
+        ar[1] = pfma(nk, w1r, ar[1]);
+        ai[1] = pfma(nk, w1i, ai[1]);
+        if constexpr (MU == 0) {  // lower = (i S w1, i S w0)
+            if constexpr (S > 0) {
+                ar[2] = pfma(pk, w1i, ar[2]); ai[2] = pfma(nk, w1r, ai[2]);
+                ar[3] = pfma(pk, w0i, ar[3]); ai[3] = pfma(nk, w0r, ai[3]);
+            } else {
+                ar[2] = pfma(nk, w1i, ar[2]); ai[2] = pfma(pk, w1r, ai[2]);
+                ar[3] = pfma(nk, w0i, ar[3]); ai[3] = pfma(pk, w0r, ai[3]);
+            }
+        } else if constexpr (MU == 1) {  // lower = (S w1, -S w0)
+            if constexpr (S > 0) {
+                ar[2] = pfma(nk, w1r, ar[2]); ai[2] = pfma(nk, w1i, ai[2]);
+                ar[3] = pfma(pk, w0r, ar[3]); ai[3] = pfma(pk, w0i, ai[3]);
+            } else {
+                ar[2] = pfma(pk, w1r, ar[2]); ai[2] = pfma(pk, w1i, ai[2]);
+                ar[3] = pfma(nk, w0r, ar[3]); ai[3] = pfma(nk, w0i, ai[3]);
+            }
+        } else {  // MU == 2: lower = (i S w0, -i S w1)
+            if constexpr (S > 0) {
+                ar[2] = pfma(pk, w0i, ar[2]); ai[2] = pfma(nk, w0r, ai[2]);
+                ar[3] = pfma(nk, w1i, ar[3]); ai[3] = pfma(pk, w1r, ai[3]);
+            } else {
+                ar[2] = pfma(nk, w0i, ar[2]); ai[2] = pfma(pk, w0r, ai[2]);
+                ar[3] = pfma(pk, w1i, ar[3]); ai[3] = pfma(nk, w1r, ai[3]);
+            }
+        }
+    }
+}
+
+template <int P, int MU, int S>
+__device__ __forceinline__ void hop_colour(const DPairArgs& a, int nb, int p, int c, int base,
+                                           const float4* __restrict__ link, float2 nk, float2 pk, float2 (&ar)[4],
+                                           float2 (&ai)[4]) {
+    float2 qr[4], qi[4];
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+        if (MU == 3 && ((S > 0) != (sp < 2))) {  // the t projector reads two spins
+            qr[sp] = make_float2(0.f, 0.f);
+            qi[sp] = make_float2(0.f, 0.f);
+            continue;
+        }
+        load_elem<P>(a.x, nb, 3 * sp + c, p, qr[sp], qi[sp]);
+    }
+    float2 h0r, h0i, h1r, h1i;
+    project_colour<MU, S>(qr, qi, h0r, h0i, h1r, h1i);
+    if constexpr (P == BK_FP16) {
+        const float2 sc = pair_scale<P>(a.x, nb, p);
+        h0r = pmul(h0r, sc);
+        h0i = pmul(h0i, sc);
+        h1r = pmul(h1r, sc);
+        h1i = pmul(h1i, sc);
+    }
+    // row c of U (forward) or column c of U^+ (backward) times all three colours
+    const float2* u2 = reinterpret_cast<const float2*>(link);
+    float2 w0r = make_float2(0.f, 0.f), w0i = w0r, w1r = w0r, w1i = w0r;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float2 g0r = shfl2(h0r, base + j), g0i = shfl2(h0i, base + j);
+        const float2 g1r = shfl2(h1r, base + j), g1i = shfl2(h1i, base + j);
+        const int e = S > 0 ? 3 * j + c : 3 * c + j;
+        const float4 q = __ldg(link + e);
+        const float2 ur = make_float2(q.x, q.y), ui = make_float2(q.z, q.w), un = __ldg(u2 + 18 + e);
+        if constexpr (S < 0) {  // U_cj h_j
+            w0r = pfma(ur, g0r, w0r); w0r = pfma(un, g0i, w0r);
+            w0i = pfma(ur, g0i, w0i); w0i = pfma(ui, g0r, w0i);
+            w1r = pfma(ur, g1r, w1r); w1r = pfma(un, g1i, w1r);
+            w1i = pfma(ur, g1i, w1i); w1i = pfma(ui, g1r, w1i);
+        } else {  // conj(U_jc) h_j
+            w0r = pfma(ur, g0r, w0r); w0r = pfma(ui, g0i, w0r);
+            w0i = pfma(ur, g0i, w0i); w0i = pfma(un, g0r, w0i);
+            w1r = pfma(ur, g1r, w1r); w1r = pfma(ui, g1i, w1r);
+            w1i = pfma(ur, g1i, w1i); w1i = pfma(un, g1r, w1i);
+        }
+    }
+    reconstruct_colour<MU, S>(w0r, w0i, w1r, w1i, nk, pk, ar, ai);
+}
+
+template <int P, int MU>
+__device__ __forceinline__ void hop_dir_colour(const DPairArgs& a, const int (&co)[4], int n, int p, int c, int base,
+                                               float2 nk, float2 pk, float2 (&ar)[4], float2 (&ai)[4]) {
+    const int Lm = a.L[MU], sm = a.st[MU];
+    const int nf = co[MU] == Lm - 1 ? n - (Lm - 1) * sm : n + sm;
+    const int nb = co[MU] == 0 ? n + (Lm - 1) * sm : n - sm;
+    hop_colour<P, MU, -1>(a, nf, p, c, base, a.U + ((size_t)MU * a.V + n) * BK_LINK32_F4, nk, pk, ar, ai);
+    hop_colour<P, MU, +1>(a, nb, p, c, base, a.U + ((size_t)MU * a.V + nb) * BK_LINK32_F4, nk, pk, ar, ai);
+}
+
+__device__ __forceinline__ float2 sel3(int c, float2 a0, float2 a1, float2 a2) {
+    return c == 0 ? a0 : (c == 1 ? a1 : a2);
+}
+
+template <int P, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_dslash_pc(const __grid_constant__ DPairArgs a) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int slot = lane < 30 ? lane / 3 : 9;
+    const int c = lane < 30 ? lane - 3 * slot : lane - 30;
+    const int base = 3 * slot;  // lane of colour 0 of this slot
+    const long long total = (long long)a.V * a.npl;
+    long long sp = warp * 10 + slot;
+    const bool valid = lane < 30 && sp < total;
+    if (sp >= total) sp = total - 1;  // idle lanes repeat a valid slot (shuffle partners), store nothing
+    const int n = (int)(sp / a.npl);
+    const int pl = (int)(sp - (long long)n * a.npl);
+    const int p = a.p0 + pl;
+    int co[4];
+    {
+        int r = n;
+        co[0] = r % a.L[0];
+        r /= a.L[0];
+        co[1] = r % a.L[1];
+        r /= a.L[1];
+        co[2] = r % a.L[2];
+        co[3] = r / a.L[2];
+    }
+    const float2 nk = a.nk[pl];
+    const float2 pk = make_float2(-nk.x, -nk.y);
+    float2 ar[4], ai[4];
+    {   // out = x - kappa C x for the thread's colour; the chiral blocks act on u + l, u - l
+        float2 vr[2][6], vi[2][6];
+        {
+            float2 qr[12], qi[12];
+            load_pair<P>(a.x, n, p, qr, qi);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                vr[0][k] = padd(qr[k], qr[k + 6]);
+                vi[0][k] = padd(qi[k], qi[k + 6]);
+                vr[1][k] = psub(qr[k], qr[k + 6]);
+                vi[1][k] = psub(qi[k], qi[k + 6]);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {  // acc = x for the thread's colour
+                ar[h] = h == 0 ? sel3(c, qr[0], qr[1], qr[2]) : sel3(c, qr[3], qr[4], qr[5]);
+                ai[h] = h == 0 ? sel3(c, qi[0], qi[1], qi[2]) : sel3(c, qi[3], qi[4], qi[5]);
+                ar[2 + h] = h == 0 ? sel3(c, qr[6], qr[7], qr[8]) : sel3(c, qr[9], qr[10], qr[11]);
+                ai[2 + h] = h == 0 ? sel3(c, qi[6], qi[7], qi[8]) : sel3(c, qi[9], qi[10], qi[11]);
+            }
+        }
+        const float4* c4 = a.C + (size_t)n * BK_CLOV32_F4;
+        const float2* c2 = reinterpret_cast<const float2*>(c4);
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const float2 sg = b == 0 ? nk : pk;  // block 1 enters the lower spins with a minus sign
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                asm volatile("" ::: "memory");
+                const int rr = 3 * h + c;
+                const float2 d = __ldg(c2 + 90 + 6 * b + rr);
+                const float2 vrr = h == 0 ? sel3(c, vr[b][0], vr[b][1], vr[b][2]) : sel3(c, vr[b][3], vr[b][4], vr[b][5]);
+                const float2 vir = h == 0 ? sel3(c, vi[b][0], vi[b][1], vi[b][2]) : sel3(c, vi[b][3], vi[b][4], vi[b][5]);
+                float2 sr = pmul(d, vrr), si = pmul(d, vir);
+#pragma unroll
+                for (int cc = 0; cc < 6; ++cc) {
+                    if (cc == rr) continue;
+                    const bool lower = rr > cc;  // stored entry (rr, cc); else (cc, rr), conjugated
+                    const int e = lower ? rr * (rr - 1) / 2 + cc : cc * (cc - 1) / 2 + rr;
+                    const float4 A = __ldg(c4 + 15 * b + e);
+                    const float2 AR = make_float2(A.x, A.y), AI = make_float2(A.z, A.w);
+                    const float2 NAI = __ldg(c2 + 60 + 15 * b + e);
+                    sr = pfma(AR, vr[b][cc], sr);
+                    sr = pfma(lower ? NAI : AI, vi[b][cc], sr);
+                    si = pfma(AR, vi[b][cc], si);
+                    si = pfma(lower ? AI : NAI, vr[b][cc], si);
+                }
+                // upper spins get -kappa (y0 + y1), lower spins -kappa (y0 - y1)
+                ar[h] = pfma(nk, sr, ar[h]);
+                ai[h] = pfma(nk, si, ai[h]);
+                ar[2 + h] = pfma(sg, sr, ar[2 + h]);
+                ai[2 + h] = pfma(sg, si, ai[2 + h]);
+            }
+        }
+    }
+    asm volatile("" ::: "memory");
+    // a compiler-level fence between directions keeps each direction's loads
+    // in its own stage: fewer registers, more resident warps
+    hop_dir_colour<P, 0>(a, co, n, p, c, base, nk, pk, ar, ai);
+    asm volatile("" ::: "memory");
+    hop_dir_colour<P, 1>(a, co, n, p, c, base, nk, pk, ar, ai);
+    asm volatile("" ::: "memory");
+    hop_dir_colour<P, 2>(a, co, n, p, c, base, nk, pk, ar, ai);
+    asm volatile("" ::: "memory");
+    hop_dir_colour<P, 3>(a, co, n, p, c, base, nk, pk, ar, ai);
+    if (a.residual) {  // b - D x
+        const float2 sc = pair_scale<P>(a.b, n, p);
+#pragma unroll
+        for (int sp2 = 0; sp2 < 4; ++sp2) {
+            float2 br, bi;
+            load_elem<P>(a.b, n, 3 * sp2 + c, p, br, bi);
+            if constexpr (P == BK_FP16) {
+                br = pmul(br, sc);
+                bi = pmul(bi, sc);
+            }
+            ar[sp2] = psub(br, ar[sp2]);
+            ai[sp2] = psub(bi, ai[sp2]);
+        }
+    }
+    if constexpr (P == BK_FP32) {
+        if (valid) {
+            float4* q = (float4*)a.y.data + ((size_t)n * 12 + c) * a.y.np + p;
+#pragma unroll
+            for (int sp2 = 0; sp2 < 4; ++sp2)
+                q[(size_t)3 * sp2 * a.y.np] = make_float4(ar[sp2].x, ar[sp2].y, ai[sp2].x, ai[sp2].y);
+        }
+    } else {
+        // FP16: the column's scale is the largest component over all colours
+        float ma = 0.f, mb = 0.f;
+#pragma unroll
+        for (int sp2 = 0; sp2 < 4; ++sp2) {
+            ma = fmaxf(ma, fmaxf(fabsf(ar[sp2].x), fabsf(ai[sp2].x)));
+            mb = fmaxf(mb, fmaxf(fabsf(ar[sp2].y), fabsf(ai[sp2].y)));
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float oa = __shfl_sync(0xffffffffu, ma, base + j), ob = __shfl_sync(0xffffffffu, mb, base + j);
+            ma = fmaxf(ma, oa);
+            mb = fmaxf(mb, ob);
+        }
+        if (valid) {
+            const float2 inv = make_float2(ma > 0.f ? 1.0f / ma : 0.f, mb > 0.f ? 1.0f / mb : 0.f);
+            uint2* q = (uint2*)a.y.data + ((size_t)n * 12 + c) * a.y.np + p;
+#pragma unroll
+            for (int sp2 = 0; sp2 < 4; ++sp2) {
+                const float2 r = pmul(ar[sp2], inv), i = pmul(ai[sp2], inv);
+                __half2 hr = __floats2half2_rn(r.x, r.y), hi = __floats2half2_rn(i.x, i.y);
+                q[(size_t)3 * sp2 * a.y.np] =
+                    make_uint2(*reinterpret_cast<uint32_t*>(&hr), *reinterpret_cast<uint32_t*>(&hi));
+            }
+            if (c == 0) a.y.norm[(size_t)n * a.y.np + p] = make_float2(ma, mb);
+        }
+    }
+}
+
+// ================================================================= FP64 / double-float: one column per thread
+
+template <int P>
+struct DColArgs {
+    Field x, y, b;
+    const typename Prec<P>::link* __restrict__ U;  // [mu][9][V] double2
+    const typename Prec<P>::clov* __restrict__ C;  // [36][V] double2
+    int L[4], st[4];
+    int V, c0, ncl, residual;
     double kappa[BK_MAX_COLS];
 };
 
@@ -96,92 +727,45 @@ __device__ __forceinline__ void load_link(const L* __restrict__ U, int mu, int s
     }
 }
 
-// Spinor load that leaves the FP16 per-site scale out of the values: the
-// projection is linear, so the scale is applied to the 12 projected reals
-// instead of the 24 loaded ones.  Returns the scale (1 for FP32 / FP64).
-template <int P>
-__device__ __forceinline__ typename Prec<P>::real load_raw(const Field& f, int c, int s,
-                                                           cx<typename Prec<P>::real> (&v)[12]) {
-    if constexpr (P == BK_FP16) {
-        const uint4* p = (const uint4*)f.data + (size_t)c * f.cstride + s;
-        const float sc = f.norm[(size_t)c * f.V + s];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            uint4 q = p[(size_t)k * f.V];
-            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                float2 g = __half22float2(*reinterpret_cast<const __half2*>(&w[m]));
-                v[4 * k + m] = mk(g.x, g.y);
-            }
-        }
-        return sc;
-    } else {
-        load_spinor<P>(f, c, s, v);
-        return typename Prec<P>::real(1);
-    }
-}
-
-// One direction mu, forward and backward hop, for RPT columns of one site.
-template <int P, int MU, int RPT>
-__device__ __forceinline__ void hop_dir(const DArgs<P>& a, const int (&co)[4], int s, int c0, int nr,
-                                        cx<typename Prec<P>::real> (&acc)[RPT][12]) {
+template <int P, int MU>
+__device__ __forceinline__ void hop_dir_col(const DColArgs<P>& a, const int (&co)[4], int n, int c,
+                                            cx<typename Prec<P>::real> (&acc)[12]) {
     using R = typename Prec<P>::real;
     const int Lm = a.L[MU], sm = a.st[MU];
-    const int sf = co[MU] == Lm - 1 ? s - (Lm - 1) * sm : s + sm;
-    const int sb = co[MU] == 0 ? s + (Lm - 1) * sm : s - sm;
+    const int nf = co[MU] == Lm - 1 ? n - (Lm - 1) * sm : n + sm;
+    const int nb = co[MU] == 0 ? n + (Lm - 1) * sm : n - sm;
     {   // forward: (1 - gamma_mu) U_mu(n) x(n + mu)
-        cx<R> u[9];
-        load_link(a.U, MU, s, a.V, u);
+        cx<R> u[9], q[12], h[6], w[6];
+        load_link(a.U, MU, n, a.V, u);
+        load_col<P>(a.x, nf, c, q);
+        project<MU, -1>(q, h);
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            if (r < nr) {
-                cx<R> q[12], h[6], w[6];
-                const R sc = load_raw<P>(a.x, c0 + r, sf, q);
-                project<MU, -1>(q, h);
-                if constexpr (P == BK_FP16) {
+        for (int hh = 0; hh < 2; ++hh)
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) h[k] = sc * h[k];
-                }
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh)
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        cx<R> t = u[3 * i] * h[3 * hh];
-                        cmac(t, u[3 * i + 1], h[3 * hh + 1]);
-                        cmac(t, u[3 * i + 2], h[3 * hh + 2]);
-                        w[3 * hh + i] = t;
-                    }
-                reconstruct<MU, -1>(w, acc[r]);
+            for (int i = 0; i < 3; ++i) {
+                cx<R> t = u[3 * i] * h[3 * hh];
+                cmac(t, u[3 * i + 1], h[3 * hh + 1]);
+                cmac(t, u[3 * i + 2], h[3 * hh + 2]);
+                w[3 * hh + i] = t;
             }
-        }
+        reconstruct<MU, -1>(w, acc);
     }
     {   // backward: (1 + gamma_mu) U_mu(n - mu)^+ x(n - mu)
-        cx<R> u[9];
-        load_link(a.U, MU, sb, a.V, u);
+        cx<R> u[9], q[12], h[6], w[6];
+        load_link(a.U, MU, nb, a.V, u);
+        load_col<P>(a.x, nb, c, q);
+        project<MU, +1>(q, h);
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            if (r < nr) {
-                cx<R> q[12], h[6], w[6];
-                const R sc = load_raw<P>(a.x, c0 + r, sb, q);
-                project<MU, +1>(q, h);
-                if constexpr (P == BK_FP16) {
+        for (int hh = 0; hh < 2; ++hh)
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) h[k] = sc * h[k];
-                }
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh)
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        cx<R> t = mk(R(0), R(0));
-                        cjmac(t, u[i], h[3 * hh]);
-                        cjmac(t, u[3 + i], h[3 * hh + 1]);
-                        cjmac(t, u[6 + i], h[3 * hh + 2]);
-                        w[3 * hh + i] = t;
-                    }
-                reconstruct<MU, +1>(w, acc[r]);
+            for (int i = 0; i < 3; ++i) {
+                cx<R> t = mk(R(0), R(0));
+                cjmac(t, u[i], h[3 * hh]);
+                cjmac(t, u[3 + i], h[3 * hh + 1]);
+                cjmac(t, u[6 + i], h[3 * hh + 2]);
+                w[3 * hh + i] = t;
             }
-        }
+        reconstruct<MU, +1>(w, acc);
     }
 }
 
@@ -201,51 +785,17 @@ __device__ __forceinline__ void herm6(const R (&m)[36], const cx<R> (&x)[6], cx<
         }
 }
 
-template <typename R>
-__device__ __forceinline__ void load_clov_block(const double2* __restrict__ C, int blk, int s, int V, R (&m)[36]) {
-#pragma unroll
-    for (int q = 0; q < 18; ++q) {
-        double2 v = __ldg(C + (size_t)(18 * blk + q) * V + s);
-        m[2 * q] = (R)v.x;
-        m[2 * q + 1] = (R)v.y;
-    }
-}
-template <typename R>
-__device__ __forceinline__ void load_clov_block(const float4* __restrict__ C, int blk, int s, int V, R (&m)[36]) {
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        float4 v = __ldg(C + (size_t)(9 * blk + q) * V + s);
-        m[4 * q] = v.x;
-        m[4 * q + 1] = v.y;
-        m[4 * q + 2] = v.z;
-        m[4 * q + 3] = v.w;
-    }
-}
-
-// FP64 needs more registers per thread: cap its blocks at 256 threads.
-template <int P, int RPT = 1>
-constexpr int dslash_max_threads() { return (P == BK_FP64 || P == BK_DF64 || RPT > 1) ? 256 : 512; }
-
-// Thread (site s, column group g) computes columns col0 + g*RPT + r, r < RPT:
-// each link and clover block is loaded into registers once and applied to the
-// RPT columns.
-template <int P, int RPT>
-__global__ void __launch_bounds__(dslash_max_threads<P, RPT>()) k_dslash(const __grid_constant__ DArgs<P> a) {
+template <int P>
+__global__ void __launch_bounds__(128) k_dslash_col(const __grid_constant__ DColArgs<P> a) {
     using R = typename Prec<P>::real;
-    const int tid = threadIdx.x;
-    // Column-group blocks of one site block are adjacent in launch order, so
-    // the links and clover they all read are served from L2.
-    const int sblk = a.groups_fast ? blockIdx.y : blockIdx.x;
-    const int gblk = a.groups_fast ? blockIdx.x : blockIdx.y;
-    const int s = sblk * a.SX + (tid % a.SX);
-    const int g = gblk * (blockDim.x / a.SX) + tid / a.SX;
-    const int cl0 = g * RPT;
-    if (s >= a.V || cl0 >= a.ncol) return;
-    const int nr = min(RPT, a.ncol - cl0);
-    const int c0 = a.col0 + cl0;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long long)a.V * a.ncl) return;
+    const int n = (int)(g / a.ncl);
+    const int cl = (int)(g - (long long)n * a.ncl);
+    const int c = a.c0 + cl;
     int co[4];
     {
-        int r = s;
+        int r = n;
         co[0] = r % a.L[0];
         r /= a.L[0];
         co[1] = r % a.L[1];
@@ -253,374 +803,254 @@ __global__ void __launch_bounds__(dslash_max_threads<P, RPT>()) k_dslash(const _
         co[2] = r % a.L[2];
         co[3] = r / a.L[2];
     }
-    cx<R> acc[RPT][12];
+    cx<R> acc[12];
 #pragma unroll
-    for (int r = 0; r < RPT; ++r)
-#pragma unroll
-        for (int k = 0; k < 12; ++k) acc[r][k] = mk(R(0), R(0));
-    hop_dir<P, 0, RPT>(a, co, s, c0, nr, acc);
-    hop_dir<P, 1, RPT>(a, co, s, c0, nr, acc);
-    hop_dir<P, 2, RPT>(a, co, s, c0, nr, acc);
-    hop_dir<P, 3, RPT>(a, co, s, c0, nr, acc);
-
+    for (int k = 0; k < 12; ++k) acc[k] = mk(R(0), R(0));
+    hop_dir_col<P, 0>(a, co, n, c, acc);
+    hop_dir_col<P, 1>(a, co, n, c, acc);
+    hop_dir_col<P, 2>(a, co, n, c, acc);
+    hop_dir_col<P, 3>(a, co, n, c, acc);
+    cx<R> q[12];
+    load_col<P>(a.x, n, c, q);
     // clover: the chiral blocks act on a = u + l (block 0) and b = u - l (block 1)
 #pragma unroll
     for (int blk = 0; blk < 2; ++blk) {
         R m[36];
-        load_clov_block(a.C, blk, s, a.V, m);
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            if (r < nr) {
-                cx<R> q[12], v[6], yv[6];
-                const R sc = load_raw<P>(a.x, c0 + r, s, q);
-#pragma unroll
-                for (int k = 0; k < 6; ++k) v[k] = blk == 0 ? q[k] + q[k + 6] : q[k] - q[k + 6];
-                if constexpr (P == BK_FP16) {
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) v[k] = sc * v[k];
-                }
-                herm6(m, v, yv);
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    acc[r][k] = acc[r][k] + yv[k];
-                    acc[r][k + 6] = blk == 0 ? acc[r][k + 6] + yv[k] : acc[r][k + 6] - yv[k];
-                }
-            }
+        for (int e = 0; e < 18; ++e) {
+            const double2 v = __ldg(a.C + (size_t)(18 * blk + e) * a.V + n);
+            m[2 * e] = (R)v.x;
+            m[2 * e + 1] = (R)v.y;
         }
-    }
+        cx<R> v[6], yv[6];
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-        if (r < nr) {
-            cx<R> q[12], out[12];
-            load_spinor<P>(a.x, c0 + r, s, q);
-            const R kap = (R)a.kappa[cl0 + r];
-#pragma unroll
-            for (int k = 0; k < 12; ++k) out[k] = q[k] - kap * acc[r][k];
-            if (a.residual) {
-                cx<R> bb[12];
-                load_spinor<P>(a.b, c0 + r, s, bb);
-#pragma unroll
-                for (int k = 0; k < 12; ++k) out[k] = bb[k] - out[k];
-            }
-            store_spinor<P>(a.y, c0 + r, s, out);
-        }
-    }
-}
-
-// ----------------------------------------------------------------- pipelined FP32 variant
-//
-// Same arithmetic as k_dslash<FP32, RPT>, with the memory latency moved off
-// the registers: while a thread computes hop h, its copies for hop h + 1 (the
-// neighbour spinors of its RPT columns and the 3x3 link) are in flight as
-// cp.async transfers into the thread's own shared-memory slots (two stages).
-// Hop 8 is the site's own spinor (clover term and axpy).  Each thread reads
-// only the slots it filled, so the only synchronisation is cp.async.wait_group.
-// Shared memory per thread: 2 stages x (RPT x 96 + 72) bytes.
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-template <int RPT>
-constexpr int pipe_smem_per_thread() { return 2 * (RPT * 96 + 72); }
-
-template <int MU, int S>
-__device__ __forceinline__ void hop_apply(const cx<float> (&u)[9], const cx<float> (&q)[12], cx<float> (&acc)[12]) {
-    cx<float> h[6], w[6];
-    project<MU, S>(q, h);
-    if constexpr (S < 0) {  // forward: U h
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh)
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                cx<float> t = u[3 * i] * h[3 * hh];
-                cmac(t, u[3 * i + 1], h[3 * hh + 1]);
-                cmac(t, u[3 * i + 2], h[3 * hh + 2]);
-                w[3 * hh + i] = t;
-            }
-    } else {  // backward: U^+ h
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh)
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                cx<float> t = mk(0.f, 0.f);
-                cjmac(t, u[i], h[3 * hh]);
-                cjmac(t, u[3 + i], h[3 * hh + 1]);
-                cjmac(t, u[6 + i], h[3 * hh + 2]);
-                w[3 * hh + i] = t;
-            }
-    }
-    reconstruct<MU, S>(w, acc);
-}
-
-template <int RPT>
-__global__ void __launch_bounds__(256) k_dslash_pipe(const __grid_constant__ DArgs<BK_FP32> a) {
-    extern __shared__ float4 pipe_smem[];
-    const int tid = threadIdx.x, NT = blockDim.x;
-    float4* sp = pipe_smem;                                   // [stage][r][chunk][NT]
-    float2* sl = reinterpret_cast<float2*>(pipe_smem + 2 * RPT * 6 * NT);  // [stage][9][NT]
-    const int sblk = a.groups_fast ? blockIdx.y : blockIdx.x;
-    const int gblk = a.groups_fast ? blockIdx.x : blockIdx.y;
-    const int s = sblk * a.SX + (tid % a.SX);
-    const int g = gblk * (NT / a.SX) + tid / a.SX;
-    const int cl0 = g * RPT;
-    if (s >= a.V || cl0 >= a.ncol) return;
-    const int nr = min(RPT, a.ncol - cl0);
-    const int c0 = a.col0 + cl0;
-    int nb[9];  // hop h: mu = h / 2, forward (even h) or backward; hop 8 = the site itself
-    {
-        int r = s, co[4];
-        co[0] = r % a.L[0];
-        r /= a.L[0];
-        co[1] = r % a.L[1];
-        r /= a.L[1];
-        co[2] = r % a.L[2];
-        co[3] = r / a.L[2];
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-            const int Lm = a.L[mu], sm = a.st[mu];
-            nb[2 * mu] = co[mu] == Lm - 1 ? s - (Lm - 1) * sm : s + sm;
-            nb[2 * mu + 1] = co[mu] == 0 ? s + (Lm - 1) * sm : s - sm;
-        }
-        nb[8] = s;
-    }
-    const float4* X = (const float4*)a.x.data;
-    const long long cs = a.x.cstride;
-    // copies of hop h into stage st: spinors at nb[h]; the link U_mu(n) for a
-    // forward hop, U_mu(n - mu) for a backward one (none for hop 8)
-    auto issue = [&](int h, int stg) {
-#pragma unroll
-        for (int r = 0; r < RPT; ++r)
-            if (r < nr)
-#pragma unroll
-                for (int k = 0; k < 6; ++k)
-                    cp_async16(sp + ((stg * RPT + r) * 6 + k) * NT + tid,
-                               X + (size_t)(c0 + r) * cs + (size_t)k * a.V + nb[h]);
-        if (h < 8) {
-            const int mu = h >> 1, ls = (h & 1) ? nb[h] : s;
-#pragma unroll
-            for (int k = 0; k < 9; ++k)
-                cp_async8(sl + (stg * 9 + k) * NT + tid, a.U + (size_t)(mu * 9 + k) * a.V + ls);
-        }
-        cp_async_commit();
-    };
-    auto spinor = [&](int stg, int r, cx<float> (&q)[12]) {
+        for (int k = 0; k < 6; ++k) v[k] = blk == 0 ? q[k] + q[k + 6] : q[k] - q[k + 6];
+        herm6(m, v, yv);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            const float4 v = sp[((stg * RPT + r) * 6 + k) * NT + tid];
-            q[2 * k] = mk(v.x, v.y);
-            q[2 * k + 1] = mk(v.z, v.w);
-        }
-    };
-    cx<float> acc[RPT][12];
-#pragma unroll
-    for (int r = 0; r < RPT; ++r)
-#pragma unroll
-        for (int k = 0; k < 12; ++k) acc[r][k] = mk(0.f, 0.f);
-    issue(0, 0);
-#pragma unroll
-    for (int h = 0; h < 8; ++h) {
-        issue(h + 1, (h + 1) & 1);
-        cp_async_wait<1>();  // this thread's copies of hop h have landed
-        const int stg = h & 1;
-        cx<float> u[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const float2 v = sl[(stg * 9 + k) * NT + tid];
-            u[k] = mk(v.x, v.y);
-        }
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            if (r < nr) {
-                cx<float> q[12];
-                spinor(stg, r, q);
-                switch (h) {
-                    case 0: hop_apply<0, -1>(u, q, acc[r]); break;
-                    case 1: hop_apply<0, +1>(u, q, acc[r]); break;
-                    case 2: hop_apply<1, -1>(u, q, acc[r]); break;
-                    case 3: hop_apply<1, +1>(u, q, acc[r]); break;
-                    case 4: hop_apply<2, -1>(u, q, acc[r]); break;
-                    case 5: hop_apply<2, +1>(u, q, acc[r]); break;
-                    case 6: hop_apply<3, -1>(u, q, acc[r]); break;
-                    default: hop_apply<3, +1>(u, q, acc[r]); break;
-                }
-            }
+            acc[k] = acc[k] + yv[k];
+            acc[k + 6] = blk == 0 ? acc[k + 6] + yv[k] : acc[k + 6] - yv[k];
         }
     }
-    cp_async_wait<0>();  // hop 8: the site's own spinors, stage 0
-    // clover: the chiral blocks act on u + l (block 0) and u - l (block 1)
+    cx<R> out[12];
+    const R kap = (R)a.kappa[cl];
 #pragma unroll
-    for (int blk = 0; blk < 2; ++blk) {
-        float m[36];
-        load_clov_block(a.C, blk, s, a.V, m);
+    for (int k = 0; k < 12; ++k) out[k] = q[k] - kap * acc[k];
+    if (a.residual) {
+        cx<R> bb[12];
+        load_col<P>(a.b, n, c, bb);
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            if (r < nr) {
-                cx<float> q[12], v[6], yv[6];
-                spinor(0, r, q);
-#pragma unroll
-                for (int k = 0; k < 6; ++k) v[k] = blk == 0 ? q[k] + q[k + 6] : q[k] - q[k + 6];
-                herm6(m, v, yv);
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    acc[r][k] = acc[r][k] + yv[k];
-                    acc[r][k + 6] = blk == 0 ? acc[r][k + 6] + yv[k] : acc[r][k + 6] - yv[k];
-                }
-            }
-        }
+        for (int k = 0; k < 12; ++k) out[k] = bb[k] - out[k];
     }
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-        if (r < nr) {
-            cx<float> q[12], out[12];
-            spinor(0, r, q);
-            const float kap = (float)a.kappa[cl0 + r];
-#pragma unroll
-            for (int k = 0; k < 12; ++k) out[k] = q[k] - kap * acc[r][k];
-            if (a.residual) {
-                cx<float> bb[12];
-                load_spinor<BK_FP32>(a.b, c0 + r, s, bb);
-#pragma unroll
-                for (int k = 0; k < 12; ++k) out[k] = bb[k] - out[k];
-            }
-            store_spinor<BK_FP32>(a.y, c0 + r, s, out);
-        }
+    store_col<P>(a.y, n, c, out);
+}
+
+void geometry(const int dims[4], int (&L)[4], int (&st)[4]) {
+    int stride = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        L[mu] = dims[mu];
+        st[mu] = stride;
+        stride *= dims[mu];
     }
 }
 
 template <int P>
-bk_status dslash_impl(const DslashOp& op, cudaStream_t st) {
-    if (op.ncol <= 0) return BK_OK;
-    if (op.ncol > BK_MAX_COLS) {
-        // split into launches of at most BK_MAX_COLS columns
-        for (int c0 = 0; c0 < op.ncol; c0 += BK_MAX_COLS) {
-            DslashOp sub = op;
-            sub.col0 = op.col0 + c0;
-            sub.ncol = op.ncol - c0 < BK_MAX_COLS ? op.ncol - c0 : BK_MAX_COLS;
-            sub.kappa = op.kappa + c0;
-            bk_status e = dslash_impl<P>(sub, st);
-            if (e != BK_OK) return e;
+bk_status dslash_pair_impl(const DslashOp& op, cudaStream_t st) {
+    // launch over whole pairs [col0 / 2, (col0 + ncol + 1) / 2)
+    const int p0 = op.col0 / 2, p1 = (op.col0 + op.ncol + 1) / 2;
+    const int maxp = BK_MAX_COLS / 2;
+    for (int q0 = p0; q0 < p1; q0 += maxp) {
+        const int npl = std::min(maxp, p1 - q0);
+        DPairArgs a;
+        a.x = op.x;
+        a.y = op.y;
+        a.b = op.b;
+        a.U = (const float4*)op.U;
+        a.C = (const float4*)op.clov;
+        geometry(op.dims, a.L, a.st);
+        a.V = op.V;
+        a.p0 = q0;
+        a.npl = npl;
+        a.residual = op.residual;
+        for (int j = 0; j < npl; ++j) {
+            // kappa of columns 2q, 2q + 1 (op.kappa[i] belongs to column col0 + i); a
+            // column outside [col0, col0 + ncol) is padding: kappa 0, it is copied through
+            const int ca = 2 * (q0 + j) - op.col0, cb = ca + 1;
+            const double ka = (ca >= 0 && ca < op.ncol) ? op.kappa[ca] : 0.0;
+            const double kb = (cb >= 0 && cb < op.ncol) ? op.kappa[cb] : 0.0;
+            a.nk[j] = make_float2((float)-ka, (float)-kb);
         }
-        return BK_OK;
-    }
-    DArgs<P> a;
-    a.x = op.x;
-    a.y = op.y;
-    a.b = op.b;
-    a.U = (const typename Prec<P>::link*)op.U;
-    a.C = (const typename Prec<P>::clov*)op.clov;
-    int stride = 1;
-    for (int mu = 0; mu < 4; ++mu) {
-        a.L[mu] = op.dims[mu];
-        a.st[mu] = stride;
-        stride *= op.dims[mu];
-    }
-    a.V = op.V;
-    a.col0 = op.col0;
-    a.ncol = op.ncol;
-    a.residual = op.residual;
-    for (int j = 0; j < op.ncol; ++j) a.kappa[j] = op.kappa[j];
-    // Launch shape: RPT columns per thread, BY column groups x SX sites per block.
-    int rpt = op.rpt > 0 ? op.rpt : 1;
-    if (P == BK_FP64 || P == BK_DF64) rpt = 1;
-    if (rpt != 1 && rpt != 2 && rpt != 4) rpt = 1;
-    const int ngroups = (op.ncol + rpt - 1) / rpt;
-    int BY = op.col_block, SX = op.site_block;
-    const int maxt = rpt > 1 ? 256 : dslash_max_threads<P>();
-    if (SX <= 0) SX = 16;
-    if (SX > maxt) SX = maxt;
-    if (BY <= 0) {
-        const int maxby = std::max(1, 256 / SX);
-        const int nyb = (ngroups + maxby - 1) / maxby;
-        BY = (ngroups + nyb - 1) / nyb;
-    }
-    if (SX * BY > maxt) BY = maxt / SX;
-    a.SX = SX;
-    const int nsb = (op.V + SX - 1) / SX, ngb = (ngroups + BY - 1) / BY;
-    a.groups_fast = nsb <= 65535 ? 1 : 0;
-    dim3 grid = a.groups_fast ? dim3(ngb, nsb) : dim3(nsb, ngb);
-    if constexpr (P == BK_FP32) {
-        if (op.pipe && rpt <= 2) {
-            const int nt = SX * BY;
-            const size_t smem = (size_t)nt * (rpt == 2 ? pipe_smem_per_thread<2>() : pipe_smem_per_thread<1>());
-            if (rpt == 2) {
-                BK_CUDA_TRY(cudaFuncSetAttribute(k_dslash_pipe<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem));
-                k_dslash_pipe<2><<<grid, nt, smem, st>>>(a);
-            } else {
-                BK_CUDA_TRY(cudaFuncSetAttribute(k_dslash_pipe<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem));
-                k_dslash_pipe<1><<<grid, nt, smem, st>>>(a);
-            }
-            BK_CUDA_TRY(cudaGetLastError());
-            return BK_OK;
+        // variants 1-3: one thread per (site, pair), register cap 255 (1 block
+        // of 256), 170 (3 blocks of 128), 128 (4 blocks of 128); variants 4-6:
+        // colour-split, three threads per (site, pair), caps 128, 96, 80
+        int threads = op.threads > 0 ? op.threads : 128;
+        if (op.variant >= 2 && op.variant <= 3 && threads > 128) threads = 128;
+        if (op.variant >= 4) {
+            threads = std::min(std::max(threads, 64), 256) / 32 * 32;
+            const long long warps = ((long long)op.V * npl + 9) / 10;
+            const unsigned blocks = (unsigned)((warps * 32 + threads - 1) / threads);
+            if (op.variant == 7)
+                k_dslash_pc<P, 256, 1><<<blocks, threads, 0, st>>>(a);
+            else if (op.variant == 4)
+                k_dslash_pc<P, 256, 2><<<blocks, threads, 0, st>>>(a);
+            else if (op.variant == 5)
+                k_dslash_pc<P, 256, 3><<<blocks, threads, 0, st>>>(a);
+            else
+                k_dslash_pc<P, 256, 4><<<blocks, threads, 0, st>>>(a);
+        } else {
+            const long long items = (long long)op.V * npl;
+            const unsigned blocks = (unsigned)((items + threads - 1) / threads);
+            if (op.variant == 1)
+                k_dslash_pair<P, 256, 1><<<blocks, threads, 0, st>>>(a);
+            else if (op.variant == 3)
+                k_dslash_pair<P, 128, 4><<<blocks, threads, 0, st>>>(a);
+            else
+                k_dslash_pair<P, 128, 3><<<blocks, threads, 0, st>>>(a);
         }
+        BK_CUDA_TRY(cudaGetLastError());
     }
-    if constexpr (P == BK_FP64 || P == BK_DF64) {
-        k_dslash<P, 1><<<grid, SX * BY, 0, st>>>(a);
-    } else {
-        switch (rpt) {
-            case 2: k_dslash<P, 2><<<grid, SX * BY, 0, st>>>(a); break;
-            case 4: k_dslash<P, 4><<<grid, SX * BY, 0, st>>>(a); break;
-            default: k_dslash<P, 1><<<grid, SX * BY, 0, st>>>(a); break;
-        }
-    }
-    BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
 }
 
-// ----------------------------------------------------------------- conversions
-
 template <int P>
-__global__ void k_pack(const double2* __restrict__ canon, Field f, int V) {
-    using R = typename Prec<P>::real;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = blockIdx.y;
-    if (s >= V) return;
-    const double2* p = canon + ((size_t)c * V + s) * 12;
-    cx<R> v[12];
+bk_status dslash_col_impl(const DslashOp& op, cudaStream_t st) {
+    for (int c0 = 0; c0 < op.ncol; c0 += BK_MAX_COLS) {
+        const int n = std::min(BK_MAX_COLS, op.ncol - c0);
+        DColArgs<P> a;
+        a.x = op.x;
+        a.y = op.y;
+        a.b = op.b;
+        a.U = (const typename Prec<P>::link*)op.U;
+        a.C = (const typename Prec<P>::clov*)op.clov;
+        geometry(op.dims, a.L, a.st);
+        a.V = op.V;
+        a.c0 = op.col0 + c0;
+        a.ncl = n;
+        a.residual = op.residual;
+        for (int j = 0; j < n; ++j) a.kappa[j] = op.kappa[c0 + j];
+        const int threads = op.threads > 0 ? std::min(op.threads, 128) : 128;
+        const long long items = (long long)op.V * n;
+        k_dslash_col<P><<<(unsigned)((items + threads - 1) / threads), threads, 0, st>>>(a);
+        BK_CUDA_TRY(cudaGetLastError());
+    }
+    return BK_OK;
+}
+
+// ================================================================= conversions
+
+// canonical column j (of a chunk of ncan columns) -> device column dcol[j]
+// (dcol == nullptr: dbase + j).  Threads: x = canonical column, y = site.
+template <int P>
+__global__ void k_pack(const double2* __restrict__ canon, int ncan, const int* __restrict__ dcol, int dbase, Field f) {
+    const int j = blockIdx.y * blockDim.x + threadIdx.x;
+    const int n = blockIdx.x * blockDim.y + threadIdx.y;
+    if (j >= ncan || n >= f.V) return;
+    const int c = dcol ? dcol[j] : dbase + j;
+    const double2* src = canon + ((size_t)j * f.V + n) * 12;
+    const size_t e0 = (size_t)n * 12 * f.np + (c >> 1);
+    const int half = c & 1;
+    double2 v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = src[k];
+    if constexpr (P == BK_FP64) {
+        double* q = (double*)f.data + 4 * e0 + half;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            q[4 * (size_t)k * f.np] = v[k].x;
+            q[4 * (size_t)k * f.np + 2] = v[k].y;
+        }
+    } else if constexpr (P == BK_FP32) {
+        float* q = (float*)f.data + 4 * e0 + half;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            q[4 * (size_t)k * f.np] = (float)v[k].x;
+            q[4 * (size_t)k * f.np + 2] = (float)v[k].y;
+        }
+    } else {
+        // the column's scale: its largest component, rounded to FP32 first
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf((float)v[k].x), fabsf((float)v[k].y)));
+        const float inv = m > 0.f ? 1.0f / m : 0.f;
+        __half* q = (__half*)f.data + 4 * e0 + half;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            q[4 * (size_t)k * f.np] = __float2half_rn((float)v[k].x * inv);
+            q[4 * (size_t)k * f.np + 2] = __float2half_rn((float)v[k].y * inv);
+        }
+        float* sc = (float*)(f.norm + (size_t)n * f.np + (c >> 1));
+        sc[half] = m;
+    }
+}
+
+// device column dcol[j] (or dbase + j) -> canonical column j of the chunk
+template <int P>
+__global__ void k_unpack(Field f, const int* __restrict__ dcol, int dbase, double2* __restrict__ canon, int ncan) {
+    const int j = blockIdx.y * blockDim.x + threadIdx.x;
+    const int n = blockIdx.x * blockDim.y + threadIdx.y;
+    if (j >= ncan || n >= f.V) return;
+    const int c = dcol ? dcol[j] : dbase + j;
+    double2* dst = canon + ((size_t)j * f.V + n) * 12;
+    const size_t e0 = (size_t)n * 12 * f.np + (c >> 1);
+    const int half = c & 1;
+    if constexpr (P == BK_FP64) {
+        const double* q = (const double*)f.data + 4 * e0 + half;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) dst[k] = make_double2(q[4 * (size_t)k * f.np], q[4 * (size_t)k * f.np + 2]);
+    } else if constexpr (P == BK_FP32) {
+        const float* q = (const float*)f.data + 4 * e0 + half;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) dst[k] = make_double2(q[4 * (size_t)k * f.np], q[4 * (size_t)k * f.np + 2]);
+    } else {
+        const __half* q = (const __half*)f.data + 4 * e0 + half;
+        const float m = ((const float*)(f.norm + (size_t)n * f.np + (c >> 1)))[half];
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+            dst[k] = make_double2((double)(__half2float(q[4 * (size_t)k * f.np]) * m),
+                                  (double)(__half2float(q[4 * (size_t)k * f.np + 2]) * m));
+    }
+}
+
+// zero device column c (both parts, every site and component)
+template <int P>
+__global__ void k_zero_col(Field f, int c) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)f.V * 12) return;
+    const size_t el = (size_t)e * f.np + (c >> 1);
+    const int half = c & 1;
+    if constexpr (P == BK_FP64 || P == BK_DF64) {
+        double* q = (double*)f.data + 4 * el + half;
+        q[0] = 0.0;
+        q[2] = 0.0;
+    } else if constexpr (P == BK_FP32) {
+        float* q = (float*)f.data + 4 * el + half;
+        q[0] = 0.f;
+        q[2] = 0.f;
+    } else {
+        __half* q = (__half*)f.data + 4 * el + half;
+        q[0] = __float2half_rn(0.f);
+        q[2] = __float2half_rn(0.f);
+        if (e % 12 == 0) ((float*)(f.norm + (size_t)(e / 12) * f.np + (c >> 1)))[half] = 0.f;
+    }
+}
+
+// precision conversion over pairs [0, np) of in and out (same pair count)
+template <int PI, int PO>
+__global__ void k_cast(Field in, Field out, int np) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long long)in.V * np) return;
+    const int n = (int)(g / np), p = (int)(g - (long long)n * np);
+    typename Prec<PI>::pair r[12], i[12];
+    load_pair<PI>(in, n, p, r, i);
+    typename Prec<PO>::pair ro[12], io[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-        double2 q = p[k];
-        v[k] = mk((R)q.x, (R)q.y);
+        ro[k].x = r[k].x;
+        ro[k].y = r[k].y;
+        io[k].x = i[k].x;
+        io[k].y = i[k].y;
     }
-    store_spinor<P>(f, c, s, v);
-}
-
-template <int P>
-__global__ void k_unpack(Field f, double2* __restrict__ canon, int V) {
-    using R = typename Prec<P>::real;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = blockIdx.y;
-    if (s >= V) return;
-    cx<R> v[12];
-    load_spinor<P>(f, c, s, v);
-    double2* p = canon + ((size_t)c * V + s) * 12;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) p[k] = make_double2((double)v[k].r, (double)v[k].i);
-}
-
-template <int PI, int PO>
-__global__ void k_cast(Field in, Field out, int V) {
-    using RI = typename Prec<PI>::real;
-    using RO = typename Prec<PO>::real;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = blockIdx.y;
-    if (s >= V) return;
-    cx<RI> v[12];
-    load_spinor<PI>(in, c, s, v);
-    cx<RO> w[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) w[k] = mk((RO)v[k].r, (RO)v[k].i);
-    store_spinor<PO>(out, c, s, w);
+    store_pair<PO>(out, n, p, ro, io);
 }
 
 __global__ void k_gamma5(const double2* __restrict__ X, double2* __restrict__ Y, long long n) {
@@ -642,50 +1072,66 @@ __global__ void k_gamma5(const double2* __restrict__ X, double2* __restrict__ Y,
 }  // namespace
 
 bk_status launch_dslash(int prec, const DslashOp& op, cudaStream_t st) {
+    if (op.ncol <= 0) return BK_OK;
     switch (prec) {
-        case BK_FP64: return dslash_impl<BK_FP64>(op, st);
-        case BK_FP32: return dslash_impl<BK_FP32>(op, st);
-        case BK_FP16: return dslash_impl<BK_FP16>(op, st);
-        case BK_DF64: return dslash_impl<BK_DF64>(op, st);
+        case BK_FP64: return dslash_col_impl<BK_FP64>(op, st);
+        case BK_DF64: return dslash_col_impl<BK_DF64>(op, st);
+        case BK_FP32: return dslash_pair_impl<BK_FP32>(op, st);
+        case BK_FP16: return dslash_pair_impl<BK_FP16>(op, st);
     }
     return BK_ERR_INVALID_ARG;
 }
 
-bk_status launch_pack(int prec, const double* canon, Field f, int L, cudaStream_t st) {
-    if (L <= 0) return BK_OK;
-    dim3 grid((f.V + 127) / 128, L);
+bk_status launch_pack(int prec, const double* canon, int ncan, const int* dcol, int dbase, Field f, cudaStream_t st) {
+    if (ncan <= 0) return BK_OK;
+    // sites on grid.x (up to 2^31 - 1 blocks), columns on grid.y
+    dim3 blk(32, 8), grid((f.V + 7) / 8, (ncan + 31) / 32);
     const double2* c = (const double2*)canon;
     switch (prec) {
-        case BK_FP64: k_pack<BK_FP64><<<grid, 128, 0, st>>>(c, f, f.V); break;
-        case BK_FP32: k_pack<BK_FP32><<<grid, 128, 0, st>>>(c, f, f.V); break;
-        case BK_FP16: k_pack<BK_FP16><<<grid, 128, 0, st>>>(c, f, f.V); break;
+        case BK_FP64: k_pack<BK_FP64><<<grid, blk, 0, st>>>(c, ncan, dcol, dbase, f); break;
+        case BK_FP32: k_pack<BK_FP32><<<grid, blk, 0, st>>>(c, ncan, dcol, dbase, f); break;
+        case BK_FP16: k_pack<BK_FP16><<<grid, blk, 0, st>>>(c, ncan, dcol, dbase, f); break;
         default: return BK_ERR_INVALID_ARG;
     }
     BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
 }
 
-bk_status launch_unpack(int prec, Field f, double* canon, int L, cudaStream_t st) {
-    if (L <= 0) return BK_OK;
-    dim3 grid((f.V + 127) / 128, L);
+bk_status launch_unpack(int prec, Field f, const int* dcol, int dbase, double* canon, int ncan, cudaStream_t st) {
+    if (ncan <= 0) return BK_OK;
+    // sites on grid.x (up to 2^31 - 1 blocks), columns on grid.y
+    dim3 blk(32, 8), grid((f.V + 7) / 8, (ncan + 31) / 32);
     double2* c = (double2*)canon;
     switch (prec) {
-        case BK_FP64: k_unpack<BK_FP64><<<grid, 128, 0, st>>>(f, c, f.V); break;
-        case BK_FP32: k_unpack<BK_FP32><<<grid, 128, 0, st>>>(f, c, f.V); break;
-        case BK_FP16: k_unpack<BK_FP16><<<grid, 128, 0, st>>>(f, c, f.V); break;
+        case BK_FP64: k_unpack<BK_FP64><<<grid, blk, 0, st>>>(f, dcol, dbase, c, ncan); break;
+        case BK_FP32: k_unpack<BK_FP32><<<grid, blk, 0, st>>>(f, dcol, dbase, c, ncan); break;
+        case BK_FP16: k_unpack<BK_FP16><<<grid, blk, 0, st>>>(f, dcol, dbase, c, ncan); break;
         default: return BK_ERR_INVALID_ARG;
     }
     BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
 }
 
-bk_status launch_cast(int pin, Field in, int pout, Field out, int L, cudaStream_t st) {
-    if (L <= 0) return BK_OK;
-    dim3 grid((in.V + 127) / 128, L);
-    const int V = in.V;
+bk_status launch_zero_col(int prec, Field f, int c, cudaStream_t st) {
+    const long long n = (long long)f.V * 12;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    switch (prec) {
+        case BK_FP64: k_zero_col<BK_FP64><<<blocks, 256, 0, st>>>(f, c); break;
+        case BK_FP32: k_zero_col<BK_FP32><<<blocks, 256, 0, st>>>(f, c); break;
+        case BK_FP16: k_zero_col<BK_FP16><<<blocks, 256, 0, st>>>(f, c); break;
+        default: return BK_ERR_INVALID_ARG;
+    }
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}
+
+bk_status launch_cast(int pin, Field in, int pout, Field out, int np, cudaStream_t st) {
+    if (np <= 0) return BK_OK;
+    const long long items = (long long)in.V * np;
+    const unsigned blocks = (unsigned)((items + 127) / 128);
 #define BK_CAST(A, B)                                              \
     if (pin == A && pout == B) {                                   \
-        k_cast<A, B><<<grid, 128, 0, st>>>(in, out, V);            \
+        k_cast<A, B><<<blocks, 128, 0, st>>>(in, out, np);         \
         BK_CUDA_TRY(cudaGetLastError());                           \
         return BK_OK;                                              \
     }

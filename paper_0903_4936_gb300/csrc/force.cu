@@ -318,11 +318,18 @@ __global__ void k_force_out(const double2* __restrict__ Sig, const double2* __re
 }
 
 // sum over all entries of conj(A) * B, FP64, per-block partial sums
-__global__ void k_canon_dot(const double2* __restrict__ A, const double2* __restrict__ B, long long n,
-                            double2* __restrict__ partial) {
+// partial[block] = sum conj(A) (B - Cm) over the block's entries (Cm may be null)
+__global__ void k_canon_dot(const double2* __restrict__ A, const double2* __restrict__ B,
+                            const double2* __restrict__ Cm, long long n, double2* __restrict__ partial) {
     double re = 0.0, im = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double2 a = A[i], b = B[i];
+        const double2 a = A[i];
+        double2 b = B[i];
+        if (Cm) {
+            const double2 c = Cm[i];
+            b.x -= c.x;
+            b.y -= c.y;
+        }
         re += a.x * b.x + a.y * b.y;
         im += a.x * b.y - a.y * b.x;
     }
@@ -342,14 +349,16 @@ __global__ void k_canon_dot(const double2* __restrict__ A, const double2* __rest
         partial[blockIdx.x] = v;
     }
 }
-__global__ void k_canon_dot_finish(const double2* __restrict__ partial, int nb, double2* __restrict__ out) {
+// *out = scale * sum of the partial sums (fixed order)
+__global__ void k_canon_dot_finish(const double2* __restrict__ partial, int nb, double scale,
+                                   double2* __restrict__ out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double2 v = make_double2(0, 0);
     for (int b = 0; b < nb; ++b) {
         v.x += partial[b].x;
         v.y += partial[b].y;
     }
-    *out = v;
+    *out = make_double2(scale * v.x, scale * v.y);
 }
 
 bool g_tables_ready[64] = {false};
@@ -437,9 +446,20 @@ bk_status launch_canon_dot(const double* A, const double* B, long long ncomplex,
                            void* scratch, cudaStream_t st) {
     const int nb = 1024;
     double2* part = (double2*)scratch;
-    k_canon_dot<<<nb, 256, 0, st>>>((const double2*)A, (const double2*)B, ncomplex, part);
+    k_canon_dot<<<nb, 256, 0, st>>>((const double2*)A, (const double2*)B, nullptr, ncomplex, part);
     BK_CUDA_TRY(cudaGetLastError());
-    k_canon_dot_finish<<<1, 32, 0, st>>>(part, nb, (double2*)result_dev);
+    k_canon_dot_finish<<<1, 32, 0, st>>>(part, nb, 1.0, (double2*)result_dev);
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}
+
+bk_status launch_canon_dot_diff(const double* A, const double* B, const double* Cm, long long ncomplex, double scale,
+                                double* result_dev, void* scratch, cudaStream_t st) {
+    const int nb = 1024;
+    double2* part = (double2*)scratch;
+    k_canon_dot<<<nb, 256, 0, st>>>((const double2*)A, (const double2*)B, (const double2*)Cm, ncomplex, part);
+    BK_CUDA_TRY(cudaGetLastError());
+    k_canon_dot_finish<<<1, 32, 0, st>>>(part, nb, scale, (double2*)result_dev);
     BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
 }

@@ -1,11 +1,19 @@
 // Gauge-field upload and clover-term construction (Section 2 of arXiv:0903.4936).
 //
-// Device gauge layout: [mu][9 = 3a + b][site] complex, FP64 (double2) and
-// FP32 (float2) copies, so that a warp reading one matrix element for 32
-// consecutive sites issues one coalesced transaction.
+// Device gauge layouts:
+//  * FP64: [mu][9 = 3a + b][site] complex (double2), so that a warp reading
+//    one matrix element for 32 consecutive sites issues one coalesced
+//    transaction (the FP64 operator takes one column per thread);
+//  * FP32, for the packed-pair operator (one thread per site and column
+//    pair, every lane of a warp on the same site): per (mu, site) 224 bytes,
+//    float2 pairs {u_r, u_r}, {u_i, u_i} of element e at float4 e (e < 9),
+//    then {-u_i, -u_i} of element e at float2 18 + e (one pad pair), so
+//    that every product with a column pair is a packed multiply-add with no
+//    operand shuffling.
 //
-// Clover layout: 72 reals per site, [72/k][site] chunks of k reals (FP64:
-// double2, FP32: float4).  The site term C(n) = c_SW sum_{mu,nu} (i/2)
+// Clover: the FP64 copy is [36][site] double2 (72 reals per site); the FP32
+// copy is per site 816 bytes in the same packed-pair form (see
+// k_clover_build).  The site term C(n) = c_SW sum_{mu,nu} (i/2)
 // sigma_mu_nu F_mu_nu(n) commutes with gamma_5, so in the basis
 // a = u + l, b = u - l (u = spins 0,1, l = spins 2,3) it is block diagonal:
 //     (C q)_u = A' a + B' b,   (C q)_l = A' a - B' b,
@@ -167,17 +175,22 @@ __device__ M3 field_strength(const double2* __restrict__ U, const Geo& g, const 
 }
 
 __global__ void k_gauge_convert(const double2* __restrict__ Uin, double2* __restrict__ U64,
-                                float2* __restrict__ U32, int V) {
+                                float4* __restrict__ U32, int V) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int mu = blockIdx.y;
     if (s >= V) return;
     const double2* p = Uin + ((size_t)mu * V + s) * 9;
+    float4* o = U32 + ((size_t)mu * V + s) * BK_LINK32_F4;
+    float2* on = reinterpret_cast<float2*>(o) + 18;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         double2 q = p[k];
         U64[(size_t)(mu * 9 + k) * V + s] = q;
-        U32[(size_t)(mu * 9 + k) * V + s] = make_float2((float)q.x, (float)q.y);
+        const float ur = (float)q.x, ui = (float)q.y;
+        o[k] = make_float4(ur, ur, ui, ui);
+        on[k] = make_float2(-ui, -ui);
     }
+    on[9] = make_float2(0.f, 0.f);
 }
 
 // Chiral 6x6 block from (G1, G2, G3), scaled: blk = scale * [[-G3, -G1 + iG2], [-G1 - iG2, G3]].
@@ -190,6 +203,10 @@ __device__ __forceinline__ cx<double> chiral_elem(const M3& G1, const M3& G2, co
     return mk(-g1.r, -g1.i) - ti(g2);
 }
 
+// FP32 packed-pair clover, per site (float2 index within the site's 816 bytes):
+//   [0, 60):    block b, entry q < 15: {A_r, A_r} at 2 (15 b + q), {A_i, A_i} at 2 (15 b + q) + 1
+//   [60, 90):   {-A_i, -A_i} of block b, entry q at 60 + 15 b + q
+//   [90, 102):  diagonal {d, d} of block b, row i at 90 + 6 b + i
 __global__ void k_clover_build(const double2* __restrict__ U, double2* __restrict__ C64,
                                float4* __restrict__ C32, Geo g, int V, double csw) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -241,15 +258,25 @@ __global__ void k_clover_build(const double2* __restrict__ U, double2* __restric
     }
 #pragma unroll
     for (int q = 0; q < 36; ++q) C64[(size_t)q * V + s] = make_double2(out[2 * q], out[2 * q + 1]);
+    float2* c2 = reinterpret_cast<float2*>(C32 + (size_t)s * BK_CLOV32_F4);
 #pragma unroll
-    for (int q = 0; q < 18; ++q)
-        C32[(size_t)q * V + s] = make_float4((float)out[4 * q], (float)out[4 * q + 1], (float)out[4 * q + 2],
-                                             (float)out[4 * q + 3]);
+    for (int b = 0; b < 2; ++b) {
+        const double* o = out + 36 * b;
+#pragma unroll
+        for (int q = 0; q < 15; ++q) {
+            const float ar = (float)o[6 + 2 * q], ai = (float)o[7 + 2 * q];
+            c2[2 * (15 * b + q)] = make_float2(ar, ar);
+            c2[2 * (15 * b + q) + 1] = make_float2(ai, ai);
+            c2[60 + 15 * b + q] = make_float2(-ai, -ai);
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) c2[90 + 6 * b + i] = make_float2((float)o[i], (float)o[i]);
+    }
 }
 
 }  // namespace
 
-bk_status launch_gauge_convert(const double* Uin_dev, double2* U64, float2* U32, int V, cudaStream_t st) {
+bk_status launch_gauge_convert(const double* Uin_dev, double2* U64, float4* U32, int V, cudaStream_t st) {
     dim3 grid((V + 127) / 128, 4);
     k_gauge_convert<<<grid, 128, 0, st>>>((const double2*)Uin_dev, U64, U32, V);
     BK_CUDA_TRY(cudaGetLastError());

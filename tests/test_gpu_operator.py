@@ -174,19 +174,22 @@ def test_df64_operator_tracks_fp64_where_fp32_cannot():
     assert np.linalg.norm(r32 - r64) > 10 * np.linalg.norm(r64)
 
 
+@pytest.mark.parametrize("variant", ["1", "2", "3", "4", "5", "6", "7"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
 @pytest.mark.parametrize("dims,L", [((4, 4, 4, 4), 12), ((2, 4, 2, 6), 5), ((3, 5, 4, 6), 1), ((8, 8, 8, 16), 13)])
-def test_dslash_pipelined_kernel(monkeypatch, dims, L):
-    """The cp.async-pipelined FP32 operator (selected for every FP32 launch
-    with BK_DSLASH_PIPE=1) against the oracle, and as the inner operator of a
-    mixed solve; odd L leaves a ragged two-column group."""
+def test_dslash_every_launch_variant(monkeypatch, variant, prec, dims, L):
+    """Each register-cap variant of the packed-pair operator the autotuner may
+    pick (forced with BK_DSLASH_VARIANT) against the oracle; odd L leaves a
+    padding column in the last pair.  On 4^4 the variant is also the inner
+    operator of a mixed-precision solve."""
     import paper_0903_4936_gb300 as bk
-    monkeypatch.setenv("BK_DSLASH_PIPE", "1")
+    monkeypatch.setenv("BK_DSLASH_VARIANT", variant)
     lat, U = _lat(dims, 0.5, 300 + L)
     X = synth.gaussian_sources(dims, L, 8)
     kappa = [0.115 + 0.001 * j for j in range(L)]
-    Y = lat.dslash(torch.from_numpy(X).cuda(), kappa, "fp32").cpu().numpy()
-    assert _rel(Y, dirac.apply_dirac(U, X, np.array(kappa), 1.0)) < TOL["fp32"]
-    if dims == (4, 4, 4, 4):
+    Y = lat.dslash(torch.from_numpy(X).cuda(), kappa, prec).cpu().numpy()
+    assert _rel(Y, dirac.apply_dirac(U, X, np.array(kappa), 1.0)) < TOL[prec]
+    if dims == (4, 4, 4, 4) and prec == "fp32":
         B = torch.from_numpy(synth.z4_noise(dims, L, 9)).cuda()
         Xs, info = lat.block_solve(B, 0.12, method="bicgstab", prec="fp32", tol=1e-10, maxiter=1000)
         assert info["converged"] == 1 and info["true_res_max"] <= 1e-10
@@ -213,3 +216,40 @@ def test_dslash_multi_and_set_clover():
     G1 = lat.unpack(lat.dslash_multi(F, 0.121, L=5, prec="fp32", layout="device"), 5, "fp32").cpu().numpy()
     G2 = lat.unpack(lat.dslash_dev(F, 5, 0.121, "fp32"), 5, "fp32").cpu().numpy()
     np.testing.assert_array_equal(G1, G2)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("dims,L,kappas", [
+    ((16, 16, 16, 32), 180, (0.120, 0.125, 0.130)),
+    ((24, 24, 24, 48), 196, (0.120, 0.122, 0.124, 0.126, 0.128, 0.130)),
+])
+def test_dslash_benchmark_sizes_sampled_sites(prec, dims, L, kappas):
+    """The benchmark's lattices and column counts (16^3 x 32 with 180 columns,
+    24^3 x 48 with 196 columns), one launch over all columns at the launch
+    shape the autotuner picks for that count, per-column kappa as in the
+    batched solves.  Column j is c_j Z_(j mod 4): four Z4 noise fields times
+    a distinct complex scale per column (D_W is linear), so every column
+    differs and a column mix-up changes the result.  Compared on sampled sites
+    (including lattice corners and the last site) with the oracle's site-wise
+    operator."""
+    lat, U = _lat(dims, 0.5, 1003 if dims[0] == 16 else 1004)
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    Z = synth.z4_noise(dims, 4, 2048)
+    j = np.arange(L)
+    cj = (1.0 + j / L) * np.exp(2j * np.pi * j / L)
+    kap = np.array([kappas[(jj * len(kappas)) // L] for jj in j])
+    Zt = torch.from_numpy(Z).cuda()
+    Xt = Zt[torch.from_numpy(j % 4).cuda()] * torch.from_numpy(cj).cuda().reshape((L,) + (1,) * 6)
+    del Zt
+    Y = lat.dslash(Xt.contiguous(), list(kap), prec)
+    del Xt
+    sites = [0, 1, dims[0] - 1, dims[0], V // 3 + 5, V // 2 + 17, V - dims[0] * dims[1] * dims[2], V - 1]
+    got = Y.reshape(L, V, 4, 3)[:, sites].cpu().numpy()
+    del Y
+    err = 0.0
+    for p in range(4):
+        cols = j[j % 4 == p]
+        Xp = np.broadcast_to(Z[p:p + 1], (len(cols),) + Z.shape[1:])
+        ref = dirac.apply_dirac_at(U, Xp, kap[cols], 1.0, sites, dims) * cj[cols][:, None, None, None]
+        err = max(err, _rel(got[cols], ref))
+    assert err < TOL[prec], err

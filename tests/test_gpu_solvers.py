@@ -125,7 +125,8 @@ def c2():
     return dims, lat, U, B, dense.from_columns(Xo, dims), A
 
 
-@pytest.mark.parametrize("method,prec", [("bicggr", "fp64"), ("bicgstab", "fp64"), ("bicgstab", "fp32")])
+@pytest.mark.parametrize("method,prec", [("bicggr", "fp64"), ("bicgstab", "fp64"), ("bicgstab", "fp32"),
+                                         ("bicggr", "fp32")])
 def test_c2_solution_matches_oracle(c2, method, prec):
     dims, lat, U, B, Xo, A = c2
     X, info = lat.block_solve(torch.from_numpy(B).cuda(), 0.125, method=method, prec=prec, tol=1e-10,
@@ -254,35 +255,56 @@ def test_not_converged_returns_iterate(c1):
 
 
 def test_bicggr_residual_gap_vs_bicgstab(c2):
-    """Section 4.3: BiCGGR's true residual stays at the tolerance; BiCGSTAB's
-    may drift above it.  Both in FP64, recursive stopping rule."""
+    """Section 4.3, Tables 2 vs 3: with the recursive stopping rule at the
+    paper's tolerance 1e-14, block BiCGGR's true residual stays at the
+    tolerance (Table 3: 0.9-1.5 x 1e-14) while block BiCGSTAB's drifts above
+    it (Table 2: up to 1e-11 at L = 4).  Both in FP64 on the same 12 point
+    sources; the true residual is the oracle's, from the returned X."""
     dims, lat, U, B, Xo, A = c2
-    _, ig = lat.block_solve(torch.from_numpy(B).cuda(), 0.125, method="bicggr", prec="fp64", tol=1e-12,
-                            maxiter=1000)
-    assert ig["true_res_max"] < 5e-12
+    Bc = dense.to_columns(B)
+    tol = 1e-14
+    res = {}
+    for method in ("bicggr", "bicgstab"):
+        X, info = lat.block_solve(torch.from_numpy(B).cuda(), 0.125, method=method, prec="fp64", tol=tol,
+                                  maxiter=1000, raise_on_fail=False)
+        assert info["rec_res_max"] <= tol
+        tr, _ = solvers.true_residual(A, Bc, dense.to_columns(X.cpu().numpy()))
+        assert abs(tr - info["true_res_max"]) <= 0.1 * tr
+        res[method] = tr
+    assert res["bicggr"] < 5 * tol, res
+    assert res["bicgstab"] > 2 * res["bicggr"], res
 
 
-def test_batched_uneven_systems_c4_structure():
-    """The batched configuration's structure on an 8^4 lattice: six systems,
+@pytest.mark.parametrize("split", [None, 6])
+def test_batched_uneven_systems_c4_structure(split):
+    """The batched configuration's structure on a 4^4 lattice: six systems,
     kappa 0.120 ... 0.130, L = 4, 12, 12, 24, 48, 96 (196 columns of Z4 noise)
-    in one batched mixed-precision solve (one operator launch for all columns
-    per step, L = 96 exercises the global-memory L x L solve).  Each system
-    must reach its FP64 true residual and agree with its own FP64 solve."""
-    import paper_0903_4936_gb300 as bk
-    dims = (8, 8, 8, 8)
+    in one batched mixed-precision solve, as given (L = 96 exercises the
+    global-memory L x L solve) and split into systems of at most 6 columns
+    as the benchmark solves them.  Every system is compared with the dense LU
+    solution of its own kappa (oracle) and must reach its FP64 true residual."""
+    dims = (4, 4, 4, 4)
     lat, U = _setup(dims, 0.5, 1004)
     kappas = [0.120, 0.122, 0.124, 0.126, 0.128, 0.130]
     Ls = [4, 12, 12, 24, 48, 96]
     B = synth.z4_noise(dims, sum(Ls), 4004)
-    Bt = torch.from_numpy(B).cuda()
-    X, infos = lat.block_solve_batched(Bt, kappas, Ls, method="bicgstab", prec="fp32", tol=1e-10, maxiter=3000)
+    ks, ls, owner = [], [], []
+    for s, (k, L) in enumerate(zip(kappas, Ls)):
+        step = L if split is None else split
+        for j0 in range(0, L, step):
+            ks.append(k)
+            ls.append(min(step, L - j0))
+            owner.append(s)
+    X, infos = lat.block_solve_batched(torch.from_numpy(B).cuda(), ks, ls, method="bicgstab", prec="fp32",
+                                       tol=1e-10, maxiter=3000)
     X = X.cpu().numpy()
+    for si, info in enumerate(infos):
+        assert info["converged"] == 1 and info["true_res_max"] <= 1e-10, (si, info)
     c0 = 0
     for s, (k, L) in enumerate(zip(kappas, Ls)):
-        assert infos[s]["converged"] == 1 and infos[s]["true_res_max"] <= 1e-10, (s, infos[s])
-        Xs, info = lat.block_solve(Bt[c0:c0 + L].contiguous(), k, method="bicggr", prec="fp64", tol=1e-12,
-                                   maxiter=3000)
-        assert _dev(X[c0:c0 + L], Xs.cpu().numpy()) <= 1e-8
+        D = dense.dense_matrix(U, k, 1.0)
+        ref = dense.from_columns(np.linalg.solve(D, dense.to_columns(B[c0:c0 + L])), dims)
+        assert _dev(X[c0:c0 + L], ref) <= 1e-8, s
         c0 += L
 
 

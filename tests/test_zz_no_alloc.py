@@ -48,12 +48,14 @@ def test_noalloc_gram_matches_allocating_gram_twice(prec):
         assert err < TOL[prec], (call, err)
 
 
-def test_noalloc_gram_rejects_too_large_L():
+@pytest.mark.parametrize("L", [361, 400, 185000, 262141, 262144, 2**31 - 1])
+def test_noalloc_gram_rejects_too_large_L(L):
+    # Sizes whose tile count would overflow or wrap in int arithmetic must be
+    # rejected before any tiling or launch, as the plain too-large case is.
     from paper_0903_4936_gb300 import _lib
     import paper_0903_4936_gb300 as bk
     dims = (4, 4, 4, 4)
     lat = bk.Lattice(dims)
-    L = 400
     A = torch.zeros(16, dtype=torch.uint8, device="cuda")
     G = torch.empty((1,), dtype=torch.complex128, device="cuda")
     rc = _lib.lib().bk_block_gram_noalloc(lat.V, C.c_void_p(A.data_ptr()), C.c_void_p(A.data_ptr()), L,
