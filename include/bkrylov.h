@@ -282,6 +282,20 @@ typedef struct bk_solve_params {
                               replacements R = B - A X: 0 = FP64 (default),
                               1 = double-float (BK_DF64).  The true residual
                               that decides convergence is FP64 in both cases */
+    int deflate;           /* breakdown robustness (not in the paper; needs
+                              x0_given = 0): 1 = orthonormalise each system's
+                              right-hand sides first, B = Q R by shifted
+                              Cholesky QR (three passes, FP64, each factoring
+                              the Gram matrix + 1e-13 of its trace), solve
+                              D_W Y = Q and return X = Y R, so that (nearly)
+                              dependent columns of B cannot make R~_0^H V
+                              singular; the stopping rule is tightened by the
+                              largest ||R e_j||_1 / ||R e_j||_2 so that it
+                              still holds column by column for X; and an L x L
+                              breakdown during the iterations restarts the
+                              recurrences from an FP64 true residual (at most
+                              20 times per system) instead of stopping.
+                              0 = the plain method                            */
 } bk_solve_params;
 
 typedef struct bk_solve_info {
@@ -310,6 +324,9 @@ typedef struct bk_solve_info {
     long long n_launches;  /* kernels launched by the call                    */
     long long cols_dslash_inner; /* columns summed over the inner-precision
                                     dslash launches (converged systems drop out) */
+    int deflated;          /* deflate = 1: directions of the right-hand sides
+                              whose weight |R_jj| is below 1e-8 max_k |R_kk|
+                              (numerically dependent columns)                 */
 } bk_solve_info;
 
 /* Solve D_W X = B (Eq. (linear_mrhs)) for L right-hand sides with one kappa

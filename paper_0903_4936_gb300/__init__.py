@@ -222,7 +222,7 @@ class Lattice:
 
     # ------------------------------------------------------------ solves
     def _params(self, method, prec, tol, maxiter, delta, x0_given, on_host, rtilde, seed, history, timing,
-                restart=False, orth=None, update="fp64"):
+                restart=False, orth=None, update="fp64", deflate=False):
         """rtilde: None -> seeded Gaussian R~_0 (library default), "r0" -> R~_0 = R_0,
         tensor -> the caller's block (canonical layout, where B lives).  update:
         arithmetic of the mixed-precision residual replacements, "df64" or "fp64"."""
@@ -238,7 +238,7 @@ class Lattice:
         return SolveParams(METHOD[method] if isinstance(method, str) else int(method), _prec(prec), float(tol),
                            int(maxiter), float(delta), int(x0_given), int(on_host), mode, int(seed), ptr,
                            int(bool(restart)), 0 if orth is None else (1 if orth else 2), int(history),
-                           int(timing), 1 if update == "df64" else 0)
+                           int(timing), 1 if update == "df64" else 0, int(bool(deflate)))
 
     @staticmethod
     def _info_dict(info: SolveInfo, hist_buf, res_buf):
@@ -250,7 +250,7 @@ class Lattice:
     def block_solve(self, B: torch.Tensor, kappa: float, method="bicggr", prec="fp64", tol=1e-10, maxiter=2000,
                     X0: torch.Tensor | None = None, delta=0.0, rtilde=None, seed=0, history=False,
                     timing=False, out: torch.Tensor | None = None, raise_on_fail=True, restart=False,
-                    orth=None, update="fp64"):
+                    orth=None, update="fp64", deflate=False):
         """Solve D_W X = B (Eq. (linear_mrhs)).  B on the GPU, or on the host
         (then pinned memory is best): X is returned where B lives."""
         self._check_block(B, "B")
@@ -264,7 +264,7 @@ class Lattice:
             if rtilde.shape != B.shape or rtilde.is_cuda != B.is_cuda:
                 raise ValueError("rtilde must have B's shape and location")
         prm = self._params(method, prec, tol, maxiter, delta, X0 is not None, on_host, rtilde, seed, history,
-                           timing, restart, orth, update)
+                           timing, restart, orth, update, deflate)
         info = SolveInfo()
         res_buf = (C.c_double * L)()
         info.true_res = C.cast(res_buf, C.POINTER(C.c_double))
@@ -282,7 +282,7 @@ class Lattice:
     def block_solve_batched(self, B: torch.Tensor, kappas: Sequence[float], Ls: Sequence[int], method="bicggr",
                             prec="fp64", tol=1e-10, maxiter=2000, delta=0.0, rtilde=None, seed=0, history=False,
                             timing=False, raise_on_fail=True, restart=False, orth=None, update="fp64",
-                            out: torch.Tensor | None = None):
+                            out: torch.Tensor | None = None, deflate=False):
         """Several systems (kappa_s, L_s columns each, concatenated in B).  X is
         returned where B lives, in `out` if given (same shape and location as
         B; pinned host memory for host blocks)."""
@@ -299,7 +299,7 @@ class Lattice:
         else:
             X = torch.empty_like(B, pin_memory=on_host) if on_host else torch.empty_like(B)
         prm = self._params(method, prec, tol, maxiter, delta, False, on_host, rtilde, seed, history, timing,
-                           restart, orth, update)
+                           restart, orth, update, deflate)
         infos = (SolveInfo * nsys)()
         res_bufs, hist_bufs = [], []
         for s in range(nsys):

@@ -36,7 +36,7 @@ class SolveParams(C.Structure):
         ("reliable_delta", C.c_double), ("x0_given", C.c_int), ("buffers_on_host", C.c_int),
         ("rtilde_mode", C.c_int), ("seed", C.c_uint64), ("rtilde", C.c_void_p), ("restart_on_update", C.c_int),
         ("orth_mode", C.c_int), ("record_history", C.c_int),
-        ("timing", C.c_int), ("update_prec", C.c_int),
+        ("timing", C.c_int), ("update_prec", C.c_int), ("deflate", C.c_int),
     ]
 
 
@@ -49,7 +49,7 @@ class SolveInfo(C.Structure):
         ("history_len", C.c_int), ("time_total_ms", C.c_double), ("time_dslash_ms", C.c_double),
         ("n_dslash", C.c_int), ("n_dslash_inner", C.c_int), ("time_dslash_inner_ms", C.c_double),
         ("n_launches", C.c_longlong),
-        ("cols_dslash_inner", C.c_longlong),
+        ("cols_dslash_inner", C.c_longlong), ("deflated", C.c_int),
     ]
 
 

@@ -111,13 +111,14 @@ struct bk_ctx {
     std::vector<cudaEvent_t> events;
     // operator launch shapes chosen by the autotuner, keyed by (prec, residual, ncol)
     struct Shape {
-        int threads, variant;
+        int threads, variant, group, prefetch;
     };
     std::map<long long, Shape> shapes;
     bool autotune = true;
     bool verbose = false;  // BK_VERBOSE=1: one line per solve and per tuning decision on stderr
-    int force_variant = 0;  // BK_DSLASH_VARIANT=1..7: FP32/FP16 operator variant (thread mapping and
-                            // register cap), 128 threads, no tuning (tests every variant the tuner may pick)
+    int force_variant = 0;  // BK_DSLASH_VARIANT=1|2|3: FP32/FP16 operator register-cap variant,
+                            // 128 threads, pair groups of 8, no tuning (tests the variants the tuner may pick)
+    int force_prefetch = 0; // BK_DSLASH_PREFETCH=0..3: its prefetch mode (with BK_DSLASH_VARIANT)
 };
 
 static bool wide(int prec) { return prec == BK_FP64 || prec == BK_DF64; }
@@ -163,7 +164,9 @@ extern "C" bk_status bk_create(const int dims[4], int device, bk_ctx** out) {
         const char* v = getenv("BK_VERBOSE");
         c->verbose = v && v[0] == '1';
         const char* fv = getenv("BK_DSLASH_VARIANT");
-        if (fv && fv[0] >= '1' && fv[0] <= '7') c->force_variant = fv[0] - '0';
+        if (fv && fv[0] >= '1' && fv[0] <= '3') c->force_variant = fv[0] - '0';
+        const char* fp = getenv("BK_DSLASH_PREFETCH");
+        if (fp && fp[0] >= '0' && fp[0] <= '3') c->force_prefetch = fp[0] - '0';
     }
     c->device = device;
     bk_status s;
@@ -255,17 +258,19 @@ extern "C" bk_status bk_unpack(bk_ctx* c, const void* Xd, double* X, int L, bk_p
 static bk_status tune_shape(bk_ctx* c, int prec, DslashOp op, cudaStream_t st, bk_ctx::Shape& best) {
     std::vector<bk_ctx::Shape> cands;
     if (wide(prec)) {
-        for (int t : {64, 128}) cands.push_back({t, 0});
+        for (int t : {64, 128}) cands.push_back({t, 0, 0, 0});
     } else {
-        // one thread per (site, pair), register caps 255 (variant 1), 170 (2),
-        // 128 (3); colour-split, three threads per (site, pair): caps 128 (4),
-        // 85 (5), 64 (6), 255 (7)
-        for (int t : {128, 256}) cands.push_back({t, 1});
-        for (int v : {2, 3})
-            for (int t : {64, 128}) cands.push_back({t, v});
-        for (int v : {4, 7})
-            for (int t : {128, 256}) cands.push_back({t, v});
-        cands.push_back({256, 5});
+        // register caps 255 (variant 1), 170 (2), 128 (3); pair groups of 16
+        // pairs or all pairs at once; no prefetch, prefetch into L2 or L1, or
+        // the looped form with L1 prefetch one hop ahead
+        const int npl = (op.ncol + 1) / 2;
+        for (int pf : {0, 1, 2, 3})
+            for (int grp : {16, 0}) {
+                if (grp > 0 && grp >= npl) continue;
+                cands.push_back({128, 1, grp, pf});
+                cands.push_back({128, 2, grp, pf});
+                cands.push_back({128, 3, grp, pf});
+            }
     }
     // events released on every return path
     struct EventPair {
@@ -283,6 +288,8 @@ static bk_status tune_shape(bk_ctx* c, int prec, DslashOp op, cudaStream_t st, b
     for (const auto& cd : cands) {
         op.threads = cd.threads;
         op.variant = cd.variant;
+        op.group = cd.group;
+        op.prefetch = cd.prefetch;
         BK_TRY(launch_dslash(prec, op, st));
         BK_CUDA_TRY(cudaEventRecord(e0, st));
         BK_TRY(launch_dslash(prec, op, st));
@@ -315,9 +322,13 @@ static bk_status dslash_fields(bk_ctx* c, int prec, const double* kappa, Field x
     op.kappa = kappa;
     op.threads = 0;
     op.variant = 0;
+    op.group = 0;
+    op.prefetch = 0;
     if (c->force_variant && !wide(prec)) {
         op.threads = 128;
         op.variant = c->force_variant;
+        op.group = 8;
+        op.prefetch = c->force_prefetch;
     } else if (c->autotune && ncol <= BK_MAX_COLS) {
         // FP64-class launches are bound by the FP64 pipe whatever their width:
         // one shape per mode, tuned at first use
@@ -329,11 +340,15 @@ static bk_status dslash_fields(bk_ctx* c, int prec, const double* kappa, Field x
             BK_TRY(tune_shape(c, prec, op, st, sh));
             it = c->shapes.emplace(key, sh).first;
             if (c->verbose)
-                fprintf(stderr, "[bkrylov] tuned operator prec=%d residual=%d ncol=%d: threads=%d variant=%d\n",
-                        prec, residual, ncol, sh.threads, sh.variant);
+                fprintf(stderr,
+                        "[bkrylov] tuned operator prec=%d residual=%d ncol=%d: threads=%d variant=%d group=%d "
+                        "prefetch=%d\n",
+                        prec, residual, ncol, sh.threads, sh.variant, sh.group, sh.prefetch);
         }
         op.threads = it->second.threads;
         op.variant = it->second.variant;
+        op.group = it->second.group;
+        op.prefetch = it->second.prefetch;
     }
     return launch_dslash(prec, op, st);
 }
@@ -532,6 +547,13 @@ struct Solve {
     std::vector<std::vector<double>> hist;
     std::vector<double> true_res, rec_res;
     std::vector<char> res_known;     // per system: true_res already holds the final FP64 residual
+    // deflate: the systems solve D Y = Q for B = Q R (orthonormal Q); the
+    // stopping rule of system s is tol_s[s] <= tol; bnorm_orig = ||b_j||
+    bool deflate = false;
+    std::vector<double> tol_s, bnorm_orig, rfac_h;
+    std::vector<int> ndefl;
+    double* rfac = nullptr;           // R per system, complex FP64 (packed like the L x L matrices)
+    const double* Bcaller = nullptr;  // the caller's B (re-read for the final true residual)
     Field B64, X64, R64, Xlo, R, Rt, Pb, Vb, Wb, Ub, Yb, Tb, Zb, Ptmp;
     bool orth = false;
     int upd_prec = BK_FP64;  // arithmetic of the residual replacements
@@ -772,7 +794,7 @@ struct Solve {
         BK_CUDA_TRY(cudaMemcpyAsync(dcol, dcol_h.data(), (size_t)Lu * sizeof(int), cudaMemcpyHostToDevice, st));
         // small arrays (complex FP64 unless noted)
         const int nc = ncoef();
-        const size_t nsmall = (size_t)7 * nc + 3 * Lt + Lt + 3 * nsys;
+        const size_t nsmall = (size_t)8 * nc + 3 * Lt + Lt + 3 * nsys;
         BK_TRY(c->small.ensure(nsmall * sizeof(double2) + (3 * nsys + Lt) * sizeof(int) + 256));
         double2* q = c->small.as<double2>();
         G_V = (double*)q;
@@ -788,6 +810,8 @@ struct Solve {
         G_Z = (double*)q;
         q += nc;
         LU = (double*)q;
+        q += nc;
+        rfac = (double*)q;
         q += nc;
         dots = (double*)q;
         q += 3 * Lt;
@@ -825,6 +849,7 @@ struct Solve {
         }
 
         // B, X0 into the FP64 device layout (padding columns zero)
+        Bcaller = Bc;
         BK_TRY(put_caller_block(Bc, B64));
         {
             Field a[1] = {B64}, b[1] = {B64};
@@ -844,6 +869,12 @@ struct Solve {
                     }
                     bnorm[j] = std::sqrt(n2);
                 }
+            bnorm_orig = bnorm;
+        }
+        if (deflate) {
+            // B = Q R: the systems now solve D Y = Q, whose columns have unit norm
+            BK_TRY(orthonormalise());
+            for (int j = 0; j < Lt; ++j) bnorm[j] = 1.0;
         }
         if (prm->rtilde_mode == 2) {
             BK_TRY(put_caller_block(prm->rtilde, R64));  // R64 is rebuilt below
@@ -888,9 +919,66 @@ struct Solve {
             const double m = sys_max(s);
             hist[s].push_back(m);
             rmax_since[s] = m;
-            if (m <= prm->tol) done[s] = 1;
+            if (m <= tol_s[s]) done[s] = 1;
         }
         update_active();
+        return BK_OK;
+    }
+
+    // Shifted Cholesky QR in three passes (FP64; after Fukaya, Kawamura,
+    // Nakatsukasa, Yamamoto, Yanagisawa 2020): per system B = Q R with Q
+    // orthonormal to rounding even when columns of B are (nearly) linearly
+    // dependent.  Each pass factors G + 1e-13 trace(G) I, G the Gram matrix
+    // of the current block: the shift keeps the Cholesky defined (an exactly
+    // dependent column becomes an arbitrary direction orthogonal to the
+    // others, with a negligible entry in R) and perturbs Q^H Q by ~1e-13;
+    // passes 2 and 3 restore orthogonality.  R = Q^H B.  B64 is replaced by
+    // Q; X64 and R64 serve as temporaries (set up afterwards).
+    bk_status orthonormalise() {
+        Field cur = B64, tmp[2] = {X64, R64};
+        for (int pass = 0; pass < 3; ++pass) {
+            BK_TRY(launch_gram(BK_FP64, cur, cur, part, G_Z, partial, V, st));
+            BK_TRY(launch_chol_inv(G_Z, gam, part, st, 1e-13));
+            GenOp g = genop0();
+            g.nmi = 1;
+            g.Mi[0] = cur;
+            g.ma_mult[0] = 1.0;
+            g.M = gam;
+            g.hasY = 1;
+            g.Y = tmp[pass & 1];
+            g.ym = 1.0;
+            BK_TRY(launch_genop(BK_FP64, g, V, st));
+            cur = tmp[pass & 1];
+            launches += 4;
+        }
+        BK_TRY(launch_gram(BK_FP64, cur, B64, part, rfac, partial, V, st));  // R = Q^H B
+        BK_CUDA_TRY(cudaMemcpyAsync(B64.data, cur.data, field_bytes(Lt, V, BK_FP64), cudaMemcpyDeviceToDevice, st));
+        launches += 2;
+        rfac_h.resize(2 * (size_t)ncoef());
+        BK_CUDA_TRY(cudaMemcpyAsync(rfac_h.data(), rfac, rfac_h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        BK_CUDA_TRY(cudaStreamSynchronize(st));
+        // column j of X gets sum_i Y_i R_ij: ||r_j|| <= max_i ||r'_i|| sum_i |R_ij|
+        // and ||b_j|| = ||R e_j||_2, so the Q system stops at tol / max_j ratio
+        for (int s = 0; s < nsys; ++s) {
+            const int L = part.L[s];
+            const double* R = rfac_h.data() + 2 * (size_t)part.coef_off[s];
+            double f = 1.0, dmax = 0.0;
+            for (int j = 0; j < L; ++j) {
+                double n1 = 0.0, n2 = 0.0;
+                for (int i = 0; i < L; ++i) {
+                    const double a = std::hypot(R[2 * (i * L + j)], R[2 * (i * L + j) + 1]);
+                    n1 += a;
+                    n2 += a * a;
+                }
+                if (n2 > 0.0) f = std::max(f, n1 / std::sqrt(n2));
+                dmax = std::max(dmax, std::hypot(R[2 * (j * L + j)], R[2 * (j * L + j) + 1]));
+            }
+            tol_s[s] = prm->tol / f;
+            int nd = 0;
+            for (int j = 0; j < L; ++j)
+                if (std::hypot(R[2 * (j * L + j)], R[2 * (j * L + j) + 1]) < 1e-8 * dmax) ++nd;
+            ndefl[s] = nd;
+        }
         return BK_OK;
     }
 
@@ -1023,7 +1111,7 @@ struct Solve {
         } else {
             BK_TRY(residual_norms());
         }
-        std::vector<int> upd, bad;
+        std::vector<int> upd, bad, restart64;
         const double delta = prm->reliable_delta > 0 ? prm->reliable_delta : 0.1;
         const int kmax = 50;  // forced FP64 update after this many iterations without one
         for (int s = 0; s < nsys; ++s) {
@@ -1034,8 +1122,12 @@ struct Solve {
             const double m = sys_max(s);
             hist[s].push_back(m);
             if (!mixed) {
-                if (brk || !std::isfinite(m)) done[s] = 2;
-                else if (m <= prm->tol) done[s] = 1;
+                // deflate: an L x L breakdown (its updates were skipped) restarts
+                // the recurrences from an FP64 true residual
+                const bool lu_brk = (info_a_h[s] || info_g_h[s]) && !zbad_h[s];
+                if (deflate && lu_brk && nrestart[s] < 20) restart64.push_back(s);
+                else if (brk || !std::isfinite(m)) done[s] = 2;
+                else if (m <= tol_s[s]) done[s] = 1;
                 continue;
             }
             since[s]++;
@@ -1044,12 +1136,22 @@ struct Solve {
                 continue;
             }
             rmax_since[s] = std::max(rmax_since[s], m);
-            if (m <= prm->tol || m < delta * rmax_since[s] || since[s] >= kmax) upd.push_back(s);
+            if (m <= tol_s[s] || m < delta * rmax_since[s] || since[s] >= kmax) upd.push_back(s);
         }
         for (int s : bad) {
             BK_TRY(discard_cycle(s));
             hist[s].back() = m_upd[s];
             if (nrestart[s] > 100) done[s] = 2;
+        }
+        if (!restart64.empty()) {
+            BK_TRY(reliable_update(restart64, BK_FP64, false));
+            for (int s : restart64) {
+                const double m = sys_max(s);
+                hist[s].back() = m;
+                nrestart[s]++;
+                restart_now[s] = 1;
+                if (m <= tol_s[s]) converged_fp64(s);
+            }
         }
         if (!upd.empty()) {
             BK_TRY(reliable_update(upd, upd_prec, true));
@@ -1060,8 +1162,8 @@ struct Solve {
                 rmax_since[s] = m;
                 m_upd[s] = m;
                 since[s] = 0;
-                if (m <= prm->tol && upd_prec != BK_FP64) conf.push_back(s);
-                else if (m <= prm->tol) converged_fp64(s);
+                if (m <= tol_s[s] && upd_prec != BK_FP64) conf.push_back(s);
+                else if (m <= tol_s[s]) converged_fp64(s);
                 else if (prm->restart_on_update) restart_now[s] = 1;
             }
             if (!conf.empty()) {
@@ -1072,7 +1174,7 @@ struct Solve {
                     hist[s].back() = m;
                     rmax_since[s] = m;
                     m_upd[s] = m;
-                    if (m <= prm->tol) converged_fp64(s);
+                    if (m <= tol_s[s]) converged_fp64(s);
                     else if (prm->restart_on_update) restart_now[s] = 1;
                 }
             }
@@ -1297,18 +1399,35 @@ struct Solve {
         // that converged on an FP64 residual replacement (mixed precision)
         sysmask need = 0;
         for (int s = 0; s < nsys; ++s)
-            if (!res_known[s]) {
+            if (!res_known[s] || deflate) {
                 need |= 1ull << s;
                 mv64[s]++;
             }
         part.active = all_systems(nsys);
-        for (const auto& cr : col_runs(need)) {
-            if (mixed) {
+        if (mixed)
+            for (const auto& cr : col_runs(need)) {
                 BK_TRY(launch_accum(X64, Xlo, cr.first / 2, cr.second / 2, st));
                 launches++;
             }
-            BK_TRY(dslash(BK_FP64, X64, R64, B64, cr.first, cr.second, 1));
+        if (deflate) {
+            // X = Y R in FP64 (R64 as the temporary), then the caller's B again
+            // for the true residual in the original basis
+            GenOp g = genop0();
+            g.nmi = 1;
+            g.Mi[0] = X64;
+            g.ma_mult[0] = 1.0;
+            g.M = rfac;
+            g.hasY = 1;
+            g.Y = R64;
+            g.ym = 1.0;
+            BK_TRY(launch_genop(BK_FP64, g, V, st));
+            BK_CUDA_TRY(cudaMemcpyAsync(X64.data, R64.data, field_bytes(Lt, V, BK_FP64), cudaMemcpyDeviceToDevice,
+                                        st));
+            BK_TRY(put_caller_block(Bcaller, B64));
+            bnorm = bnorm_orig;
+            launches += 2;
         }
+        for (const auto& cr : col_runs(need)) BK_TRY(dslash(BK_FP64, X64, R64, B64, cr.first, cr.second, 1));
         BK_TRY(norms_runs(BK_FP64, R64, need));
         BK_TRY(get_caller_block(X64, Xc));
         BK_TRY(readback());
@@ -1331,6 +1450,7 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
     BK_CHECK_ARG(prm->tol > 0 && prm->maxiter >= 0, "tol must be > 0 and maxiter >= 0");
     BK_CHECK_ARG(prm->rtilde_mode >= 0 && prm->rtilde_mode <= 2, "rtilde_mode must be 0, 1 or 2");
     BK_CHECK_ARG(prm->rtilde_mode != 2 || prm->rtilde, "rtilde_mode 2 needs the rtilde block");
+    BK_CHECK_ARG(!prm->deflate || !prm->x0_given, "deflate needs X_0 = 0 (x0_given = 0)");
     int Lu = 0;
     for (int s = 0; s < nsys; ++s) {
         BK_CHECK_ARG(Ls[s] >= 1 && Ls[s] <= 128, "every system needs 1 <= L <= 128");
@@ -1379,6 +1499,9 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
     S.hist.resize(nsys);
     S.true_res.assign(Lt, 0.0);
     S.res_known.assign(nsys, 0);
+    S.deflate = prm->deflate != 0;
+    S.tol_s.assign(nsys, prm->tol);
+    S.ndefl.assign(nsys, 0);
 
     // host buffers (buffers_on_host) are copied in and out a chunk of
     // columns at a time inside setup() and finish()
@@ -1426,6 +1549,7 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
         in.n_dslash_inner = S.n_dslash_inner;
         in.n_launches = S.launches;
         in.cols_dslash_inner = S.cols_inner;
+        in.deflated = S.ndefl[s];
         if (S.done[s] == 2 && result == BK_OK) result = BK_ERR_BREAKDOWN;
         if (S.done[s] == 0 && result == BK_OK) result = BK_ERR_NOT_CONVERGED;
     }

@@ -23,7 +23,12 @@ struct DslashOp {
     int residual;
     const double* kappa;   // host array, ncol entries (kappa of column col0 + j)
     int threads;           // launch shape: threads per block (0 = default)
-    int variant;           // FP32/FP16: 1 = register cap for 1 block of 256 per SM, else 2
+    int variant;           // FP32/FP16: register cap, 1 = 255, 2 = 170, 3 = 128 (0 = 2)
+    int group;             // FP32/FP16: column pairs per group, groups run one after the
+                           // other over all sites (0 = all pairs in one group)
+    int prefetch;          // FP32/FP16: prefetch every row of the eight hops at thread
+                           // start, 0 = no, 1 = into L2, 2 = into L1; 3 = the hops as
+                           // a loop, each prefetching the next hop's rows into L1
 };
 bk_status launch_dslash(int prec, const DslashOp& op, cudaStream_t st);
 
@@ -152,6 +157,7 @@ bk_status launch_canon_dot_diff(const double* A, const double* B, const double* 
 bk_status launch_lu_factor(const double* G, double* LU, int* piv, int* info, const SysPart& p, cudaStream_t st);
 bk_status launch_lu_solve(const double* LU, const int* piv, const double* H, const double* scale_dev,
                           const double* scale_host, double* Xs, int* info, const SysPart& p, cudaStream_t st);
-// S_s = T^H T (Cholesky, FP64, one block per system), Tinv_s = T^-1; identity if
-// S_s is not numerically positive definite.  L <= 118 per system.
-bk_status launch_chol_inv(const double* S, double* Tinv, const SysPart& p, cudaStream_t st);
+// S_s + shift_rel trace(S_s) I = T^H T (Cholesky, FP64, one block per
+// system), Tinv_s = T^-1; identity if not numerically positive definite.
+// L <= 118 per system.
+bk_status launch_chol_inv(const double* S, double* Tinv, const SysPart& p, cudaStream_t st, double shift_rel = 0.0);

@@ -121,14 +121,16 @@ __device__ __forceinline__ double2 warp_sum2(double2 v, int width) {
 // ---------------------------------------------------------------- Gram, small systems
 //
 // G_s = A_s^H B_s (and G2_s = A_s^H B2_s with NB = 2) for systems of at most
-// MAXL columns.  Thread block: SR site rows x 64 pair slots over a tile of
-// whole systems (the site row is the fastest index, so the SR threads of one
-// pair are lanes of one warp); grid: (tiles, site chunks).  Per site every
-// thread puts its pair of A and of each B in shared memory; after a barrier
-// it adds conj(A_i) B_j for its two columns i and every column j of its
-// system.  FP32 / FP16 products are summed in FP32 registers and moved every
-// GS_FLUSH sites into per-pair FP64 accumulators in shared memory, which
-// also combine the SR site rows; chunks are combined in FP64 (fixed order).
+// MAXL columns.  Thread block: 64 pair slots (fastest, so a warp reads one
+// contiguous row) x SR site rows over a tile of whole systems; grid: (tiles,
+// site chunks).  Each thread owns its pair's two columns i and adds
+// conj(A_i) B_j for every column j of its system, reading the partner pairs
+// of B straight from memory (the threads of one system share them through
+// L1): no barrier inside the site loop, so the loads of successive sites
+// overlap.  FP32 / FP16 products are summed in FP32 registers and moved
+// every GS_FLUSH sites into per-pair FP64 accumulators in shared memory
+// (shared atomics), which also combine the SR site rows; chunks are combined
+// in FP64 by the finishing kernel (fixed order).
 
 constexpr int GS_FLUSH = 8;
 
@@ -139,25 +141,25 @@ __global__ void __launch_bounds__(256) k_gram_small(Field A, Field B0, Field B1,
     using R2 = typename Prec<P>::pair;
     constexpr int SR = srows<P>();
     constexpr int FL = P == BK_FP64 ? (1 << 30) : GS_FLUSH;
-    extern __shared__ __align__(16) unsigned char gs_smem[];
-    CxPair<R2>* As = reinterpret_cast<CxPair<R2>*>(gs_smem);  // [SR][12][TILE_MAXP]
-    CxPair<R2>* Bs = As + SR * 12 * TILE_MAXP;                  // [NB][SR][12][TILE_MAXP]
-    double2* Acc = reinterpret_cast<double2*>(Bs + NB * SR * 12 * TILE_MAXP);  // [TILE_MAXP][NB][2][MAXL]
-    const int r = threadIdx.x, t = threadIdx.y;
-    const int tid = t * SR + r;
+    // per site row: no two threads share an entry (dynamic: up to 96 KB)
+    extern __shared__ double2 gs_acc[];
+    constexpr int ACC_ROW = TILE_MAXP * NB * 2 * MAXL;
+    double2(*Acc)[ACC_ROW] = reinterpret_cast<double2(*)[ACC_ROW]>(gs_acc);
+    const int t = threadIdx.x, r = threadIdx.y;
+    const int tid = r * TILE_MAXP + t;
     const int tile = blockIdx.x, chunk = blockIdx.y;
     const int tp0 = tl.p0[tile], tnp = tl.np[tile];
     const bool on = t < tnp;
     const int q = tp0 + t;
-    int s = 0, ps0 = 0, Ls = 0, i0 = 0;
+    int s = 0, qs = 0, Ls = 0, i0 = 0;
     if (on) {
         s = sys_of_pair(p, q);
-        ps0 = p.col0[s] / 2 - tp0;
+        qs = p.col0[s] / 2;
         Ls = p.L[s];
         i0 = 2 * q - p.col0[s];
     }
     const int nps = (Ls + 1) / 2;
-    for (int e = tid; e < TILE_MAXP * NB * 2 * MAXL; e += SR * TILE_MAXP) Acc[e] = make_double2(0.0, 0.0);
+    for (int e = t; e < TILE_MAXP * NB * 2 * MAXL; e += TILE_MAXP) Acc[r][e] = make_double2(0.0, 0.0);
     cx<R> acc[NB][2][MAXL];
 #pragma unroll
     for (int b = 0; b < NB; ++b)
@@ -168,39 +170,39 @@ __global__ void __launch_bounds__(256) k_gram_small(Field A, Field B0, Field B1,
     const int iters = (V + SR * nchunk - 1) / (SR * nchunk);
     for (int it = 0; it < iters; ++it) {
         const int n = (it * nchunk + chunk) * SR + r;
-        const bool live = on && n < V;
-        if (live) {
+        if (on && n < V) {
+            const R2 sa = pair_scale<P>(A, n, q);
+            R2 sb[NB][MAXL / 2];
 #pragma unroll
-            for (int b = 0; b <= NB; ++b) {
-                R2 xr[12], xi[12];
-                load_pair<P>(b == 0 ? A : (b == 1 ? B0 : B1), n, q, xr, xi);
-                CxPair<R2>* dst = b == 0 ? As + r * 12 * TILE_MAXP : Bs + ((b - 1) * SR + r) * 12 * TILE_MAXP;
+            for (int b = 0; b < NB; ++b)
 #pragma unroll
-                for (int k = 0; k < 12; ++k) {
-                    CxPair<R2> v;
-                    v.re = xr[k];
-                    v.im = xi[k];
-                    dst[k * TILE_MAXP + t] = v;
-                }
-            }
-        }
-        __syncthreads();
-        if (live) {
+                for (int jp = 0; jp < MAXL / 2; ++jp)
+                    if (jp < nps) sb[b][jp] = pair_scale<P>(b == 0 ? B0 : B1, n, qs + jp);
 #pragma unroll 2
             for (int k = 0; k < 12; ++k) {
-                const CxPair<R2> aa = As[(r * 12 + k) * TILE_MAXP + t];
+                R2 ar, ai;
+                load_elem<P>(A, n, k, q, ar, ai);
+                if constexpr (P == BK_FP16) {
+                    ar = pmul(ar, sa);
+                    ai = pmul(ai, sa);
+                }
 #pragma unroll
                 for (int jp = 0; jp < MAXL / 2; ++jp) {
                     if (jp < nps) {
 #pragma unroll
                         for (int b = 0; b < NB; ++b) {
-                            const CxPair<R2> bb = Bs[((b * SR + r) * 12 + k) * TILE_MAXP + ps0 + jp];
+                            R2 br, bi;
+                            load_elem<P>(b == 0 ? B0 : B1, n, k, qs + jp, br, bi);
+                            if constexpr (P == BK_FP16) {
+                                br = pmul(br, sb[b][jp]);
+                                bi = pmul(bi, sb[b][jp]);
+                            }
 #pragma unroll
                             for (int ii = 0; ii < 2; ++ii) {
-                                const R xr = ii ? aa.re.y : aa.re.x, xi = ii ? aa.im.y : aa.im.x;
+                                const R xr = ii ? ar.y : ar.x, xi = ii ? ai.y : ai.x;
 #pragma unroll
                                 for (int jj = 0; jj < 2; ++jj) {
-                                    const R yr = jj ? bb.re.y : bb.re.x, yi = jj ? bb.im.y : bb.im.x;
+                                    const R yr = jj ? br.y : br.x, yi = jj ? bi.y : bi.x;
                                     cx<R>& c = acc[b][ii][2 * jp + jj];
                                     c.r = fma(xr, yr, c.r);
                                     c.r = fma(xi, yi, c.r);
@@ -213,19 +215,18 @@ __global__ void __launch_bounds__(256) k_gram_small(Field A, Field B0, Field B1,
                 }
             }
         }
-        __syncthreads();
         if (on && ((it % FL) == FL - 1 || it == iters - 1)) {
-            double2* my = Acc + t * NB * 2 * MAXL;
+            double2* my = Acc[r] + t * NB * 2 * MAXL;  // this thread's own entries
 #pragma unroll
             for (int b = 0; b < NB; ++b)
 #pragma unroll
                 for (int ii = 0; ii < 2; ++ii)
 #pragma unroll
                     for (int j = 0; j < MAXL; ++j) {
-                        if (j < Ls) {
-                            atomicAdd(&my[(b * 2 + ii) * MAXL + j].x, (double)acc[b][ii][j].r);
-                            atomicAdd(&my[(b * 2 + ii) * MAXL + j].y, (double)acc[b][ii][j].i);
-                        }
+                        double2 v = my[(b * 2 + ii) * MAXL + j];
+                        v.x += (double)acc[b][ii][j].r;
+                        v.y += (double)acc[b][ii][j].i;
+                        my[(b * 2 + ii) * MAXL + j] = v;
                         acc[b][ii][j] = mk(R(0), R(0));
                     }
         }
@@ -233,13 +234,18 @@ __global__ void __launch_bounds__(256) k_gram_small(Field A, Field B0, Field B1,
     __syncthreads();
     if (!on || r != 0) return;
     const int ne = p.coef_off[p.nsys];
-    const double2* my = Acc + t * NB * 2 * MAXL;
     for (int b = 0; b < NB; ++b)
         for (int ii = 0; ii < 2; ++ii)
             for (int j = 0; j < Ls; ++j)
-                if (i0 + ii < Ls)
-                    partial[(size_t)(b * nchunk + chunk) * ne + p.coef_off[s] + (i0 + ii) * Ls + j] =
-                        my[(b * 2 + ii) * MAXL + j];
+                if (i0 + ii < Ls) {
+                    double2 v = make_double2(0.0, 0.0);
+                    for (int rr = 0; rr < SR; ++rr) {
+                        const double2 a = Acc[rr][t * NB * 2 * MAXL + (b * 2 + ii) * MAXL + j];
+                        v.x += a.x;
+                        v.y += a.y;
+                    }
+                    partial[(size_t)(b * nchunk + chunk) * ne + p.coef_off[s] + (i0 + ii) * Ls + j] = v;
+                }
 }
 
 // ---------------------------------------------------------------- Gram, any system size
@@ -384,15 +390,16 @@ __global__ void k_gram_finish(const double2* __restrict__ partial, int nchunk, i
 // groups, site chunks).  Sums as in the Gram kernels; the 8 site rows are
 // combined in shared memory.
 
-template <int P, int NPAIR>
+template <int P, int NPAIR, int TX>
 __global__ void __launch_bounds__(256) k_coldot(Field A0, Field B0, Field A1, Field B1, int q0, int nq,
                                                 double2* __restrict__ partial, int V, int nchunk) {
     using R = typename Prec<P>::real;
     using R2 = typename Prec<P>::pair;
+    constexpr int TY = 256 / TX;  // site rows: narrow column ranges get more sites per block
     constexpr int FL = P == BK_FP64 ? (1 << 30) : GS_FLUSH;
-    __shared__ double2 red[8][32][NPAIR * 2];
+    __shared__ double2 red[TY][TX][NPAIR * 2];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int ql = blockIdx.x * 32 + tx, q = q0 + ql;
+    const int ql = blockIdx.x * TX + tx, q = q0 + ql;
     const bool on = ql < nq;
     const int chunk = blockIdx.y;
     cx<R> acc[NPAIR][2];
@@ -404,9 +411,9 @@ __global__ void __launch_bounds__(256) k_coldot(Field A0, Field B0, Field A1, Fi
             acc[kk][h] = mk(R(0), R(0));
             acc64[kk][h] = make_double2(0.0, 0.0);
         }
-    const int iters = (V + 8 * nchunk - 1) / (8 * nchunk);
+    const int iters = (V + TY * nchunk - 1) / (TY * nchunk);
     for (int it = 0; it < iters; ++it) {
-        const int n = (it * nchunk + chunk) * 8 + ty;
+        const int n = (it * nchunk + chunk) * TY + ty;
         if (on && n < V) {
 #pragma unroll
             for (int kk = 0; kk < NPAIR; ++kk) {
@@ -448,7 +455,7 @@ __global__ void __launch_bounds__(256) k_coldot(Field A0, Field B0, Field A1, Fi
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 double2 v = make_double2(0.0, 0.0);
-                for (int y = 0; y < 8; ++y) {
+                for (int y = 0; y < TY; ++y) {
                     v.x += red[y][tx][kk * 2 + h].x;
                     v.y += red[y][tx][kk * 2 + h].y;
                 }
@@ -531,21 +538,21 @@ __global__ void __launch_bounds__(256) k_genop(const __grid_constant__ GenOp g, 
     using XR = typename Prec<XP>::real;
     using X2 = typename Prec<XP>::pair;
     constexpr int SR = srows<P>();
-    extern __shared__ __align__(16) unsigned char go_smem[];
-    CxPair<R2>* Cs = reinterpret_cast<CxPair<R2>*>(go_smem);  // [SR][12][TILE_MAXP]
-    const int r = threadIdx.x, t = threadIdx.y;
+    __shared__ double2 ynred[SR][TILE_MAXP];
+    const int t = threadIdx.x, r = threadIdx.y;
     const int tile = blockIdx.x, chunk = blockIdx.y;
     const int tp0 = tl.p0[tile], tnp = tl.np[tile];
     bool on = t < tnp;
     const int q = tp0 + t;
-    int s = 0, ps0 = 0, Ls = 0, i0 = 0;
+    int s = 0, qs = 0, Ls = 0, i0 = 0;
     if (on) {
         s = sys_of_pair(g.p, q);
-        ps0 = g.p.col0[s] / 2 - tp0;
+        qs = g.p.col0[s] / 2;
         Ls = g.p.L[s];
         i0 = 2 * q - g.p.col0[s];
         if (g.skip && g.skip[s]) on = false;
     }
+    const int nps = (Ls + 1) / 2;
     const bool mat = g.nmi > 0 && g.M != nullptr && ((g.hasY && g.ym != 0.0) || (g.hasX && g.xm != 0.0));
     cx<R> ea[GENOP_MAXE], ma[GENOP_MAXMI], xa = mk(R(0), R(0));
 #pragma unroll
@@ -571,134 +578,141 @@ __global__ void __launch_bounds__(256) k_genop(const __grid_constant__ GenOp g, 
             Mi[i].y = (R)m1.y;
         }
     }
-    R2 ym2, xm2r;
+    R2 ym2;
     ym2.x = (R)g.ym;
     ym2.y = (R)g.ym;
     X2 xm2;
     xm2.x = (XR)g.xm;
     xm2.y = (XR)g.xm;
-    (void)xm2r;
     double yn[2] = {0.0, 0.0};
     const int iters = (V + SR * nchunk - 1) / (SR * nchunk);
     for (int it = 0; it < iters; ++it) {
         const int n = (it * nchunk + chunk) * SR + r;
-        const bool live = on && n < V;
-        if (mat) {
-            if (live) {
-                R2 msc[GENOP_MAXMI];
+        if (!on || n >= V) continue;
+        R2 esc[GENOP_MAXE];
 #pragma unroll
-                for (int u = 0; u < GENOP_MAXMI; ++u)
-                    if (u < g.nmi) msc[u] = pair_scale<P>(g.Mi[u], n, q);
-#pragma unroll 4
-                for (int k = 0; k < 12; ++k) {
+        for (int e = 0; e < GENOP_MAXE; ++e)
+            if (e < g.ne) esc[e] = pair_scale<P>(g.E[e], n, q);
+        const R2 xsc = g.hasX ? pair_scale<P>(g.Xin, n, q) : pzero<R2>();
+        R2 yr[P == BK_FP16 ? 12 : 1], yi[P == BK_FP16 ? 12 : 1];
+        R sa = R(0), sb = R(0);
+#pragma unroll 2
+        for (int k = 0; k < 12; ++k) {
+            // matpart of the thread's columns j = i0, i0 + 1 (pair over j):
+            // comb_i = sum_u ma_u Mi_u,i for every column i of the system, read
+            // pair by pair (the system's threads share the rows through L1)
+            CxPair<R2> mp;
+            mp.re = pzero<R2>();
+            mp.im = pzero<R2>();
+            if (mat) {
+                // one partner pair ip of the system at a time; i = 2 ip + h
+                auto accumulate = [&](int ip, const R2 (&mr2)[2], const R2 (&mi2)[2]) {
                     CxPair<R2> c;
                     c.re = pzero<R2>();
                     c.im = pzero<R2>();
 #pragma unroll
                     for (int u = 0; u < GENOP_MAXMI; ++u)
-                        if (u < g.nmi) cpair_mac<R, R2>(c, ma[u], load_scaled<P>(g.Mi[u], n, k, q, msc[u]));
-                    Cs[(r * 12 + k) * TILE_MAXP + t] = c;
-                }
-            }
-            __syncthreads();
-        }
-        if (live) {
-            R2 esc[GENOP_MAXE];
+                        if (u < g.nmi)
+                            cpair_mac<R, R2>(c, ma[u], load_scaled<P>(g.Mi[u], n, k, qs + ip,
+                                                                      pair_scale<P>(g.Mi[u], n, qs + ip)));
 #pragma unroll
-            for (int e = 0; e < GENOP_MAXE; ++e)
-                if (e < g.ne) esc[e] = pair_scale<P>(g.E[e], n, q);
-            const R2 xsc = g.hasX ? pair_scale<P>(g.Xin, n, q) : pzero<R2>();
-            R2 yr[P == BK_FP16 ? 12 : 1], yi[P == BK_FP16 ? 12 : 1];
-            R sa = R(0), sb = R(0);
-#pragma unroll 2
-            for (int k = 0; k < 12; ++k) {
-                CxPair<R2> mp;
-                mp.re = pzero<R2>();
-                mp.im = pzero<R2>();
-                if (mat) {
-                    const CxPair<R2>* crow = Cs + (r * 12 + k) * TILE_MAXP + ps0;
-                    if constexpr (MAXL > 0) {
+                    for (int h = 0; h < 2; ++h) {
+                        const R cr = h ? c.re.y : c.re.x, ci = h ? c.im.y : c.im.x;
+                        R2 crr, cii, nmi;
+                        crr.x = cr;
+                        crr.y = cr;
+                        cii.x = ci;
+                        cii.y = ci;
+                        nmi.x = -mi2[h].x;
+                        nmi.y = -mi2[h].y;
+                        mp.re = pfma(crr, mr2[h], mp.re);
+                        mp.re = pfma(cii, nmi, mp.re);
+                        mp.im = pfma(crr, mi2[h], mp.im);
+                        mp.im = pfma(cii, mr2[h], mp.im);
+                    }
+                };
+                if constexpr (MAXL > 0) {
 #pragma unroll
-                        for (int i = 0; i < MAXL; ++i) {
+                    for (int ip = 0; ip < MAXL / 2; ++ip) {
+                        if (ip < nps) {
+                            // an odd system's padding column has M rows of zero
+                            const R2 mr2[2] = {Mr[2 * ip], Mr[2 * ip + 1]};
+                            const R2 mi2[2] = {Mi[2 * ip], Mi[2 * ip + 1]};
+                            accumulate(ip, mr2, mi2);
+                        }
+                    }
+                } else {
+                    for (int ip = 0; ip < nps; ++ip) {
+                        R2 mr2[2], mi2[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int i = 2 * ip + h;
+                            double2 m0 = make_double2(0.0, 0.0), m1 = make_double2(0.0, 0.0);
                             if (i < Ls) {
-                                const CxPair<R2> cc = crow[i >> 1];
-                                const R cr = (i & 1) ? cc.re.y : cc.re.x, ci = (i & 1) ? cc.im.y : cc.im.x;
-                                R2 crr, cii, nmi;
-                                crr.x = cr;
-                                crr.y = cr;
-                                cii.x = ci;
-                                cii.y = ci;
-                                nmi.x = -Mi[i].x;
-                                nmi.y = -Mi[i].y;
-                                mp.re = pfma(crr, Mr[i], mp.re);
-                                mp.re = pfma(cii, nmi, mp.re);
-                                mp.im = pfma(crr, Mi[i], mp.im);
-                                mp.im = pfma(cii, Mr[i], mp.im);
+                                m0 = __ldg(M + i * Ls + i0);
+                                if (j1ok) m1 = __ldg(M + i * Ls + i0 + 1);
                             }
+                            mr2[h].x = (R)m0.x;
+                            mr2[h].y = (R)m1.x;
+                            mi2[h].x = (R)m0.y;
+                            mi2[h].y = (R)m1.y;
                         }
-                    } else {
-                        for (int i = 0; i < Ls; ++i) {
-                            const double2 m0 = __ldg(M + i * Ls + i0);
-                            const double2 m1 = j1ok ? __ldg(M + i * Ls + i0 + 1) : make_double2(0.0, 0.0);
-                            const CxPair<R2> cc = crow[i >> 1];
-                            const R cr = (i & 1) ? cc.re.y : cc.re.x, ci = (i & 1) ? cc.im.y : cc.im.x;
-                            // mp += c * M (pair over the two columns j)
-                            mp.re.x += cr * (R)m0.x - ci * (R)m0.y;
-                            mp.re.y += cr * (R)m1.x - ci * (R)m1.y;
-                            mp.im.x += cr * (R)m0.y + ci * (R)m0.x;
-                            mp.im.y += cr * (R)m1.y + ci * (R)m1.x;
-                        }
+                        accumulate(ip, mr2, mi2);
                     }
                 }
-                if (g.hasY) {
-                    CxPair<R2> y;
-                    y.re = pmul(ym2, mp.re);
-                    y.im = pmul(ym2, mp.im);
+            }
+            if (g.hasY) {
+                CxPair<R2> y;
+                y.re = pmul(ym2, mp.re);
+                y.im = pmul(ym2, mp.im);
 #pragma unroll
-                    for (int e = 0; e < GENOP_MAXE; ++e)
-                        if (e < g.ne) cpair_mac<R, R2>(y, ea[e], load_scaled<P>(g.E[e], n, k, q, esc[e]));
-                    if (g.ynorm) {
-                        sa = fma(y.re.x, y.re.x, sa);
-                        sa = fma(y.im.x, y.im.x, sa);
-                        sb = fma(y.re.y, y.re.y, sb);
-                        sb = fma(y.im.y, y.im.y, sb);
-                    }
-                    if constexpr (P == BK_FP16) {
-                        yr[k] = y.re;
-                        yi[k] = y.im;
-                    } else {
-                        store_elem<P>(g.Y, n, k, q, y.re, y.im);
-                    }
+                for (int e = 0; e < GENOP_MAXE; ++e)
+                    if (e < g.ne) cpair_mac<R, R2>(y, ea[e], load_scaled<P>(g.E[e], n, k, q, esc[e]));
+                if (g.ynorm) {
+                    sa = fma(y.re.x, y.re.x, sa);
+                    sa = fma(y.im.x, y.im.x, sa);
+                    sb = fma(y.re.y, y.re.y, sb);
+                    sb = fma(y.im.y, y.im.y, sb);
                 }
-                if (g.hasX) {
-                    const CxPair<R2> v = load_scaled<P>(g.Xin, n, k, q, xsc);
-                    CxPair<X2> x, vx;
-                    load_elem<XP>(g.X, n, k, q, x.re, x.im);
-                    vx.re.x = v.re.x;
-                    vx.re.y = v.re.y;
-                    vx.im.x = v.im.x;
-                    vx.im.y = v.im.y;
-                    cpair_mac<XR, X2>(x, mk((XR)xa.r, (XR)xa.i), vx);
-                    X2 mr, mi;
-                    mr.x = mp.re.x;
-                    mr.y = mp.re.y;
-                    mi.x = mp.im.x;
-                    mi.y = mp.im.y;
-                    store_elem<XP>(g.X, n, k, q, pfma(xm2, mr, x.re), pfma(xm2, mi, x.im));
+                if constexpr (P == BK_FP16) {
+                    yr[k] = y.re;
+                    yi[k] = y.im;
+                } else {
+                    store_elem<P>(g.Y, n, k, q, y.re, y.im);
                 }
             }
-            if constexpr (P == BK_FP16) {
-                if (g.hasY) store_pair<P>(g.Y, n, q, yr, yi);
+            if (g.hasX) {
+                const CxPair<R2> v = load_scaled<P>(g.Xin, n, k, q, xsc);
+                CxPair<X2> x, vx;
+                load_elem<XP>(g.X, n, k, q, x.re, x.im);
+                vx.re.x = v.re.x;
+                vx.re.y = v.re.y;
+                vx.im.x = v.im.x;
+                vx.im.y = v.im.y;
+                cpair_mac<XR, X2>(x, mk((XR)xa.r, (XR)xa.i), vx);
+                X2 mr, mi;
+                mr.x = mp.re.x;
+                mr.y = mp.re.y;
+                mi.x = mp.im.x;
+                mi.y = mp.im.y;
+                store_elem<XP>(g.X, n, k, q, pfma(xm2, mr, x.re), pfma(xm2, mi, x.im));
             }
-            yn[0] += (double)sa;
-            yn[1] += (double)sb;
         }
-        if (mat) __syncthreads();
+        if constexpr (P == BK_FP16) {
+            if (g.hasY) store_pair<P>(g.Y, n, q, yr, yi);
+        }
+        yn[0] += (double)sa;
+        yn[1] += (double)sb;
     }
     if (g.ynorm) {
-        double2 v = make_double2(yn[0], yn[1]);
-        v = warp_sum2(v, SR);
+        ynred[r][t] = make_double2(yn[0], yn[1]);
+        __syncthreads();
         if (on && r == 0) {
+            double2 v = make_double2(0.0, 0.0);
+            for (int rr = 0; rr < SR; ++rr) {
+                v.x += ynred[rr][t].x;
+                v.y += ynred[rr][t].y;
+            }
             g.ynorm[(size_t)chunk * ncols + 2 * q] = v.x;
             g.ynorm[(size_t)chunk * ncols + 2 * q + 1] = v.y;
         }
@@ -990,7 +1004,7 @@ __global__ void __launch_bounds__(128) k_lu_solve(const double2* __restrict__ LU
 // numerically positive definite, Tinv = identity (the basis is left as it is).
 
 __global__ void __launch_bounds__(256) k_chol_inv(const double2* __restrict__ S, double2* __restrict__ Tinv,
-                                                  SysPart p) {
+                                                  SysPart p, double shift_rel) {
     extern __shared__ double2 ch_smem_raw[];
     const int s = blockIdx.x;
     if (!((p.active >> s) & 1u)) return;
@@ -1005,10 +1019,18 @@ __global__ void __launch_bounds__(256) k_chol_inv(const double2* __restrict__ S,
         const double2 v = S[off + e];
         A[e] = mk(v.x, v.y);
     }
+    __syncthreads();  // the diagonal shift below updates entries other threads loaded
     if (tid == 0) {
         bad = 0;
         dmax = 0.0;
-        for (int k = 0; k < n; ++k) dmax = fmax(dmax, S[off + k * n + k].x);
+        double tr = 0.0;
+        for (int k = 0; k < n; ++k) {
+            dmax = fmax(dmax, S[off + k * n + k].x);
+            tr += S[off + k * n + k].x;
+        }
+        // shifted factorisation S + shift_rel trace(S) I (shifted Cholesky QR)
+        if (shift_rel > 0.0)
+            for (int k = 0; k < n; ++k) A[k * n + k].r += shift_rel * tr;
     }
     __syncthreads();
     for (int k = 0; k < n; ++k) {
@@ -1073,11 +1095,10 @@ template <int P, int NB, int MAXL>
 bk_status run_gram_small(Field A, Field B0, Field B1, const SysPart& p, const PTiles& tl, double2* part,
                          int nchunk, int V, cudaStream_t st) {
     constexpr int SR = srows<P>();
-    const size_t smem = (size_t)(NB + 1) * pair_smem<P>(SR, TILE_MAXP) +
-                        (size_t)TILE_MAXP * NB * 2 * MAXL * sizeof(double2);
+    const size_t smem = (size_t)SR * TILE_MAXP * NB * 2 * MAXL * sizeof(double2);
     BK_CUDA_TRY(cudaFuncSetAttribute(k_gram_small<P, NB, MAXL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-    k_gram_small<P, NB, MAXL><<<dim3(tl.n, nchunk), dim3(SR, TILE_MAXP), smem, st>>>(A, B0, B1, p, tl, part, V,
+    k_gram_small<P, NB, MAXL><<<dim3(tl.n, nchunk), dim3(TILE_MAXP, SR), smem, st>>>(A, B0, B1, p, tl, part, V,
                                                                                   nchunk);
     BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
@@ -1189,10 +1210,17 @@ bk_status launch_coldot(int prec, int npair, const Field* A, const Field* B, int
     }
     const int q0 = c0 / 2, nq = (n + 1) / 2;
     const int nchunk = site_chunks(V);
-    dim3 blk(32, 8), grid((nq + 31) / 32, nchunk);
     double2* part = (double2*)partial;
     const Field A1 = npair > 1 ? A[1] : A[0], B1 = npair > 1 ? B[1] : B[0];
-#define BK_CD(PP, NP) k_coldot<PP, NP><<<grid, blk, 0, st>>>(A[0], B[0], A1, B1, q0, nq, part, V, nchunk)
+    // pair slots per block: the smallest of 4, 8, 16, 32 that covers the range
+    const int tx = nq <= 4 ? 4 : (nq <= 8 ? 8 : (nq <= 16 ? 16 : 32));
+    dim3 grid((nq + tx - 1) / tx, nchunk);
+#define BK_CD1(PP, NP, TX) k_coldot<PP, NP, TX><<<grid, dim3(TX, 256 / TX), 0, st>>>(A[0], B[0], A1, B1, q0, nq, part, V, nchunk)
+#define BK_CD(PP, NP)                       \
+    if (tx == 4) BK_CD1(PP, NP, 4);         \
+    else if (tx == 8) BK_CD1(PP, NP, 8);    \
+    else if (tx == 16) BK_CD1(PP, NP, 16);  \
+    else BK_CD1(PP, NP, 32);
     if (npair == 1) {
         switch (prec) {
             case BK_FP64: BK_CD(BK_FP64, 1); break;
@@ -1209,6 +1237,7 @@ bk_status launch_coldot(int prec, int npair, const Field* A, const Field* B, int
         }
     }
 #undef BK_CD
+#undef BK_CD1
     BK_CUDA_TRY(cudaGetLastError());
     k_coldot_finish<<<(npair * n + 127) / 128, 128, 0, st>>>(part, nchunk, npair, nq, n,
                                                              (double2*)out + c0, ldo);
@@ -1231,9 +1260,7 @@ bk_status launch_genop(int prec, const GenOp& g, int V, cudaStream_t st, bool* y
 #define BK_GO(PP, ML)                                                                                       \
     {                                                                                                       \
         constexpr int SR = srows<PP>();                                                                     \
-        const size_t smem = pair_smem<PP>(SR, TILE_MAXP);                                                   \
-        BK_CUDA_TRY(cudaFuncSetAttribute(k_genop<PP, ML>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        k_genop<PP, ML><<<dim3(tl.n, nchunk), dim3(SR, TILE_MAXP), smem, st>>>(g, tl, V, nchunk, ncols);     \
+        k_genop<PP, ML><<<dim3(tl.n, nchunk), dim3(TILE_MAXP, SR), 0, st>>>(g, tl, V, nchunk, ncols);        \
     }
 #define BK_GOP(PP)                        \
     if (ml == 6) BK_GO(PP, 6)             \
@@ -1330,7 +1357,7 @@ bk_status launch_lu_solve(const double* LU, const int* piv, const double* H, con
     return BK_OK;
 }
 
-bk_status launch_chol_inv(const double* S, double* Tinv, const SysPart& p, cudaStream_t st) {
+bk_status launch_chol_inv(const double* S, double* Tinv, const SysPart& p, cudaStream_t st, double shift_rel) {
     int maxL = 0;
     for (int s = 0; s < p.nsys; ++s) maxL = std::max(maxL, p.L[s]);
     if (maxL > 118) {
@@ -1339,7 +1366,7 @@ bk_status launch_chol_inv(const double* S, double* Tinv, const SysPart& p, cudaS
     }
     const size_t smem = (size_t)maxL * maxL * sizeof(double2);
     BK_CUDA_TRY(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_chol_inv<<<p.nsys, 256, smem, st>>>((const double2*)S, (double2*)Tinv, p);
+    k_chol_inv<<<p.nsys, 256, smem, st>>>((const double2*)S, (double2*)Tinv, p, shift_rel);
     BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
 }

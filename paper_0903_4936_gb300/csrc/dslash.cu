@@ -42,6 +42,7 @@ struct DPairArgs {
     const float4* __restrict__ C;  // packed-pair clover, BK_CLOV32_F4 float4 per site
     int L[4], st[4];
     int V, p0, npl, residual;
+    int G;  // pairs per group: all sites of group g run before group g + 1 starts
     float2 nk[BK_MAX_COLS / 2];  // {-kappa_2p, -kappa_2p+1} of launch pair p - p0
 };
 
@@ -310,12 +311,104 @@ __device__ __forceinline__ void clover_pair(const float4* __restrict__ c4, const
     }
 }
 
-template <int P, int MAXT, int MINB>
+// Prefetch (no register cost) of every row this thread will read: the eight
+// neighbours' spinor elements of its pair and the eight links, so that the
+// DRAM requests of all hops are in flight at once instead of one hop after
+// the other.  PF 1: into L2, PF 2: into L1.
+template <int PF>
+__device__ __forceinline__ void prefetch_row(const void* ptr) {
+    if constexpr (PF == 1) asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+    if constexpr (PF == 2) asm volatile("prefetch.global.L1 [%0];" ::"l"(ptr));
+}
+
+template <int P, int PF>
+__device__ __forceinline__ void prefetch_hops(const DPairArgs& a, const int (&co)[4], int n, int p) {
+    if constexpr (PF > 0) {
+        const int eb = Prec<P>::ebytes;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const int Lm = a.L[mu], sm = a.st[mu];
+            const int nf = co[mu] == Lm - 1 ? n - (Lm - 1) * sm : n + sm;
+            const int nb = co[mu] == 0 ? n + (Lm - 1) * sm : n - sm;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                prefetch_row<PF>((const char*)a.x.data + (((size_t)nf * 12 + k) * a.x.np + p) * eb);
+                prefetch_row<PF>((const char*)a.x.data + (((size_t)nb * 12 + k) * a.x.np + p) * eb);
+            }
+            const float4* lf = a.U + ((size_t)mu * a.V + n) * BK_LINK32_F4;
+            const float4* lb = a.U + ((size_t)mu * a.V + nb) * BK_LINK32_F4;
+            prefetch_row<PF>(lf);
+            prefetch_row<PF>(lf + 8);
+            prefetch_row<PF>(lb);
+            prefetch_row<PF>(lb + 8);
+        }
+    }
+}
+
+// Looped form (PF 3): the eight hops run as a loop the compiler does not
+// unroll, so only one hop's operands are live (fewer registers, more resident
+// warps); while hop h computes, the rows of hop h + 1 are prefetched into L1.
+template <int P>
+__device__ __forceinline__ void prefetch_hop_l1(const DPairArgs& a, int nbr, int mu, int link_site, int p) {
+    const int eb = Prec<P>::ebytes;
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"((const char*)a.x.data + (((size_t)nbr * 12 + k) * a.x.np + p) * eb));
+    const float4* l = a.U + ((size_t)mu * a.V + link_site) * BK_LINK32_F4;
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(l));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(l + 8));
+}
+
+template <int P>
+__device__ __forceinline__ void hops_looped(const DPairArgs& a, const int (&co)[4], int n, int p, float2 nk,
+                                            float2 pk, float2 (&ar)[12], float2 (&ai)[12]) {
+    int nbr[8];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        const int Lm = a.L[mu], sm = a.st[mu];
+        nbr[2 * mu] = co[mu] == Lm - 1 ? n - (Lm - 1) * sm : n + sm;
+        nbr[2 * mu + 1] = co[mu] == 0 ? n + (Lm - 1) * sm : n - sm;
+    }
+    prefetch_hop_l1<P>(a, nbr[0], 0, n, p);
+#pragma unroll 1
+    for (int h = 0; h < 8; ++h) {
+        const int mu = h >> 1;
+        const int nb = h == 0 ? nbr[0] : h == 1 ? nbr[1] : h == 2 ? nbr[2] : h == 3 ? nbr[3]
+                     : h == 4 ? nbr[4] : h == 5 ? nbr[5] : h == 6 ? nbr[6] : nbr[7];
+        if (h < 7) {
+            const int h1 = h + 1;
+            const int nb1 = h1 == 1 ? nbr[1] : h1 == 2 ? nbr[2] : h1 == 3 ? nbr[3] : h1 == 4 ? nbr[4]
+                          : h1 == 5 ? nbr[5] : h1 == 6 ? nbr[6] : nbr[7];
+            prefetch_hop_l1<P>(a, nb1, h1 >> 1, (h1 & 1) ? nb1 : n, p);
+        }
+        const float4* link = a.U + ((size_t)mu * a.V + ((h & 1) ? nb : n)) * BK_LINK32_F4;
+        switch (h) {
+            case 0: hop_pair<P, 0, -1>(a, nb, p, link, nk, pk, ar, ai); break;
+            case 1: hop_pair<P, 0, +1>(a, nb, p, link, nk, pk, ar, ai); break;
+            case 2: hop_pair<P, 1, -1>(a, nb, p, link, nk, pk, ar, ai); break;
+            case 3: hop_pair<P, 1, +1>(a, nb, p, link, nk, pk, ar, ai); break;
+            case 4: hop_pair<P, 2, -1>(a, nb, p, link, nk, pk, ar, ai); break;
+            case 5: hop_pair<P, 2, +1>(a, nb, p, link, nk, pk, ar, ai); break;
+            case 6: hop_pair<P, 3, -1>(a, nb, p, link, nk, pk, ar, ai); break;
+            default: hop_pair<P, 3, +1>(a, nb, p, link, nk, pk, ar, ai); break;
+        }
+    }
+}
+
+template <int P, int MAXT, int MINB, int PF>
 __global__ void __launch_bounds__(MAXT, MINB) k_dslash_pair(const __grid_constant__ DPairArgs a) {
+    // Thread order: pair groups of G pairs outermost, then sites, then the
+    // group's pairs.  The blocks run roughly in this order, so the neighbour
+    // rows a group needs one time slice later are still in L2 (the window is
+    // two time slices of G pairs, not of every column).
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= (long long)a.V * a.npl) return;
-    const int n = (int)(g / a.npl);
-    const int pl = (int)(g - (long long)n * a.npl);
+    const long long per_group = (long long)a.V * a.G;
+    const int grp = (int)(g / per_group);
+    const long long r = g - (long long)grp * per_group;
+    const int gw = min(a.G, a.npl - grp * a.G);  // pairs in this group (the last may be short)
+    const int n = (int)(r / gw);
+    const int pl = grp * a.G + (int)(r - (long long)n * gw);
     const int p = a.p0 + pl;
     int co[4];
     {
@@ -327,6 +420,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_dslash_pair(const __grid_constan
         co[2] = r % a.L[2];
         co[3] = r / a.L[2];
     }
+    prefetch_hops<P, PF>(a, co, n, p);
     const float2 nk = a.nk[pl];
     const float2 pk = make_float2(-nk.x, -nk.y);
     float2 ar[12], ai[12];
@@ -335,10 +429,14 @@ __global__ void __launch_bounds__(MAXT, MINB) k_dslash_pair(const __grid_constan
         load_pair<P>(a.x, n, p, qr, qi);
         clover_pair(a.C + (size_t)n * BK_CLOV32_F4, qr, qi, nk, ar, ai);
     }
-    hop_dir_pair<P, 0>(a, co, n, p, nk, pk, ar, ai);
-    hop_dir_pair<P, 1>(a, co, n, p, nk, pk, ar, ai);
-    hop_dir_pair<P, 2>(a, co, n, p, nk, pk, ar, ai);
-    hop_dir_pair<P, 3>(a, co, n, p, nk, pk, ar, ai);
+    if constexpr (PF == 3) {
+        hops_looped<P>(a, co, n, p, nk, pk, ar, ai);
+    } else {
+        hop_dir_pair<P, 0>(a, co, n, p, nk, pk, ar, ai);
+        hop_dir_pair<P, 1>(a, co, n, p, nk, pk, ar, ai);
+        hop_dir_pair<P, 2>(a, co, n, p, nk, pk, ar, ai);
+        hop_dir_pair<P, 3>(a, co, n, p, nk, pk, ar, ai);
+    }
     if (a.residual) {  // b - D x
         float2 br[12], bi[12];
         load_pair<P>(a.b, n, p, br, bi);
@@ -349,307 +447,6 @@ __global__ void __launch_bounds__(MAXT, MINB) k_dslash_pair(const __grid_constan
         }
     }
     store_pair<P>(a.y, n, p, ar, ai);
-}
-
-// ----------------------------------------------------------------- colour-split form
-//
-// The same operator with three threads per (site, column pair), one per
-// colour c: each keeps only the four spin components of its colour (a
-// quarter of the accumulators), loads only its colour's spin components of
-// each neighbour, projects them, and receives the other two colours'
-// projected half spinors from its two partner lanes by warp shuffles; it
-// then multiplies row c of the link (column c for U^+) and expands into its
-// own components.  Lanes 3 j + c (j < 10) of a warp serve ten (site, pair)
-// slots; lanes 30 and 31 repeat slot 9 and store nothing.  Fewer registers
-// per thread and three times the threads per site give the memory system
-// more independent warps to overlap.
-
-template <int MU, int S>
-__device__ __forceinline__ void project_colour(const float2 (&qr)[4], const float2 (&qi)[4], float2& h0r,
-                                               float2& h0i, float2& h1r, float2& h1i) {
-    // qr/qi[s] = spin s of the thread's colour
-    if constexpr (MU == 0) {
-        if constexpr (S > 0) {
-            h0r = padd(qr[0], qi[3]); h0i = psub(qi[0], qr[3]);
-            h1r = padd(qr[1], qi[2]); h1i = psub(qi[1], qr[2]);
-        } else {
-            h0r = psub(qr[0], qi[3]); h0i = padd(qi[0], qr[3]);
-            h1r = psub(qr[1], qi[2]); h1i = padd(qi[1], qr[2]);
-        }
-    } else if constexpr (MU == 1) {
-        if constexpr (S > 0) {
-            h0r = psub(qr[0], qr[3]); h0i = psub(qi[0], qi[3]);
-            h1r = padd(qr[1], qr[2]); h1i = padd(qi[1], qi[2]);
-        } else {
-            h0r = padd(qr[0], qr[3]); h0i = padd(qi[0], qi[3]);
-            h1r = psub(qr[1], qr[2]); h1i = psub(qi[1], qi[2]);
-        }
-    } else if constexpr (MU == 2) {
-        if constexpr (S > 0) {
-            h0r = padd(qr[0], qi[2]); h0i = psub(qi[0], qr[2]);
-            h1r = psub(qr[1], qi[3]); h1i = padd(qi[1], qr[3]);
-        } else {
-            h0r = psub(qr[0], qi[2]); h0i = padd(qi[0], qr[2]);
-            h1r = padd(qr[1], qi[3]); h1i = psub(qi[1], qr[3]);
-        }
-    } else {
-        if constexpr (S > 0) {
-            h0r = qr[0]; h0i = qi[0]; h1r = qr[1]; h1i = qi[1];
-        } else {
-            h0r = qr[2]; h0i = qi[2]; h1r = qr[3]; h1i = qi[3];
-        }
-    }
-}
-
-__device__ __forceinline__ float2 shfl2(float2 v, int src) {
-    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
-}
-
-// acc (spins 0..3 of the thread's colour) += -kappa expand(w0, w1)
-template <int MU, int S>
-__device__ __forceinline__ void reconstruct_colour(float2 w0r, float2 w0i, float2 w1r, float2 w1i, float2 nk,
-                                                   float2 pk, float2 (&ar)[4], float2 (&ai)[4]) {
-    if constexpr (MU == 3) {
-        const float2 n2 = padd(nk, nk);
-        const int s0 = S > 0 ? 0 : 2;
-        ar[s0] = pfma(n2, w0r, ar[s0]);
-        ai[s0] = pfma(n2, w0i, ai[s0]);
-        ar[s0 + 1] = pfma(n2, w1r, ar[s0 + 1]);
-        ai[s0 + 1] = pfma(n2, w1i, ai[s0 + 1]);
-    } else {
-        ar[0] = pfma(nk, w0r, ar[0]);
-        ai[0] = pfma(nk, w0i, ai[0]);
-        ar[1] = pfma(nk, w1r, ar[1]);
-        ai[1] = pfma(nk, w1i, ai[1]);
-        if constexpr (MU == 0) {  // lower = (i S w1, i S w0)
-            if constexpr (S > 0) {
-                ar[2] = pfma(pk, w1i, ar[2]); ai[2] = pfma(nk, w1r, ai[2]);
-                ar[3] = pfma(pk, w0i, ar[3]); ai[3] = pfma(nk, w0r, ai[3]);
-            } else {
-                ar[2] = pfma(nk, w1i, ar[2]); ai[2] = pfma(pk, w1r, ai[2]);
-                ar[3] = pfma(nk, w0i, ar[3]); ai[3] = pfma(pk, w0r, ai[3]);
-            }
-        } else if constexpr (MU == 1) {  // lower = (S w1, -S w0)
-            if constexpr (S > 0) {
-                ar[2] = pfma(nk, w1r, ar[2]); ai[2] = pfma(nk, w1i, ai[2]);
-                ar[3] = pfma(pk, w0r, ar[3]); ai[3] = pfma(pk, w0i, ai[3]);
-            } else {
-                ar[2] = pfma(pk, w1r, ar[2]); ai[2] = pfma(pk, w1i, ai[2]);
-                ar[3] = pfma(nk, w0r, ar[3]); ai[3] = pfma(nk, w0i, ai[3]);
-            }
-        } else {  // MU == 2: lower = (i S w0, -i S w1)
-            if constexpr (S > 0) {
-                ar[2] = pfma(pk, w0i, ar[2]); ai[2] = pfma(nk, w0r, ai[2]);
-                ar[3] = pfma(nk, w1i, ar[3]); ai[3] = pfma(pk, w1r, ai[3]);
-            } else {
-                ar[2] = pfma(nk, w0i, ar[2]); ai[2] = pfma(pk, w0r, ai[2]);
-                ar[3] = pfma(pk, w1i, ar[3]); ai[3] = pfma(nk, w1r, ai[3]);
-            }
-        }
-    }
-}
-
-template <int P, int MU, int S>
-__device__ __forceinline__ void hop_colour(const DPairArgs& a, int nb, int p, int c, int base,
-                                           const float4* __restrict__ link, float2 nk, float2 pk, float2 (&ar)[4],
-                                           float2 (&ai)[4]) {
-    float2 qr[4], qi[4];
-#pragma unroll
-    for (int sp = 0; sp < 4; ++sp) {
-        if (MU == 3 && ((S > 0) != (sp < 2))) {  // the t projector reads two spins
-            qr[sp] = make_float2(0.f, 0.f);
-            qi[sp] = make_float2(0.f, 0.f);
-            continue;
-        }
-        load_elem<P>(a.x, nb, 3 * sp + c, p, qr[sp], qi[sp]);
-    }
-    float2 h0r, h0i, h1r, h1i;
-    project_colour<MU, S>(qr, qi, h0r, h0i, h1r, h1i);
-    if constexpr (P == BK_FP16) {
-        const float2 sc = pair_scale<P>(a.x, nb, p);
-        h0r = pmul(h0r, sc);
-        h0i = pmul(h0i, sc);
-        h1r = pmul(h1r, sc);
-        h1i = pmul(h1i, sc);
-    }
-    // row c of U (forward) or column c of U^+ (backward) times all three colours
-    const float2* u2 = reinterpret_cast<const float2*>(link);
-    float2 w0r = make_float2(0.f, 0.f), w0i = w0r, w1r = w0r, w1i = w0r;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const float2 g0r = shfl2(h0r, base + j), g0i = shfl2(h0i, base + j);
-        const float2 g1r = shfl2(h1r, base + j), g1i = shfl2(h1i, base + j);
-        const int e = S > 0 ? 3 * j + c : 3 * c + j;
-        const float4 q = __ldg(link + e);
-        const float2 ur = make_float2(q.x, q.y), ui = make_float2(q.z, q.w), un = __ldg(u2 + 18 + e);
-        if constexpr (S < 0) {  // U_cj h_j
-            w0r = pfma(ur, g0r, w0r); w0r = pfma(un, g0i, w0r);
-            w0i = pfma(ur, g0i, w0i); w0i = pfma(ui, g0r, w0i);
-            w1r = pfma(ur, g1r, w1r); w1r = pfma(un, g1i, w1r);
-            w1i = pfma(ur, g1i, w1i); w1i = pfma(ui, g1r, w1i);
-        } else {  // conj(U_jc) h_j
-            w0r = pfma(ur, g0r, w0r); w0r = pfma(ui, g0i, w0r);
-            w0i = pfma(ur, g0i, w0i); w0i = pfma(un, g0r, w0i);
-            w1r = pfma(ur, g1r, w1r); w1r = pfma(ui, g1i, w1r);
-            w1i = pfma(ur, g1i, w1i); w1i = pfma(un, g1r, w1i);
-        }
-    }
-    reconstruct_colour<MU, S>(w0r, w0i, w1r, w1i, nk, pk, ar, ai);
-}
-
-template <int P, int MU>
-__device__ __forceinline__ void hop_dir_colour(const DPairArgs& a, const int (&co)[4], int n, int p, int c, int base,
-                                               float2 nk, float2 pk, float2 (&ar)[4], float2 (&ai)[4]) {
-    const int Lm = a.L[MU], sm = a.st[MU];
-    const int nf = co[MU] == Lm - 1 ? n - (Lm - 1) * sm : n + sm;
-    const int nb = co[MU] == 0 ? n + (Lm - 1) * sm : n - sm;
-    hop_colour<P, MU, -1>(a, nf, p, c, base, a.U + ((size_t)MU * a.V + n) * BK_LINK32_F4, nk, pk, ar, ai);
-    hop_colour<P, MU, +1>(a, nb, p, c, base, a.U + ((size_t)MU * a.V + nb) * BK_LINK32_F4, nk, pk, ar, ai);
-}
-
-__device__ __forceinline__ float2 sel3(int c, float2 a0, float2 a1, float2 a2) {
-    return c == 0 ? a0 : (c == 1 ? a1 : a2);
-}
-
-template <int P, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) k_dslash_pc(const __grid_constant__ DPairArgs a) {
-    const int lane = threadIdx.x & 31;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int slot = lane < 30 ? lane / 3 : 9;
-    const int c = lane < 30 ? lane - 3 * slot : lane - 30;
-    const int base = 3 * slot;  // lane of colour 0 of this slot
-    const long long total = (long long)a.V * a.npl;
-    long long sp = warp * 10 + slot;
-    const bool valid = lane < 30 && sp < total;
-    if (sp >= total) sp = total - 1;  // idle lanes repeat a valid slot (shuffle partners), store nothing
-    const int n = (int)(sp / a.npl);
-    const int pl = (int)(sp - (long long)n * a.npl);
-    const int p = a.p0 + pl;
-    int co[4];
-    {
-        int r = n;
-        co[0] = r % a.L[0];
-        r /= a.L[0];
-        co[1] = r % a.L[1];
-        r /= a.L[1];
-        co[2] = r % a.L[2];
-        co[3] = r / a.L[2];
-    }
-    const float2 nk = a.nk[pl];
-    const float2 pk = make_float2(-nk.x, -nk.y);
-    float2 ar[4], ai[4];
-    {   // out = x - kappa C x for the thread's colour; the chiral blocks act on u + l, u - l
-        float2 vr[2][6], vi[2][6];
-        {
-            float2 qr[12], qi[12];
-            load_pair<P>(a.x, n, p, qr, qi);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                vr[0][k] = padd(qr[k], qr[k + 6]);
-                vi[0][k] = padd(qi[k], qi[k + 6]);
-                vr[1][k] = psub(qr[k], qr[k + 6]);
-                vi[1][k] = psub(qi[k], qi[k + 6]);
-            }
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {  // acc = x for the thread's colour
-                ar[h] = h == 0 ? sel3(c, qr[0], qr[1], qr[2]) : sel3(c, qr[3], qr[4], qr[5]);
-                ai[h] = h == 0 ? sel3(c, qi[0], qi[1], qi[2]) : sel3(c, qi[3], qi[4], qi[5]);
-                ar[2 + h] = h == 0 ? sel3(c, qr[6], qr[7], qr[8]) : sel3(c, qr[9], qr[10], qr[11]);
-                ai[2 + h] = h == 0 ? sel3(c, qi[6], qi[7], qi[8]) : sel3(c, qi[9], qi[10], qi[11]);
-            }
-        }
-        const float4* c4 = a.C + (size_t)n * BK_CLOV32_F4;
-        const float2* c2 = reinterpret_cast<const float2*>(c4);
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const float2 sg = b == 0 ? nk : pk;  // block 1 enters the lower spins with a minus sign
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                asm volatile("" ::: "memory");
-                const int rr = 3 * h + c;
-                const float2 d = __ldg(c2 + 90 + 6 * b + rr);
-                const float2 vrr = h == 0 ? sel3(c, vr[b][0], vr[b][1], vr[b][2]) : sel3(c, vr[b][3], vr[b][4], vr[b][5]);
-                const float2 vir = h == 0 ? sel3(c, vi[b][0], vi[b][1], vi[b][2]) : sel3(c, vi[b][3], vi[b][4], vi[b][5]);
-                float2 sr = pmul(d, vrr), si = pmul(d, vir);
-#pragma unroll
-                for (int cc = 0; cc < 6; ++cc) {
-                    if (cc == rr) continue;
-                    const bool lower = rr > cc;  // stored entry (rr, cc); else (cc, rr), conjugated
-                    const int e = lower ? rr * (rr - 1) / 2 + cc : cc * (cc - 1) / 2 + rr;
-                    const float4 A = __ldg(c4 + 15 * b + e);
-                    const float2 AR = make_float2(A.x, A.y), AI = make_float2(A.z, A.w);
-                    const float2 NAI = __ldg(c2 + 60 + 15 * b + e);
-                    sr = pfma(AR, vr[b][cc], sr);
-                    sr = pfma(lower ? NAI : AI, vi[b][cc], sr);
-                    si = pfma(AR, vi[b][cc], si);
-                    si = pfma(lower ? AI : NAI, vr[b][cc], si);
-                }
-                // upper spins get -kappa (y0 + y1), lower spins -kappa (y0 - y1)
-                ar[h] = pfma(nk, sr, ar[h]);
-                ai[h] = pfma(nk, si, ai[h]);
-                ar[2 + h] = pfma(sg, sr, ar[2 + h]);
-                ai[2 + h] = pfma(sg, si, ai[2 + h]);
-            }
-        }
-    }
-    asm volatile("" ::: "memory");
-    // a compiler-level fence between directions keeps each direction's loads
-    // in its own stage: fewer registers, more resident warps
-    hop_dir_colour<P, 0>(a, co, n, p, c, base, nk, pk, ar, ai);
-    asm volatile("" ::: "memory");
-    hop_dir_colour<P, 1>(a, co, n, p, c, base, nk, pk, ar, ai);
-    asm volatile("" ::: "memory");
-    hop_dir_colour<P, 2>(a, co, n, p, c, base, nk, pk, ar, ai);
-    asm volatile("" ::: "memory");
-    hop_dir_colour<P, 3>(a, co, n, p, c, base, nk, pk, ar, ai);
-    if (a.residual) {  // b - D x
-        const float2 sc = pair_scale<P>(a.b, n, p);
-#pragma unroll
-        for (int sp2 = 0; sp2 < 4; ++sp2) {
-            float2 br, bi;
-            load_elem<P>(a.b, n, 3 * sp2 + c, p, br, bi);
-            if constexpr (P == BK_FP16) {
-                br = pmul(br, sc);
-                bi = pmul(bi, sc);
-            }
-            ar[sp2] = psub(br, ar[sp2]);
-            ai[sp2] = psub(bi, ai[sp2]);
-        }
-    }
-    if constexpr (P == BK_FP32) {
-        if (valid) {
-            float4* q = (float4*)a.y.data + ((size_t)n * 12 + c) * a.y.np + p;
-#pragma unroll
-            for (int sp2 = 0; sp2 < 4; ++sp2)
-                q[(size_t)3 * sp2 * a.y.np] = make_float4(ar[sp2].x, ar[sp2].y, ai[sp2].x, ai[sp2].y);
-        }
-    } else {
-        // FP16: the column's scale is the largest component over all colours
-        float ma = 0.f, mb = 0.f;
-#pragma unroll
-        for (int sp2 = 0; sp2 < 4; ++sp2) {
-            ma = fmaxf(ma, fmaxf(fabsf(ar[sp2].x), fabsf(ai[sp2].x)));
-            mb = fmaxf(mb, fmaxf(fabsf(ar[sp2].y), fabsf(ai[sp2].y)));
-        }
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const float oa = __shfl_sync(0xffffffffu, ma, base + j), ob = __shfl_sync(0xffffffffu, mb, base + j);
-            ma = fmaxf(ma, oa);
-            mb = fmaxf(mb, ob);
-        }
-        if (valid) {
-            const float2 inv = make_float2(ma > 0.f ? 1.0f / ma : 0.f, mb > 0.f ? 1.0f / mb : 0.f);
-            uint2* q = (uint2*)a.y.data + ((size_t)n * 12 + c) * a.y.np + p;
-#pragma unroll
-            for (int sp2 = 0; sp2 < 4; ++sp2) {
-                const float2 r = pmul(ar[sp2], inv), i = pmul(ai[sp2], inv);
-                __half2 hr = __floats2half2_rn(r.x, r.y), hi = __floats2half2_rn(i.x, i.y);
-                q[(size_t)3 * sp2 * a.y.np] =
-                    make_uint2(*reinterpret_cast<uint32_t*>(&hr), *reinterpret_cast<uint32_t*>(&hi));
-            }
-            if (c == 0) a.y.norm[(size_t)n * a.y.np + p] = make_float2(ma, mb);
-        }
-    }
 }
 
 // ================================================================= FP64 / double-float: one column per thread
@@ -880,33 +677,27 @@ bk_status dslash_pair_impl(const DslashOp& op, cudaStream_t st) {
             const double kb = (cb >= 0 && cb < op.ncol) ? op.kappa[cb] : 0.0;
             a.nk[j] = make_float2((float)-ka, (float)-kb);
         }
-        // variants 1-3: one thread per (site, pair), register cap 255 (1 block
-        // of 256), 170 (3 blocks of 128), 128 (4 blocks of 128); variants 4-6:
-        // colour-split, three threads per (site, pair), caps 128, 96, 80
+        // variants: register cap 255 (1: 1 block of 256), 170 (2: 3 blocks of
+        // 128), 128 (3: 4 blocks of 128)
         int threads = op.threads > 0 ? op.threads : 128;
-        if (op.variant >= 2 && op.variant <= 3 && threads > 128) threads = 128;
-        if (op.variant >= 4) {
-            threads = std::min(std::max(threads, 64), 256) / 32 * 32;
-            const long long warps = ((long long)op.V * npl + 9) / 10;
-            const unsigned blocks = (unsigned)((warps * 32 + threads - 1) / threads);
-            if (op.variant == 7)
-                k_dslash_pc<P, 256, 1><<<blocks, threads, 0, st>>>(a);
-            else if (op.variant == 4)
-                k_dslash_pc<P, 256, 2><<<blocks, threads, 0, st>>>(a);
-            else if (op.variant == 5)
-                k_dslash_pc<P, 256, 3><<<blocks, threads, 0, st>>>(a);
-            else
-                k_dslash_pc<P, 256, 4><<<blocks, threads, 0, st>>>(a);
+        if (op.variant >= 2 && threads > 128) threads = 128;
+        a.G = op.group > 0 ? std::min(op.group, npl) : npl;
+        const long long items = (long long)op.V * npl;
+        const unsigned blocks = (unsigned)((items + threads - 1) / threads);
+        // op.prefetch: 0 none, 1 into L2, 2 into L1 (see prefetch_hops)
+#define BK_DP(MT, MB)                                                                    \
+    if (op.prefetch == 1) k_dslash_pair<P, MT, MB, 1><<<blocks, threads, 0, st>>>(a);    \
+    else if (op.prefetch == 2) k_dslash_pair<P, MT, MB, 2><<<blocks, threads, 0, st>>>(a); \
+    else if (op.prefetch == 3) k_dslash_pair<P, MT, MB, 3><<<blocks, threads, 0, st>>>(a); \
+    else k_dslash_pair<P, MT, MB, 0><<<blocks, threads, 0, st>>>(a);
+        if (op.variant == 1) {
+            BK_DP(256, 1)
+        } else if (op.variant == 3) {
+            BK_DP(128, 4)
         } else {
-            const long long items = (long long)op.V * npl;
-            const unsigned blocks = (unsigned)((items + threads - 1) / threads);
-            if (op.variant == 1)
-                k_dslash_pair<P, 256, 1><<<blocks, threads, 0, st>>>(a);
-            else if (op.variant == 3)
-                k_dslash_pair<P, 128, 4><<<blocks, threads, 0, st>>>(a);
-            else
-                k_dslash_pair<P, 128, 3><<<blocks, threads, 0, st>>>(a);
+            BK_DP(128, 3)
         }
+#undef BK_DP
         BK_CUDA_TRY(cudaGetLastError());
     }
     return BK_OK;

@@ -1,22 +1,31 @@
-"""The paper's experiment shape (Section 4, Tables 2 and 3, Figure 1) on
+"""The paper's experiment shape (Section 4, Tables 2 and 3, Figures 1 and 2) on
 synthetic gauge fields: L dependence of block BiCGSTAB and block BiCGGR.
 
-    python -m paper_0903_4936_gb300.experiments [--dims 16 16 16 32] [--seeds 1003 1013 1023]
+    python -m paper_0903_4936_gb300.experiments [--dims 16 16 16 32] [--seeds 1003 1013]
+        [--kappas ...] [--scan] [--json out.json] [--markdown]
 
 For every kappa, method and block size L, the 12 point sources at the origin
 are split into 12 / L blocks of L columns, each block a system of its own (the
 paper solves them one after another; here they run in one batched FP64 call,
 so "time" is the call's wall time for all 12 sources).  The stopping rule is
 the paper's: recursive relative residual <= tol (1e-14 in the paper), after
-which the true residual max_i ||A x_i - b_i|| / ||b_i|| is evaluated.  Printed
-per row, averaged over the gauge seeds: iterations (mean over blocks),
-time, time per source, and the max / min true residual over seeds and blocks,
-as in the paper's tables; a block that does not reach tol within maxiter is
-counted in the "failed" column.
+which the true residual max_i ||A x_i - b_i|| / ||b_i|| is evaluated.  Per
+row, averaged over the gauge seeds: iterations (mean over blocks), time, time
+per source, and the max / min true residual over seeds and blocks, as in the
+paper's tables; a block that does not reach tol within maxiter is counted in
+the "failed" column.
+
+--scan first raises kappa on the first seed until the single-source solve
+needs about 1000 iterations (the paper's light quarks: 1519 to 2440
+iterations at kappa 0.1355 to 0.1359 on its Iwasaki configurations), and runs
+the grid at three kappas approaching that point.  --json writes the scan, the
+grid and the residual histories of the first seed at the lightest kappa (the
+paper's Figure 2) to a file; --markdown prints the grid as a table.
 """
 from __future__ import annotations
 
 import argparse
+import json
 import os
 import sys
 import time
@@ -29,23 +38,50 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def block_size_scan(dims, kappas, Ls, methods, seeds, tol=1e-14, eps=0.5, csw=1.0, maxiter=1000):
-    """Rows of (kappa, method, L, mean iterations, mean seconds, seconds per
-    source, max true residual, min true residual, failed blocks)."""
+def _lattice(dims, eps, seed, csw):
     import synth
 
     import paper_0903_4936_gb300 as bk
+    lat = bk.Lattice(dims)
+    lat.upload_gauge(synth.random_su3_field(dims, eps, seed))
+    lat.build_clover(csw)
+    return lat
+
+
+def kappa_scan(dims, seed, kappas, eps=0.5, csw=1.0, target=1000, maxiter=4000):
+    """Iterations of the FP64 single-source solve (point source, column 0) as
+    kappa rises; stops after the first kappa that needs more than `target`
+    iterations or does not converge."""
+    import synth
+    lat = _lattice(dims, eps, seed, csw)
+    B = torch.from_numpy(synth.point_sources(dims)[:1].copy()).cuda()
+    out = []
+    for k in kappas:
+        X, info = lat.block_solve(B, k, method="bicgstab", prec="fp64", tol=1e-14, maxiter=maxiter,
+                                  raise_on_fail=False)
+        out.append(dict(kappa=k, iterations=info["iterations"], converged=bool(info["converged"]),
+                        true_res=info["true_res_max"]))
+        if info["iterations"] > target or not info["converged"]:
+            break
+    return out
+
+
+def block_size_scan(dims, kappas, Ls, methods, seeds, tol=1e-14, eps=0.5, csw=1.0, maxiter=6000,
+                    history_seed=None, history_kappa=None):
+    """Rows of (kappa, method, L, mean iterations, mean seconds, seconds per
+    source, max true residual, min true residual, failed blocks), and the
+    residual histories (first block) of history_seed at history_kappa."""
+    import synth
 
     B = torch.from_numpy(synth.point_sources(dims)).cuda()
-    acc = {}
+    acc, hist = {}, {}
     for seed in seeds:
-        lat = bk.Lattice(dims)
-        lat.upload_gauge(synth.random_su3_field(dims, eps, seed))
-        lat.build_clover(csw)
+        lat = _lattice(dims, eps, seed, csw)
         for kappa in kappas:
             for method in methods:
                 for L in Ls:
                     Ls_sys = [L] * (12 // L)
+                    want_hist = seed == history_seed and kappa == history_kappa
                     # warm-up of the operator's launch shapes for this column count
                     lat.block_solve_batched(B, [kappa] * len(Ls_sys), Ls_sys, method=method, prec="fp64",
                                             tol=1e-4, maxiter=50, raise_on_fail=False)
@@ -53,19 +89,33 @@ def block_size_scan(dims, kappas, Ls, methods, seeds, tol=1e-14, eps=0.5, csw=1.
                     t0 = time.perf_counter()
                     X, infos = lat.block_solve_batched(B, [kappa] * len(Ls_sys), Ls_sys, method=method,
                                                        prec="fp64", tol=tol, maxiter=maxiter,
-                                                       raise_on_fail=False)
+                                                       raise_on_fail=False, history=want_hist)
                     torch.cuda.synchronize()
                     dt = time.perf_counter() - t0
                     a = acc.setdefault((kappa, method, L), dict(it=[], t=[], tr=[], fail=0))
-                    a["it"].append(np.mean([i["iterations"] for i in infos]))
+                    a["it"].append(float(np.mean([i["iterations"] for i in infos])))
                     a["t"].append(dt)
                     a["tr"] += [i["true_res_max"] for i in infos]
                     a["fail"] += sum(1 for i in infos if not i["converged"])
+                    if want_hist:
+                        hist[f"{method}_L{L}"] = infos[0]["history"]
     rows = []
     for (kappa, method, L), a in acc.items():
         t = float(np.mean(a["t"]))
-        rows.append((kappa, method, L, float(np.mean(a["it"])), t, t / 12.0, max(a["tr"]), min(a["tr"]), a["fail"]))
-    return rows
+        rows.append(dict(kappa=kappa, method=method, L=L, iterations=float(np.mean(a["it"])), time_s=t,
+                         time_per_source_s=t / 12.0, true_res_max=max(a["tr"]), true_res_min=min(a["tr"]),
+                         failed=a["fail"]))
+    return rows, hist
+
+
+def markdown(rows):
+    lines = ["| kappa | method | L | iterations | time [s] | time/source [s] | true res max | true res min | failed |",
+             "|---|---|---|---|---|---|---|---|---|"]
+    for r in rows:
+        lines.append(f"| {r['kappa']:.4f} | {r['method']} | {r['L']} | {r['iterations']:.1f} | {r['time_s']:.3f} | "
+                     f"{r['time_per_source_s']:.4f} | {r['true_res_max']:.2e} | {r['true_res_min']:.2e} | "
+                     f"{r['failed']} |")
+    return "\n".join(lines)
 
 
 def main(argv=None) -> None:
@@ -76,13 +126,42 @@ def main(argv=None) -> None:
     ap.add_argument("--methods", nargs="+", default=["bicgstab", "bicggr"])
     ap.add_argument("--seeds", type=int, nargs="+", default=[1003, 1013, 1023])
     ap.add_argument("--tol", type=float, default=1e-14)
+    ap.add_argument("--scan", action="store_true")
+    ap.add_argument("--json")
+    ap.add_argument("--markdown", action="store_true")
     args = ap.parse_args(argv)
-    rows = block_size_scan(tuple(args.dims), args.kappas, args.L, args.methods, args.seeds, args.tol)
-    print(f"| kappa | method | L | iterations | time [s] | time/source [s] | true res max | true res min | failed |")
-    print("|---|---|---|---|---|---|---|---|---|")
-    for r in rows:
-        print(f"| {r[0]:.3f} | {r[1]} | {r[2]} | {r[3]:.1f} | {r[4]:.3f} | {r[5]:.4f} | {r[6]:.2e} | {r[7]:.2e} | {r[8]} |",
-              flush=True)
+    dims = tuple(args.dims)
+    result = dict(dims=list(dims), eps=0.5, csw=1.0, tol=args.tol, seeds=args.seeds,
+                  sources="the 12 point sources at the origin, split into 12/L blocks of L columns",
+                  precision="FP64 (the paper's method)")
+    kappas = args.kappas
+    if args.scan:
+        scan = kappa_scan(dims, args.seeds[0], [round(0.130 + 0.005 * i, 4) for i in range(9)])
+        result["scan"] = scan
+        print(json.dumps(dict(scan=scan)), flush=True)
+        # the last converged kappa below ~1000 iterations and the first beyond:
+        # refine between them and take three kappas approaching the light point
+        conv = [s for s in scan if s["converged"]]
+        lo = conv[-1]["kappa"] if conv else 0.130
+        hi = scan[-1]["kappa"] if scan and (scan[-1]["iterations"] > 1000 or not scan[-1]["converged"]) else lo
+        fine = kappa_scan(dims, args.seeds[0], [round(lo + (hi - lo) * f, 5) for f in (0.25, 0.5, 0.75)]) \
+            if hi > lo else []
+        result["scan_fine"] = fine
+        print(json.dumps(dict(scan_fine=fine)), flush=True)
+        pts = [s for s in scan + fine if s["converged"]]
+        pts.sort(key=lambda s: s["kappa"])
+        light = [s["kappa"] for s in pts if s["iterations"] <= 3000][-3:]
+        kappas = light
+    rows, hist = block_size_scan(dims, kappas, args.L, args.methods, args.seeds, args.tol,
+                                 history_seed=args.seeds[0], history_kappa=max(kappas))
+    result["kappas"] = kappas
+    result["grid"] = rows
+    result["histories"] = dict(kappa=max(kappas), seed=args.seeds[0], by_method_L=hist)
+    if args.json:
+        with open(args.json, "w") as f:
+            json.dump(result, f, indent=1)
+    if args.markdown or not args.json:
+        print(markdown(rows), flush=True)
 
 
 if __name__ == "__main__":

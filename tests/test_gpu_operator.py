@@ -174,16 +174,22 @@ def test_df64_operator_tracks_fp64_where_fp32_cannot():
     assert np.linalg.norm(r32 - r64) > 10 * np.linalg.norm(r64)
 
 
-@pytest.mark.parametrize("variant", ["1", "2", "3", "4", "5", "6", "7"])
+@pytest.mark.parametrize("variant", ["1", "2", "3", "1:1", "2:2", "2:3", "3:3"])
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
-@pytest.mark.parametrize("dims,L", [((4, 4, 4, 4), 12), ((2, 4, 2, 6), 5), ((3, 5, 4, 6), 1), ((8, 8, 8, 16), 13)])
+@pytest.mark.parametrize("dims,L", [((4, 4, 4, 4), 12), ((2, 4, 2, 6), 5), ((3, 5, 4, 6), 1), ((8, 8, 8, 16), 13),
+                                    ((4, 4, 4, 8), 21)])
 def test_dslash_every_launch_variant(monkeypatch, variant, prec, dims, L):
     """Each register-cap variant of the packed-pair operator the autotuner may
-    pick (forced with BK_DSLASH_VARIANT) against the oracle; odd L leaves a
-    padding column in the last pair.  On 4^4 the variant is also the inner
-    operator of a mixed-precision solve."""
+    pick, with and without the L2 / L1 prefetch of its rows and in its looped
+    form (forced with
+    BK_DSLASH_VARIANT / BK_DSLASH_PREFETCH, pair groups of 8: L = 21 runs a full
+    group of 8 pairs and a short one of 3) against the oracle; odd L leaves a
+    padding column in the last pair.  On 4^4 the variant is also the inner operator of
+    a mixed-precision solve."""
     import paper_0903_4936_gb300 as bk
-    monkeypatch.setenv("BK_DSLASH_VARIANT", variant)
+    v, _, pf = variant.partition(":")
+    monkeypatch.setenv("BK_DSLASH_VARIANT", v)
+    monkeypatch.setenv("BK_DSLASH_PREFETCH", pf or "0")
     lat, U = _lat(dims, 0.5, 300 + L)
     X = synth.gaussian_sources(dims, L, 8)
     kappa = [0.115 + 0.001 * j for j in range(L)]
