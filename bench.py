@@ -355,6 +355,8 @@ def gb300_arm(args, wl, rank, world, local_rank):
         c0 += L
     sysl = systems(wl)
     kap_s, L_s, owner = [s[0] for s in sysl], [s[1] for s in sysl], [s[2] for s in sysl]
+    update = args.update or wl.get("update", "fp64")
+    delta = args.delta if args.delta is not None else wl.get("delta", 0.0)
     Xdev = torch.empty_like(Ball)
     Bh = Ball.cpu().pin_memory()
     Xh = torch.empty_like(Bh).pin_memory()
@@ -362,8 +364,8 @@ def gb300_arm(args, wl, rank, world, local_rank):
 
     def solve(B, X, record, prec=None, method=None):
         return lat.block_solve_batched(B, kap_s, L_s, method=method or wl["method"], prec=prec or wl["prec"],
-                                       tol=TOL, maxiter=MAXITER, timing=record, delta=wl.get("delta", 0.0),
-                                       out=X, raise_on_fail=False)
+                                       tol=TOL, maxiter=MAXITER, timing=record, delta=delta,
+                                       out=X, raise_on_fail=False, update=update)
 
     def check(infos, what):
         for si, info in enumerate(infos):
@@ -509,6 +511,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-full", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--delta", type=float, default=None,
+                    help="residual-replacement threshold (default: the workload's)")
+    ap.add_argument("--update", choices=["fp64", "df64"], default=None,
+                    help="arithmetic of the residual replacements (default: the workload's)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))

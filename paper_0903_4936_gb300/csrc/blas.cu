@@ -60,7 +60,7 @@ struct PTiles {
     int np[BK_MAX_SYS];
 };
 
-PTiles make_ptiles(const SysPart& p) {
+PTiles make_ptiles(const SysPart& p, int maxp = TILE_MAXP) {
     PTiles t;
     t.n = 0;
     bool open = false;
@@ -70,7 +70,7 @@ PTiles make_ptiles(const SysPart& p) {
             open = false;
             continue;
         }
-        if (open && t.np[t.n - 1] + nq <= TILE_MAXP) {
+        if (open && t.np[t.n - 1] + nq <= maxp) {
             t.np[t.n - 1] += nq;
         } else {
             t.p0[t.n] = q0;
@@ -86,10 +86,6 @@ PTiles make_ptiles(const SysPart& p) {
 // tiles so that per-chunk partial sums have a fixed row count for a lattice.
 constexpr int MAX_CHUNKS = 304;  // 2 per SM of 152
 inline int site_chunks(int V) { return std::max(1, std::min(MAX_CHUNKS, V / 64)); }
-
-// site rows of a thread block: 4 (FP32 / FP16 arithmetic) or 2 (FP64)
-template <int P>
-constexpr int srows() { return P == BK_FP64 ? 2 : 4; }
 
 // element store (FP32 / FP64 pair layouts)
 template <int P>
@@ -110,142 +106,197 @@ struct CxPair {  // one spinor component of a column pair, arithmetic type
     R2 re, im;
 };
 
-__device__ __forceinline__ double2 warp_sum2(double2 v, int width) {
-    for (int o = 1; o < width; o <<= 1) {
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+// ---------------------------------------------------------------- warp tiles
+//
+// The small-system kernels (systems of at most 12 columns, so at most 6
+// pairs) give every warp a run of whole active systems of at most 32 pairs,
+// one pair per lane, and let the warps of a block take different sites.  A
+// lane loads only its own pair of each operand (a warp reads contiguous
+// 16-byte elements, and no element is read twice); the pairs of the other
+// columns of its system come from the lanes that hold them by register
+// shuffles.  No shared-memory round trip, no barrier, no dependence between
+// the warps inside the site loop.
+constexpr int WT_PAIRS = 32;
+
+struct WLane {
+    bool live;  // the lane holds a pair of an active system
+    int q, s, qs, Ls, i0, nps, base;  // pair, system, its first pair, size, first column, pairs, first lane
+};
+
+__device__ __forceinline__ WLane wlane(const SysPart& p, int tp0, int tnp, int lane) {
+    WLane w;
+    w.live = lane < tnp;
+    if (w.live) {
+        w.q = tp0 + lane;
+        w.s = sys_of_pair(p, w.q);
+        w.qs = p.col0[w.s] / 2;
+        w.Ls = p.L[w.s];
+        w.i0 = 2 * w.q - p.col0[w.s];
+        w.nps = (w.Ls + 1) / 2;
+        w.base = lane - (w.q - w.qs);
+    } else {
+        w.q = tp0;
+        w.s = 0;
+        w.qs = tp0;
+        w.Ls = 0;
+        w.i0 = 0;
+        w.nps = 1;
+        w.base = lane;
+    }
+    return w;
+}
+
+template <typename R2>
+__device__ __forceinline__ CxPair<R2> shfl_pair(const CxPair<R2>& v, int src) {
+    CxPair<R2> o;
+    o.re.x = __shfl_sync(0xffffffffu, v.re.x, src);
+    o.re.y = __shfl_sync(0xffffffffu, v.re.y, src);
+    o.im.x = __shfl_sync(0xffffffffu, v.im.x, src);
+    o.im.y = __shfl_sync(0xffffffffu, v.im.y, src);
+    return o;
+}
+
+// Element (n, k, p) through the read-only data path, FP16 scale applied.
+// Only for operands that no thread of the kernel writes, or that the reading
+// thread alone writes after its one read.
+template <int P>
+__device__ __forceinline__ CxPair<typename Prec<P>::pair> ldg_elem(const Field& f, int n, int k, int p,
+                                                                    typename Prec<P>::pair sc) {
+    CxPair<typename Prec<P>::pair> v;
+    const size_t e = ((size_t)n * 12 + k) * f.np + p;
+    if constexpr (P == BK_FP64) {
+        const double2* q = (const double2*)f.data + 2 * e;
+        v.re = __ldg(q);
+        v.im = __ldg(q + 1);
+    } else if constexpr (P == BK_FP32) {
+        const float4 q = __ldg((const float4*)f.data + e);
+        v.re = make_float2(q.x, q.y);
+        v.im = make_float2(q.z, q.w);
+    } else {
+        const uint2 q = __ldg((const uint2*)f.data + e);
+        v.re = pmul(__half22float2(*reinterpret_cast<const __half2*>(&q.x)), sc);
+        v.im = pmul(__half22float2(*reinterpret_cast<const __half2*>(&q.y)), sc);
     }
     return v;
 }
 
+__device__ __forceinline__ float2 bcast(float v) { return make_float2(v, v); }
+__device__ __forceinline__ double2 bcast(double v) { return make_double2(v, v); }
+
 // ---------------------------------------------------------------- Gram, small systems
 //
 // G_s = A_s^H B_s (and G2_s = A_s^H B2_s with NB = 2) for systems of at most
-// MAXL columns.  Thread block: 64 pair slots (fastest, so a warp reads one
-// contiguous row) x SR site rows over a tile of whole systems; grid: (tiles,
-// site chunks).  Each thread owns its pair's two columns i and adds
-// conj(A_i) B_j for every column j of its system, reading the partner pairs
-// of B straight from memory (the threads of one system share them through
-// L1): no barrier inside the site loop, so the loads of successive sites
-// overlap.  FP32 / FP16 products are summed in FP32 registers and moved
-// every GS_FLUSH sites into per-pair FP64 accumulators in shared memory
-// (shared atomics), which also combine the SR site rows; chunks are combined
-// in FP64 by the finishing kernel (fixed order).
+// MAXL columns over warp tiles; grid: (warp tiles, site chunks), GW_WARPS
+// warps per block on different sites.  A lane adds conj(A_i) B_j for its two
+// columns i and every column j of its system, the pairs of B shuffled in
+// from their lanes.  FP32 / FP16 products are summed in FP32 registers
+// (packed pairs over j) and moved every GS_FLUSH sites into the lane's own
+// FP64 accumulators in shared memory; the warps' accumulators are added at
+// the end and the site chunks in FP64 by the finishing kernel (fixed order).
 
 constexpr int GS_FLUSH = 8;
+constexpr int GW_WARPS = 8;
 
 template <int P, int NB, int MAXL>
-__global__ void __launch_bounds__(256) k_gram_small(Field A, Field B0, Field B1, SysPart p, PTiles tl,
-                                                    double2* __restrict__ partial, int V, int nchunk) {
+__global__ void __launch_bounds__(GW_WARPS * 32) k_gram_w(Field A, Field B0, Field B1, SysPart p, PTiles wt,
+                                                          double2* __restrict__ partial, int V, int nchunk) {
     using R = typename Prec<P>::real;
     using R2 = typename Prec<P>::pair;
-    constexpr int SR = srows<P>();
     constexpr int FL = P == BK_FP64 ? (1 << 30) : GS_FLUSH;
-    // per site row: no two threads share an entry (dynamic: up to 96 KB)
-    extern __shared__ double2 gs_acc[];
-    constexpr int ACC_ROW = TILE_MAXP * NB * 2 * MAXL;
-    double2(*Acc)[ACC_ROW] = reinterpret_cast<double2(*)[ACC_ROW]>(gs_acc);
-    const int t = threadIdx.x, r = threadIdx.y;
-    const int tid = r * TILE_MAXP + t;
-    const int tile = blockIdx.x, chunk = blockIdx.y;
-    const int tp0 = tl.p0[tile], tnp = tl.np[tile];
-    const bool on = t < tnp;
-    const int q = tp0 + t;
-    int s = 0, qs = 0, Ls = 0, i0 = 0;
-    if (on) {
-        s = sys_of_pair(p, q);
-        qs = p.col0[s] / 2;
-        Ls = p.L[s];
-        i0 = 2 * q - p.col0[s];
-    }
-    const int nps = (Ls + 1) / 2;
-    for (int e = t; e < TILE_MAXP * NB * 2 * MAXL; e += TILE_MAXP) Acc[r][e] = make_double2(0.0, 0.0);
-    cx<R> acc[NB][2][MAXL];
+    constexpr int NACC = NB * 2 * MAXL;
+    // [warp][entry][lane]: every lane its own entries, no two threads share one
+    extern __shared__ double2 gw_acc[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int chunk = blockIdx.y;
+    const WLane L = wlane(p, wt.p0[blockIdx.x], wt.np[blockIdx.x], lane);
+    double2* my = gw_acc + (size_t)w * NACC * 32 + lane;
+#pragma unroll
+    for (int e = 0; e < NACC; ++e) my[e * 32] = make_double2(0.0, 0.0);
+    CxPair<R2> acc[NB][2][MAXL / 2];
 #pragma unroll
     for (int b = 0; b < NB; ++b)
 #pragma unroll
         for (int ii = 0; ii < 2; ++ii)
 #pragma unroll
-            for (int j = 0; j < MAXL; ++j) acc[b][ii][j] = mk(R(0), R(0));
-    const int iters = (V + SR * nchunk - 1) / (SR * nchunk);
+            for (int jp = 0; jp < MAXL / 2; ++jp) acc[b][ii][jp].re = acc[b][ii][jp].im = pzero<R2>();
+    const int iters = (V + GW_WARPS * nchunk - 1) / (GW_WARPS * nchunk);
     for (int it = 0; it < iters; ++it) {
-        const int n = (it * nchunk + chunk) * SR + r;
-        if (on && n < V) {
-            const R2 sa = pair_scale<P>(A, n, q);
-            R2 sb[NB][MAXL / 2];
+        const int n = (it * nchunk + chunk) * GW_WARPS + w;
+        if (n < V) {  // the same for the whole warp
+            R2 sa = pzero<R2>(), sb[NB];
+            if (L.live) sa = pair_scale<P>(A, n, L.q);
 #pragma unroll
-            for (int b = 0; b < NB; ++b)
-#pragma unroll
-                for (int jp = 0; jp < MAXL / 2; ++jp)
-                    if (jp < nps) sb[b][jp] = pair_scale<P>(b == 0 ? B0 : B1, n, qs + jp);
+            for (int b = 0; b < NB; ++b) sb[b] = L.live ? pair_scale<P>(b == 0 ? B0 : B1, n, L.q) : pzero<R2>();
 #pragma unroll 2
             for (int k = 0; k < 12; ++k) {
-                R2 ar, ai;
-                load_elem<P>(A, n, k, q, ar, ai);
-                if constexpr (P == BK_FP16) {
-                    ar = pmul(ar, sa);
-                    ai = pmul(ai, sa);
+                CxPair<R2> a, bv[NB];
+                a.re = a.im = pzero<R2>();
+#pragma unroll
+                for (int b = 0; b < NB; ++b) bv[b].re = bv[b].im = pzero<R2>();
+                if (L.live) {
+                    a = ldg_elem<P>(A, n, k, L.q, sa);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) bv[b] = ldg_elem<P>(b == 0 ? B0 : B1, n, k, L.q, sb[b]);
                 }
 #pragma unroll
-                for (int jp = 0; jp < MAXL / 2; ++jp) {
-                    if (jp < nps) {
+                for (int b = 0; b < NB; ++b)
 #pragma unroll
-                        for (int b = 0; b < NB; ++b) {
-                            R2 br, bi;
-                            load_elem<P>(b == 0 ? B0 : B1, n, k, qs + jp, br, bi);
-                            if constexpr (P == BK_FP16) {
-                                br = pmul(br, sb[b][jp]);
-                                bi = pmul(bi, sb[b][jp]);
-                            }
+                    for (int jp = 0; jp < MAXL / 2; ++jp) {
+                        const CxPair<R2> bp = shfl_pair(bv[b], L.base + min(jp, L.nps - 1));
+                        if (jp < L.nps) {
 #pragma unroll
                             for (int ii = 0; ii < 2; ++ii) {
-                                const R xr = ii ? ar.y : ar.x, xi = ii ? ai.y : ai.x;
-#pragma unroll
-                                for (int jj = 0; jj < 2; ++jj) {
-                                    const R yr = jj ? br.y : br.x, yi = jj ? bi.y : bi.x;
-                                    cx<R>& c = acc[b][ii][2 * jp + jj];
-                                    c.r = fma(xr, yr, c.r);
-                                    c.r = fma(xi, yi, c.r);
-                                    c.i = fma(xr, yi, c.i);
-                                    c.i = fma(-xi, yr, c.i);
-                                }
+                                const R2 ar = bcast(ii ? a.re.y : a.re.x);
+                                const R2 ai = bcast(ii ? a.im.y : a.im.x);
+                                const R2 nai = bcast(ii ? -a.im.y : -a.im.x);
+                                CxPair<R2>& c = acc[b][ii][jp];
+                                c.re = pfma(ar, bp.re, c.re);
+                                c.re = pfma(ai, bp.im, c.re);
+                                c.im = pfma(ar, bp.im, c.im);
+                                c.im = pfma(nai, bp.re, c.im);
                             }
                         }
                     }
-                }
             }
         }
-        if (on && ((it % FL) == FL - 1 || it == iters - 1)) {
-            double2* my = Acc[r] + t * NB * 2 * MAXL;  // this thread's own entries
+        if ((it % FL) == FL - 1 || it == iters - 1) {
 #pragma unroll
             for (int b = 0; b < NB; ++b)
 #pragma unroll
                 for (int ii = 0; ii < 2; ++ii)
 #pragma unroll
-                    for (int j = 0; j < MAXL; ++j) {
-                        double2 v = my[(b * 2 + ii) * MAXL + j];
-                        v.x += (double)acc[b][ii][j].r;
-                        v.y += (double)acc[b][ii][j].i;
-                        my[(b * 2 + ii) * MAXL + j] = v;
-                        acc[b][ii][j] = mk(R(0), R(0));
-                    }
+                    for (int jp = 0; jp < MAXL / 2; ++jp)
+#pragma unroll
+                        for (int jj = 0; jj < 2; ++jj) {
+                            double2& v = my[((b * 2 + ii) * MAXL + 2 * jp + jj) * 32];
+                            CxPair<R2>& c = acc[b][ii][jp];
+                            v.x += (double)(jj ? c.re.y : c.re.x);
+                            v.y += (double)(jj ? c.im.y : c.im.x);
+                        }
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+                    for (int jp = 0; jp < MAXL / 2; ++jp) acc[b][ii][jp].re = acc[b][ii][jp].im = pzero<R2>();
         }
     }
     __syncthreads();
-    if (!on || r != 0) return;
+    if (w != 0 || !L.live) return;
     const int ne = p.coef_off[p.nsys];
     for (int b = 0; b < NB; ++b)
-        for (int ii = 0; ii < 2; ++ii)
-            for (int j = 0; j < Ls; ++j)
-                if (i0 + ii < Ls) {
-                    double2 v = make_double2(0.0, 0.0);
-                    for (int rr = 0; rr < SR; ++rr) {
-                        const double2 a = Acc[rr][t * NB * 2 * MAXL + (b * 2 + ii) * MAXL + j];
-                        v.x += a.x;
-                        v.y += a.y;
-                    }
-                    partial[(size_t)(b * nchunk + chunk) * ne + p.coef_off[s] + (i0 + ii) * Ls + j] = v;
+        for (int ii = 0; ii < 2; ++ii) {
+            if (L.i0 + ii >= L.Ls) continue;
+            for (int j = 0; j < L.Ls; ++j) {
+                double2 v = make_double2(0.0, 0.0);
+                for (int ww = 0; ww < GW_WARPS; ++ww) {
+                    const double2 a = gw_acc[((size_t)ww * NACC + (b * 2 + ii) * MAXL + j) * 32 + lane];
+                    v.x += a.x;
+                    v.y += a.y;
                 }
+                partial[(size_t)(b * nchunk + chunk) * ne + p.coef_off[L.s] + (L.i0 + ii) * L.Ls + j] = v;
+            }
+        }
 }
 
 // ---------------------------------------------------------------- Gram, any system size
@@ -486,12 +537,14 @@ __global__ void k_coldot_finish(const double2* __restrict__ partial, int nchunk,
 //   X_j      += xa Xin_j + xm matpart_j          (X in FP64 for FP64 blocks, else FP32)
 // coefficient value = mult * (ptr ? ptr[s] : 1), ptr complex FP64 per system.
 //
-// Thread block: SR site rows x 64 pair slots over a tile of whole systems;
-// grid: (tiles, site chunks).  Each thread forms comb for its pair and puts
-// it in shared memory; after a barrier it combines the comb columns of its
-// system with its two columns of M (read through L1) and writes its pair of
-// Y and X.  Optionally the squared norms of the Y columns are summed per
-// chunk (the residual norms of the stopping rule come with the R update).
+// Systems of at most 12 columns run in k_genop_w (warp tiles, below);
+// larger ones in k_genop: SR site rows x 64 pair slots over a tile of whole
+// systems, grid (tiles, site chunks).  Each thread forms the comb columns of
+// its system pair by pair (the system's threads share the reads through L1)
+// and combines them with its two columns of M, read through the read-only
+// path, then writes its pair of Y and X.  Optionally the squared norms of
+// the Y columns are summed per chunk (the residual norms of the stopping
+// rule come with the R update).
 
 template <int P>
 __device__ __forceinline__ cx<typename Prec<P>::real> coef(const double* ptr, double mult, int s) {
@@ -529,7 +582,7 @@ __device__ __forceinline__ CxPair<typename Prec<P>::pair> load_scaled(const Fiel
     return v;
 }
 
-template <int P, int MAXL>
+template <int P, int SR>
 __global__ void __launch_bounds__(256) k_genop(const __grid_constant__ GenOp g, PTiles tl, int V, int nchunk,
                                                int ncols) {
     using R = typename Prec<P>::real;
@@ -537,7 +590,6 @@ __global__ void __launch_bounds__(256) k_genop(const __grid_constant__ GenOp g, 
     constexpr int XP = P == BK_FP64 ? BK_FP64 : BK_FP32;
     using XR = typename Prec<XP>::real;
     using X2 = typename Prec<XP>::pair;
-    constexpr int SR = srows<P>();
     __shared__ double2 ynred[SR][TILE_MAXP];
     const int t = threadIdx.x, r = threadIdx.y;
     const int tile = blockIdx.x, chunk = blockIdx.y;
@@ -562,22 +614,6 @@ __global__ void __launch_bounds__(256) k_genop(const __grid_constant__ GenOp g, 
     if (g.hasX) xa = coef<P>(g.xa, g.xa_mult, s);
     const double2* M = reinterpret_cast<const double2*>(g.M) + (on && mat ? g.p.coef_off[s] : 0);
     const bool j1ok = i0 + 1 < Ls;
-    // the thread's two columns of M (small systems: in registers)
-    R2 Mr[MAXL > 0 ? MAXL : 1], Mi[MAXL > 0 ? MAXL : 1];
-    if constexpr (MAXL > 0) {
-#pragma unroll
-        for (int i = 0; i < MAXL; ++i) {
-            double2 m0 = make_double2(0.0, 0.0), m1 = make_double2(0.0, 0.0);
-            if (on && mat && i < Ls) {
-                m0 = M[i * Ls + i0];
-                if (j1ok) m1 = M[i * Ls + i0 + 1];
-            }
-            Mr[i].x = (R)m0.x;
-            Mr[i].y = (R)m1.x;
-            Mi[i].x = (R)m0.y;
-            Mi[i].y = (R)m1.y;
-        }
-    }
     R2 ym2;
     ym2.x = (R)g.ym;
     ym2.y = (R)g.ym;
@@ -631,17 +667,7 @@ __global__ void __launch_bounds__(256) k_genop(const __grid_constant__ GenOp g, 
                         mp.im = pfma(cii, mr2[h], mp.im);
                     }
                 };
-                if constexpr (MAXL > 0) {
-#pragma unroll
-                    for (int ip = 0; ip < MAXL / 2; ++ip) {
-                        if (ip < nps) {
-                            // an odd system's padding column has M rows of zero
-                            const R2 mr2[2] = {Mr[2 * ip], Mr[2 * ip + 1]};
-                            const R2 mi2[2] = {Mi[2 * ip], Mi[2 * ip + 1]};
-                            accumulate(ip, mr2, mi2);
-                        }
-                    }
-                } else {
+                {
                     for (int ip = 0; ip < nps; ++ip) {
                         R2 mr2[2], mi2[2];
 #pragma unroll
@@ -715,6 +741,237 @@ __global__ void __launch_bounds__(256) k_genop(const __grid_constant__ GenOp g, 
             }
             g.ynorm[(size_t)chunk * ncols + 2 * q] = v.x;
             g.ynorm[(size_t)chunk * ncols + 2 * q + 1] = v.y;
+        }
+    }
+}
+
+// Update kernel over warp tiles (systems of at most MAXL <= 12 columns).
+// Each lane forms comb = sum_u ma_u Mi_u for its own pair, takes the comb
+// pairs of its system's other lanes by shuffles and combines them with its
+// two columns of M (registers), then adds the elementwise terms and writes
+// its pair of Y and X.  The loads of UK spinor components are issued before
+// any of their arithmetic and stores; the operands read through the
+// read-only path are never written by another thread of the launch.  NMI,
+// NE and HX fix the operand counts of the hot updates at compile time (-1:
+// taken from the GenOp); every operand has the layout's pair count np, so
+// one element offset serves them all.
+template <int P>
+__device__ __forceinline__ CxPair<typename Prec<P>::pair> ldg_at(const Field& f, size_t e,
+                                                                  typename Prec<P>::pair sc) {
+    CxPair<typename Prec<P>::pair> v;
+    if constexpr (P == BK_FP64) {
+        const double2* q = (const double2*)f.data + 2 * e;
+        v.re = __ldg(q);
+        v.im = __ldg(q + 1);
+    } else if constexpr (P == BK_FP32) {
+        const float4 q = __ldg((const float4*)f.data + e);
+        v.re = make_float2(q.x, q.y);
+        v.im = make_float2(q.z, q.w);
+    } else {
+        const uint2 q = __ldg((const uint2*)f.data + e);
+        v.re = pmul(__half22float2(*reinterpret_cast<const __half2*>(&q.x)), sc);
+        v.im = pmul(__half22float2(*reinterpret_cast<const __half2*>(&q.y)), sc);
+    }
+    return v;
+}
+
+template <int P>
+__device__ __forceinline__ CxPair<typename Prec<P>::pair> load_at(const Field& f, size_t e) {
+    CxPair<typename Prec<P>::pair> v;
+    if constexpr (P == BK_FP64) {
+        const double2* q = (const double2*)f.data + 2 * e;
+        v.re = q[0];
+        v.im = q[1];
+    } else {
+        static_assert(P == BK_FP32, "accumulators are FP32 or FP64");
+        const float4 q = ((const float4*)f.data)[e];
+        v.re = make_float2(q.x, q.y);
+        v.im = make_float2(q.z, q.w);
+    }
+    return v;
+}
+
+template <int P>
+__device__ __forceinline__ void store_at(const Field& f, size_t e, typename Prec<P>::pair re,
+                                         typename Prec<P>::pair im) {
+    if constexpr (P == BK_FP64) {
+        double2* q = (double2*)f.data + 2 * e;
+        q[0] = re;
+        q[1] = im;
+    } else {
+        static_assert(P == BK_FP32, "element stores are for FP32 / FP64 blocks");
+        ((float4*)f.data)[e] = make_float4(re.x, re.y, im.x, im.y);
+    }
+}
+
+template <int P, int MAXL, int UK, int MINB, int NMI, int NE, int HX>
+__global__ void __launch_bounds__(GW_WARPS * 32, MINB) k_genop_w(const __grid_constant__ GenOp g, PTiles wt, int V,
+                                                                 int nchunk, int ncols, int np) {
+    using R = typename Prec<P>::real;
+    using R2 = typename Prec<P>::pair;
+    constexpr int XP = P == BK_FP64 ? BK_FP64 : BK_FP32;
+    using XR = typename Prec<XP>::real;
+    using X2 = typename Prec<XP>::pair;
+    static_assert(12 % UK == 0, "components per step divide 12");
+    constexpr int MMI = NMI >= 0 ? NMI : GENOP_MAXMI;
+    constexpr int ME = NE >= 0 ? NE : GENOP_MAXE;
+    const int nmi = NMI >= 0 ? NMI : g.nmi;
+    const int ne = NE >= 0 ? NE : g.ne;
+    const bool hx = HX >= 0 ? HX != 0 : g.hasX != 0;
+    __shared__ double2 ynred[GW_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int chunk = blockIdx.y;
+    const WLane L = wlane(g.p, wt.p0[blockIdx.x], wt.np[blockIdx.x], lane);
+    const bool act = L.live && !(g.skip && g.skip[L.s]);
+    const int s = L.s;
+    const bool mat = nmi > 0 && g.M != nullptr && ((g.hasY && g.ym != 0.0) || (hx && g.xm != 0.0));
+    cx<R> ea[ME > 0 ? ME : 1], ma[MMI > 0 ? MMI : 1], xa = mk(R(0), R(0));
+#pragma unroll
+    for (int e = 0; e < ME; ++e) ea[e] = e < ne ? coef<P>(g.ea[e], g.ea_mult[e], s) : mk(R(0), R(0));
+#pragma unroll
+    for (int u = 0; u < MMI; ++u) ma[u] = u < nmi ? coef<P>(g.ma[u], g.ma_mult[u], s) : mk(R(0), R(0));
+    if (hx) xa = coef<P>(g.xa, g.xa_mult, s);
+    // the lane's two columns of M; rows and columns past the system's size are zero
+    R2 Mr[MAXL], Mi[MAXL];
+    {
+        const double2* M = reinterpret_cast<const double2*>(g.M) + (act && mat ? g.p.coef_off[s] : 0);
+        const bool j1ok = L.i0 + 1 < L.Ls;
+#pragma unroll
+        for (int i = 0; i < MAXL; ++i) {
+            double2 m0 = make_double2(0.0, 0.0), m1 = make_double2(0.0, 0.0);
+            if (act && mat && i < L.Ls) {
+                m0 = M[i * L.Ls + L.i0];
+                if (j1ok) m1 = M[i * L.Ls + L.i0 + 1];
+            }
+            Mr[i].x = (R)m0.x;
+            Mr[i].y = (R)m1.x;
+            Mi[i].x = (R)m0.y;
+            Mi[i].y = (R)m1.y;
+        }
+    }
+    const R2 ym2 = bcast((R)g.ym);
+    const X2 xm2 = bcast((XR)g.xm);
+    const cx<XR> xax = mk((XR)xa.r, (XR)xa.i);
+    double yn0 = 0.0, yn1 = 0.0;
+    const int iters = (V + GW_WARPS * nchunk - 1) / (GW_WARPS * nchunk);
+    for (int it = 0; it < iters; ++it) {
+        const int n = (it * nchunk + chunk) * GW_WARPS + w;
+        if (n >= V) break;  // the same for the whole warp
+        R2 msc[MMI > 0 ? MMI : 1], esc[ME > 0 ? ME : 1], xsc = pzero<R2>();
+#pragma unroll
+        for (int u = 0; u < MMI; ++u) msc[u] = act && u < nmi ? pair_scale<P>(g.Mi[u], n, L.q) : pzero<R2>();
+#pragma unroll
+        for (int e = 0; e < ME; ++e) esc[e] = act && e < ne ? pair_scale<P>(g.E[e], n, L.q) : pzero<R2>();
+        if (act && hx) xsc = pair_scale<P>(g.Xin, n, L.q);
+        R2 yr[P == BK_FP16 ? 12 : 1], yi[P == BK_FP16 ? 12 : 1];
+        R sa = R(0), sb = R(0);
+        const size_t e0 = (size_t)n * 12 * np + L.q;
+        // FP16 keeps the site's 12 components in registers for the scaled store
+        constexpr int K0U = P == BK_FP16 ? 12 / UK : 1;
+#pragma unroll K0U
+        for (int k0 = 0; k0 < 12; k0 += UK) {
+            CxPair<R2> vm[UK][MMI > 0 ? MMI : 1], ve[UK][ME > 0 ? ME : 1], vx[UK];
+            CxPair<X2> xo[UK];
+#pragma unroll
+            for (int uk = 0; uk < UK; ++uk) {
+                const size_t e = e0 + (size_t)(k0 + uk) * np;
+#pragma unroll
+                for (int u = 0; u < MMI; ++u)
+                    vm[uk][u] = act && mat && u < nmi ? ldg_at<P>(g.Mi[u], e, msc[u])
+                                                      : CxPair<R2>{pzero<R2>(), pzero<R2>()};
+#pragma unroll
+                for (int t = 0; t < ME; ++t)
+                    ve[uk][t] = act && g.hasY && t < ne ? ldg_at<P>(g.E[t], e, esc[t])
+                                                        : CxPair<R2>{pzero<R2>(), pzero<R2>()};
+                vx[uk].re = vx[uk].im = pzero<R2>();
+                xo[uk].re = xo[uk].im = pzero<X2>();
+                if (act && hx) {
+                    vx[uk] = ldg_at<P>(g.Xin, e, xsc);
+                    xo[uk] = load_at<XP>(g.X, e);
+                }
+            }
+#pragma unroll
+            for (int uk = 0; uk < UK; ++uk) {
+                const int k = k0 + uk;
+                const size_t e = e0 + (size_t)k * np;
+                CxPair<R2> mp;
+                mp.re = mp.im = pzero<R2>();
+                if (mat) {
+                    CxPair<R2> c;
+                    c.re = c.im = pzero<R2>();
+#pragma unroll
+                    for (int u = 0; u < MMI; ++u)
+                        if (u < nmi) cpair_mac<R, R2>(c, ma[u], vm[uk][u]);
+#pragma unroll
+                    for (int ip = 0; ip < MAXL / 2; ++ip) {
+                        const CxPair<R2> cp = shfl_pair(c, L.base + min(ip, L.nps - 1));
+                        if (ip < L.nps) {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const R2 cr = bcast(h ? cp.re.y : cp.re.x), ci = bcast(h ? cp.im.y : cp.im.x);
+                                const R2 nci = bcast(h ? -cp.im.y : -cp.im.x);
+                                mp.re = pfma(cr, Mr[2 * ip + h], mp.re);
+                                mp.re = pfma(nci, Mi[2 * ip + h], mp.re);
+                                mp.im = pfma(cr, Mi[2 * ip + h], mp.im);
+                                mp.im = pfma(ci, Mr[2 * ip + h], mp.im);
+                            }
+                        }
+                    }
+                }
+                if (!act) continue;
+                if (g.hasY) {
+                    CxPair<R2> y;
+                    y.re = pmul(ym2, mp.re);
+                    y.im = pmul(ym2, mp.im);
+#pragma unroll
+                    for (int t = 0; t < ME; ++t)
+                        if (t < ne) cpair_mac<R, R2>(y, ea[t], ve[uk][t]);
+                    if (g.ynorm) {
+                        sa = fma(y.re.x, y.re.x, sa);
+                        sa = fma(y.im.x, y.im.x, sa);
+                        sb = fma(y.re.y, y.re.y, sb);
+                        sb = fma(y.im.y, y.im.y, sb);
+                    }
+                    if constexpr (P == BK_FP16) {
+                        yr[k] = y.re;
+                        yi[k] = y.im;
+                    } else {
+                        store_at<P>(g.Y, e, y.re, y.im);
+                    }
+                }
+                if (hx) {
+                    CxPair<X2> x = xo[uk], v;
+                    v.re.x = vx[uk].re.x;
+                    v.re.y = vx[uk].re.y;
+                    v.im.x = vx[uk].im.x;
+                    v.im.y = vx[uk].im.y;
+                    cpair_mac<XR, X2>(x, xax, v);
+                    X2 mr, mi;
+                    mr.x = mp.re.x;
+                    mr.y = mp.re.y;
+                    mi.x = mp.im.x;
+                    mi.y = mp.im.y;
+                    store_at<XP>(g.X, e, pfma(xm2, mr, x.re), pfma(xm2, mi, x.im));
+                }
+            }
+        }
+        if constexpr (P == BK_FP16) {
+            if (act && g.hasY) store_pair<P>(g.Y, n, L.q, yr, yi);
+        }
+        yn0 += (double)sa;
+        yn1 += (double)sb;
+    }
+    if (g.ynorm) {
+        ynred[w][lane] = make_double2(yn0, yn1);
+        __syncthreads();
+        if (act && w == 0) {
+            double2 v = make_double2(0.0, 0.0);
+            for (int ww = 0; ww < GW_WARPS; ++ww) {
+                v.x += ynred[ww][lane].x;
+                v.y += ynred[ww][lane].y;
+            }
+            g.ynorm[(size_t)chunk * ncols + 2 * L.q] = v.x;
+            g.ynorm[(size_t)chunk * ncols + 2 * L.q + 1] = v.y;
         }
     }
 }
@@ -1092,14 +1349,11 @@ size_t pair_smem(int rows, int np) {
 }
 
 template <int P, int NB, int MAXL>
-bk_status run_gram_small(Field A, Field B0, Field B1, const SysPart& p, const PTiles& tl, double2* part,
-                         int nchunk, int V, cudaStream_t st) {
-    constexpr int SR = srows<P>();
-    const size_t smem = (size_t)SR * TILE_MAXP * NB * 2 * MAXL * sizeof(double2);
-    BK_CUDA_TRY(cudaFuncSetAttribute(k_gram_small<P, NB, MAXL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    k_gram_small<P, NB, MAXL><<<dim3(tl.n, nchunk), dim3(TILE_MAXP, SR), smem, st>>>(A, B0, B1, p, tl, part, V,
-                                                                                  nchunk);
+bk_status run_gram_w(Field A, Field B0, Field B1, const SysPart& p, const PTiles& wt, double2* part, int nchunk,
+                     int V, cudaStream_t st) {
+    const size_t smem = (size_t)GW_WARPS * NB * 2 * MAXL * 32 * sizeof(double2);
+    BK_CUDA_TRY(cudaFuncSetAttribute(k_gram_w<P, NB, MAXL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_gram_w<P, NB, MAXL><<<dim3(wt.n, nchunk), GW_WARPS * 32, smem, st>>>(A, B0, B1, p, wt, part, V, nchunk);
     BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
 }
@@ -1112,15 +1366,15 @@ bk_status gram_impl(Field A, Field B, Field B2, int NB, const SysPart& p, double
     if (maxL == 0) return BK_OK;
     const int ne = p.coef_off[p.nsys];
     if (maxL <= GS_MAXL) {
-        const PTiles tl = make_ptiles(p);
+        const PTiles wt = make_ptiles(p, WT_PAIRS);
         if (NB == 2 && maxL <= GS2_MAXL) {
-            BK_TRY((run_gram_small<P, 2, GS2_MAXL>(A, B, B2, p, tl, part, nchunk, V, st)));
+            BK_TRY((run_gram_w<P, 2, GS2_MAXL>(A, B, B2, p, wt, part, nchunk, V, st)));
         } else {
             for (int b = 0; b < NB; ++b) {
                 Field Bb = b == 0 ? B : B2;
                 double2* pb = part + (size_t)b * nchunk * ne;
-                if (maxL <= 6) BK_TRY((run_gram_small<P, 1, 6>(A, Bb, Bb, p, tl, pb, nchunk, V, st)));
-                else BK_TRY((run_gram_small<P, 1, GS_MAXL>(A, Bb, Bb, p, tl, pb, nchunk, V, st)));
+                if (maxL <= 6) BK_TRY((run_gram_w<P, 1, 6>(A, Bb, Bb, p, wt, pb, nchunk, V, st)));
+                else BK_TRY((run_gram_w<P, 1, GS_MAXL>(A, Bb, Bb, p, wt, pb, nchunk, V, st)));
             }
         }
     } else {
@@ -1249,31 +1503,64 @@ int genop_norm_rows(int V) { return site_chunks(V); }
 
 bk_status launch_genop(int prec, const GenOp& g, int V, cudaStream_t st, bool* ynorm_done) {
     if (ynorm_done) *ynorm_done = false;
-    const PTiles tl = make_ptiles(g.p);
-    if (tl.n == 0) return BK_OK;
     const int nchunk = site_chunks(V);
     const int ncols = g.p.col0[g.p.nsys];
     int maxL = 0;
     for (int s = 0; s < g.p.nsys; ++s)
         if ((g.p.active >> s) & 1ull) maxL = std::max(maxL, g.p.L[s]);
-    const int ml = maxL <= 6 ? 6 : (maxL <= 12 ? 12 : 0);
-#define BK_GO(PP, ML)                                                                                       \
-    {                                                                                                       \
-        constexpr int SR = srows<PP>();                                                                     \
-        k_genop<PP, ML><<<dim3(tl.n, nchunk), dim3(TILE_MAXP, SR), 0, st>>>(g, tl, V, nchunk, ncols);        \
+    if (maxL == 0) return BK_OK;
+    // every operand in the layout's pair count (the fast kernels use one offset)
+    const int np = g.Y.np;
+    bool same_np = true;
+    for (int u = 0; u < g.nmi; ++u) same_np &= g.Mi[u].np == np;
+    for (int e = 0; e < g.ne; ++e) same_np &= g.E[e].np == np;
+    if (g.hasX) same_np &= g.X.np == np && g.Xin.np == np;
+    if (maxL <= 12 && g.hasY && same_np) {
+        const PTiles wt = make_ptiles(g.p, WT_PAIRS);
+        const dim3 grid(wt.n, nchunk);
+        const bool h = g.hasX != 0;
+#define BK_GW(PP, ML, UK, MB, NM, NE, HX) \
+    k_genop_w<PP, ML, UK, MB, NM, NE, HX><<<grid, GW_WARPS * 32, 0, st>>>(g, wt, V, nchunk, ncols, np)
+        // the FP32 updates of the two methods, then any other combination
+#define BK_GW32(ML)                                                                     \
+    if (g.nmi == 1 && g.ne == 0 && !h) BK_GW(BK_FP32, ML, 2, 2, 1, 0, 0);               \
+    else if (g.nmi == 1 && g.ne == 1 && !h) BK_GW(BK_FP32, ML, 2, 2, 1, 1, 0);          \
+    else if (g.nmi == 1 && g.ne == 2 && h) BK_GW(BK_FP32, ML, 2, 2, 1, 2, 1);           \
+    else if (g.nmi == 2 && g.ne == 1 && !h) BK_GW(BK_FP32, ML, 2, 2, 2, 1, 0);          \
+    else if (g.nmi == 2 && g.ne == 0 && h) BK_GW(BK_FP32, ML, 2, 2, 2, 0, 1);           \
+    else if (g.nmi == 0 && g.ne == 3 && !h) BK_GW(BK_FP32, ML, 2, 2, 0, 3, 0);          \
+    else BK_GW(BK_FP32, ML, 1, 2, -1, -1, -1);
+        switch (prec) {
+            case BK_FP64:
+                if (maxL <= 6) BK_GW(BK_FP64, 6, 1, 1, -1, -1, -1);
+                else BK_GW(BK_FP64, 12, 1, 1, -1, -1, -1);
+                break;
+            case BK_FP32:
+                if (maxL <= 6) {
+                    BK_GW32(6)
+                } else {
+                    BK_GW32(12)
+                }
+                break;
+            case BK_FP16:
+                if (maxL <= 6) BK_GW(BK_FP16, 6, 1, 1, -1, -1, -1);
+                else BK_GW(BK_FP16, 12, 1, 1, -1, -1, -1);
+                break;
+            default: return BK_ERR_INVALID_ARG;
+        }
+#undef BK_GW32
+#undef BK_GW
+    } else {
+        const PTiles tl = make_ptiles(g.p);
+        constexpr int SR = 4;
+        const dim3 grid(tl.n, nchunk), block(TILE_MAXP, SR);
+        switch (prec) {
+            case BK_FP64: k_genop<BK_FP64, SR><<<grid, block, 0, st>>>(g, tl, V, nchunk, ncols); break;
+            case BK_FP32: k_genop<BK_FP32, SR><<<grid, block, 0, st>>>(g, tl, V, nchunk, ncols); break;
+            case BK_FP16: k_genop<BK_FP16, SR><<<grid, block, 0, st>>>(g, tl, V, nchunk, ncols); break;
+            default: return BK_ERR_INVALID_ARG;
+        }
     }
-#define BK_GOP(PP)                        \
-    if (ml == 6) BK_GO(PP, 6)             \
-    else if (ml == 12) BK_GO(PP, 12)      \
-    else BK_GO(PP, 0)
-    switch (prec) {
-        case BK_FP64: BK_GOP(BK_FP64); break;
-        case BK_FP32: BK_GOP(BK_FP32); break;
-        case BK_FP16: BK_GOP(BK_FP16); break;
-        default: return BK_ERR_INVALID_ARG;
-    }
-#undef BK_GOP
-#undef BK_GO
     BK_CUDA_TRY(cudaGetLastError());
     if (ynorm_done && g.ynorm && g.hasY) *ynorm_done = true;
     return BK_OK;
