@@ -10,10 +10,12 @@ with multiple right-hand sides in lattice QCD" (arXiv:0903.4936):
 * ``dirac``   - D_W applied to a block of L spinor columns, Eq. (wd-op)
 * ``dense``   - the dense N x N matrix of D_W on small lattices
 * ``solvers`` - scalar BiCGSTAB, block BiCGSTAB and block BiCGGR (Section 3)
+* ``evenodd`` - the even-odd (Schur complement) form of the same system, a
+  reordering that is not in the paper, defined from the pieces above
 
 It is test infrastructure only.  Only ``tests/``, ``__graft_entry__.smoke()``
 and ``bench.py``'s CPU-baseline / reference arm may import it.  The product
 path (``paper_0903_4936_gb300``) never imports it, and it shares no code with
 the CUDA kernels; the only common module is ``synth`` (seeded inputs).
 """
-from . import gamma, clover, dirac, dense, solvers  # noqa: F401
+from . import gamma, clover, dirac, dense, solvers, evenodd  # noqa: F401
