@@ -45,11 +45,11 @@ _C3_CASES = [(k, L, src) for k in (0.120, 0.125, 0.130) for (L, src) in ((12, "p
 # Workloads: (Lx, Ly, Lz, Lt), link spread eps, c_SW, cases (kappa, L, source kind).
 WORKLOADS = {
     "c4": dict(dims=(24, 24, 24, 48), eps=0.5, csw=1.0, gauge_seed=1004, prec="fp32", method="bicgstab",
-               block=6, delta=0.03, distinct_sources=True, cases=_C4_CASES,
+               block=6, delta=0.003, distinct_sources=True, cases=_C4_CASES,
                desc="24^3x48 clover Wilson-Dirac, random SU(3) links eps=0.5, c_SW=1.0: 6 systems, kappa "
                     "{0.120,...,0.130} with L {4,12,12,24,48,96} Z4 noise = 196 right-hand sides; one batched "
                     "block BiCGSTAB solve over 33 block systems of at most 6 columns, FP32 inner iterations, FP64 "
-                    "residual replacement (delta 0.03), FP64 true residual <= 1e-10 for every column"),
+                    "residual replacement (delta 0.003), FP64 true residual <= 1e-10 for every column"),
     "c3": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp32", method="bicgstab",
                block=6, delta=0.03, cases=_C3_CASES,
                desc="16^3x32 clover Wilson-Dirac, random SU(3) links eps=0.5, c_SW=1.0, kappa in "
@@ -251,10 +251,10 @@ def _mem_available_gb():
     return 16.0
 
 
-def oracle_samples(wl, nsamples, rank=0):
+def oracle_samples(wl, nsamples, rank=0, max_procs=None):
     """Run nsamples timed oracle applications spread over the host cores
-    (one process per core, spawned, no GPU).  Returns (per-sample seconds,
-    processes used, the sampled system's (kappa, L))."""
+    (one process per core, at most max_procs, spawned, no GPU).  Returns
+    (per-sample seconds, processes used, the sampled system's (kappa, L))."""
     import numpy as np
 
     import synth
@@ -273,6 +273,8 @@ def oracle_samples(wl, nsamples, rank=0):
     V = synth.lattice_volume(dims)
     per_proc_gb = 2.5 + V * L * 12 * 16 * 8 / 2**30  # the application's temporaries
     procs = max(1, min(_host_cores(), nsamples, int(_mem_available_gb() * 0.7 / per_proc_gb)))
+    if max_procs:
+        procs = min(procs, max_procs)
     reps = [nsamples // procs + (1 if i < nsamples % procs else 0) for i in range(procs)]
     jobs = [(ROOT, dims, wl["eps"], gpath, fpath, wl["csw"], kappa, Lcase, kind, seed, r) for r in reps if r > 0]
     try:
@@ -288,6 +290,44 @@ def oracle_samples(wl, nsamples, rank=0):
         os.rmdir(tmp)
     secs = [t for r in res for t in r]
     return secs, len(jobs), (kappa, L)
+
+
+def _oracle_solve_worker(args):
+    """One process, one core: the full FP64 oracle block BiCGGR solve of one
+    block system to the benchmark's tolerance (the oracle as it stands)."""
+    root, dims, eps, gauge_seed, csw, kappa, L, kind, seed = args
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    sys.path.insert(0, root)
+    import synth
+    from oracle import clover, dense, dirac, solvers
+    U = synth.random_su3_field(dims, eps, gauge_seed)
+    F = clover.field_strength(U)
+    B = sources(dims, L, kind, seed)[:L]
+
+    def A(M):
+        return dense.to_columns(dirac.apply_dirac(U, dense.from_columns(M, dims), kappa, csw, F=F))
+
+    Bc = dense.to_columns(B)
+    t0 = time.perf_counter()
+    X, info = solvers.block_bicggr(A, Bc, TOL, MAXITER)
+    secs = time.perf_counter() - t0
+    res, _ = solvers.true_residual(A, Bc, X)
+    return secs, int(info["iterations"]), float(res)
+
+
+def oracle_full_solve(wl, rank=0):
+    """Seconds, iterations and true residual of the oracle's full solve of the
+    workload's first block system (spawned, so the thread limits hold)."""
+    kappa, L, ci = systems(wl)[0]
+    kind = wl["cases"][ci][2]
+    Lcase = wl["cases"][ci][1]
+    job = (ROOT, wl["dims"], wl["eps"], wl["gauge_seed"], wl["csw"], kappa, Lcase, kind,
+           case_seed(wl, ci, Lcase, rank))
+    ctx = multiprocessing.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        secs, iters, res = pool.map(_oracle_solve_worker, [job])[0]
+    return secs, iters, res, (kappa, Lcase)
 
 
 def oracle_rhs_per_s(secs, procs, L, iters):
@@ -511,6 +551,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-full", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-solve", action="store_true",
+                    help="with --impl reference: time the oracle's full solve of the first block system")
+    ap.add_argument("--cpu-procs", type=int, default=None,
+                    help="with --impl reference: at most this many oracle processes")
     ap.add_argument("--delta", type=float, default=None,
                     help="residual-replacement threshold (default: the workload's)")
     ap.add_argument("--update", choices=["fp64", "df64"], default=None,
@@ -528,7 +572,24 @@ def main():
         # Reference arm: the CPU oracle as it stands.  Each step is one sample
         # (an oracle operator application on the first block system); the
         # steps run concurrently, one process per host core.
-        secs, procs, (kappa, L) = oracle_samples(wl, args.warmup + args.steps)
+        if args.oracle_solve:
+            # the full oracle solve of the first block system, one core
+            secs, iters, res, (kappa, L) = oracle_full_solve(wl)
+            value = L / secs
+            sample = (f"one full FP64 numpy-oracle block BiCGGR solve of the first block system ({L} columns, "
+                      f"kappa={kappa}, R~0 = R0) to {TOL}: {iters} iterations, {secs:.1f} s, FP64 true residual "
+                      f"{res:.1e}; one process, one thread")
+            print(json.dumps({
+                "impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
+                "steps": 1, "warmup": 0, "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["desc"], "lattice": "x".join(map(str, wl["dims"])),
+                           "parallelism": "CPU oracle, 1 process"},
+                "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "host": {"nproc": _host_cores()}}))
+            return
+        secs, procs, (kappa, L) = oracle_samples(wl, args.warmup + args.steps, max_procs=args.cpu_procs)
         timed = secs[args.warmup:] if len(secs) > args.warmup else secs
         iters = FP64_ITERS_FIRST_SYSTEM[args.workload]
         value, mean = oracle_rhs_per_s(timed, procs, L, iters)
@@ -544,6 +605,7 @@ def main():
                        "parallelism": f"CPU oracle, {procs} processes"},
             "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": procs, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "host": {"nproc": _host_cores()},
         }
         print(json.dumps(line))
         return

@@ -116,7 +116,7 @@ struct bk_ctx {
     std::map<long long, Shape> shapes;
     bool autotune = true;
     bool verbose = false;  // BK_VERBOSE=1: one line per solve and per tuning decision on stderr
-    int force_variant = 0;  // BK_DSLASH_VARIANT=1|2|3: FP32/FP16 operator register-cap variant,
+    int force_variant = 0;  // BK_DSLASH_VARIANT=1..5: FP32/FP16 operator variant (4, 5: FP32 staged form),
                             // 128 threads, pair groups of 8, no tuning (tests the variants the tuner may pick)
     int force_prefetch = 0; // BK_DSLASH_PREFETCH=0..3: its prefetch mode (with BK_DSLASH_VARIANT)
 };
@@ -164,7 +164,7 @@ extern "C" bk_status bk_create(const int dims[4], int device, bk_ctx** out) {
         const char* v = getenv("BK_VERBOSE");
         c->verbose = v && v[0] == '1';
         const char* fv = getenv("BK_DSLASH_VARIANT");
-        if (fv && fv[0] >= '1' && fv[0] <= '3') c->force_variant = fv[0] - '0';
+        if (fv && fv[0] >= '1' && fv[0] <= '5') c->force_variant = fv[0] - '0';
         const char* fp = getenv("BK_DSLASH_PREFETCH");
         if (fp && fp[0] >= '0' && fp[0] <= '3') c->force_prefetch = fp[0] - '0';
     }
@@ -270,6 +270,13 @@ static bk_status tune_shape(bk_ctx* c, int prec, DslashOp op, cudaStream_t st, b
                 cands.push_back({128, 1, grp, pf});
                 cands.push_back({128, 2, grp, pf});
                 cands.push_back({128, 3, grp, pf});
+            }
+        // FP32: the staged form (rows through a shared-memory ring of 2 or 3 slots)
+        if (prec == BK_FP32)
+            for (int grp : {16, 0}) {
+                if (grp > 0 && grp >= npl) continue;
+                cands.push_back({128, 4, grp, 0});
+                cands.push_back({128, 5, grp, 0});
             }
     }
     // events released on every return path

@@ -107,74 +107,79 @@ __device__ __forceinline__ void project_pair(const float2 (&qr)[12], const float
     }
 }
 
-// acc += -kappa * expand(w) for projector (1 + S gamma_mu); nk = {-kappa}, pk = {+kappa}
+// acc += -kappa * expand(w) for projector (1 + S gamma_mu), colour a of both
+// half-spinor vectors (w0, w1); nk = {-kappa}, pk = {+kappa}
+template <int MU, int S>
+__device__ __forceinline__ void reconstruct_colour(int a, float2 w0r, float2 w0i, float2 w1r, float2 w1i, float2 nk,
+                                                   float2 pk, float2 (&ar)[12], float2 (&ai)[12]) {
+    const int c0 = a, c1 = 3 + a, c2 = 6 + a, c3 = 9 + a;
+    if constexpr (MU == 3) {
+        const float2 n2 = padd(nk, nk);
+        if constexpr (S > 0) {
+            ar[c0] = pfma(n2, w0r, ar[c0]);
+            ai[c0] = pfma(n2, w0i, ai[c0]);
+            ar[c1] = pfma(n2, w1r, ar[c1]);
+            ai[c1] = pfma(n2, w1i, ai[c1]);
+        } else {
+            ar[c2] = pfma(n2, w0r, ar[c2]);
+            ai[c2] = pfma(n2, w0i, ai[c2]);
+            ar[c3] = pfma(n2, w1r, ar[c3]);
+            ai[c3] = pfma(n2, w1i, ai[c3]);
+        }
+    } else {
+        ar[c0] = pfma(nk, w0r, ar[c0]);
+        ai[c0] = pfma(nk, w0i, ai[c0]);
+        ar[c1] = pfma(nk, w1r, ar[c1]);
+        ai[c1] = pfma(nk, w1i, ai[c1]);
+        if constexpr (MU == 0) {
+            // lower = (i S w1, i S w0); i w = (-w_i, w_r)
+            if constexpr (S > 0) {
+                ar[c2] = pfma(pk, w1i, ar[c2]);
+                ai[c2] = pfma(nk, w1r, ai[c2]);
+                ar[c3] = pfma(pk, w0i, ar[c3]);
+                ai[c3] = pfma(nk, w0r, ai[c3]);
+            } else {
+                ar[c2] = pfma(nk, w1i, ar[c2]);
+                ai[c2] = pfma(pk, w1r, ai[c2]);
+                ar[c3] = pfma(nk, w0i, ar[c3]);
+                ai[c3] = pfma(pk, w0r, ai[c3]);
+            }
+        } else if constexpr (MU == 1) {
+            // lower = (S w1, -S w0)
+            if constexpr (S > 0) {
+                ar[c2] = pfma(nk, w1r, ar[c2]);
+                ai[c2] = pfma(nk, w1i, ai[c2]);
+                ar[c3] = pfma(pk, w0r, ar[c3]);
+                ai[c3] = pfma(pk, w0i, ai[c3]);
+            } else {
+                ar[c2] = pfma(pk, w1r, ar[c2]);
+                ai[c2] = pfma(pk, w1i, ai[c2]);
+                ar[c3] = pfma(nk, w0r, ar[c3]);
+                ai[c3] = pfma(nk, w0i, ai[c3]);
+            }
+        } else {
+            // MU == 2: lower = (i S w0, -i S w1)
+            if constexpr (S > 0) {
+                ar[c2] = pfma(pk, w0i, ar[c2]);
+                ai[c2] = pfma(nk, w0r, ai[c2]);
+                ar[c3] = pfma(nk, w1i, ar[c3]);
+                ai[c3] = pfma(pk, w1r, ai[c3]);
+            } else {
+                ar[c2] = pfma(nk, w0i, ar[c2]);
+                ai[c2] = pfma(pk, w0r, ai[c2]);
+                ar[c3] = pfma(pk, w1i, ar[c3]);
+                ai[c3] = pfma(nk, w1r, ai[c3]);
+            }
+        }
+    }
+}
+
 template <int MU, int S>
 __device__ __forceinline__ void reconstruct_pair(const Hop& w, float2 nk, float2 pk, float2 (&ar)[12],
                                                  float2 (&ai)[12]) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int c0 = a, c1 = 3 + a, c2 = 6 + a, c3 = 9 + a;
-        const float2 w0r = w.r[a], w0i = w.i[a], w1r = w.r[3 + a], w1i = w.i[3 + a];
-        if constexpr (MU == 3) {
-            const float2 n2 = padd(nk, nk);
-            if constexpr (S > 0) {
-                ar[c0] = pfma(n2, w0r, ar[c0]);
-                ai[c0] = pfma(n2, w0i, ai[c0]);
-                ar[c1] = pfma(n2, w1r, ar[c1]);
-                ai[c1] = pfma(n2, w1i, ai[c1]);
-            } else {
-                ar[c2] = pfma(n2, w0r, ar[c2]);
-                ai[c2] = pfma(n2, w0i, ai[c2]);
-                ar[c3] = pfma(n2, w1r, ar[c3]);
-                ai[c3] = pfma(n2, w1i, ai[c3]);
-            }
-        } else {
-            ar[c0] = pfma(nk, w0r, ar[c0]);
-            ai[c0] = pfma(nk, w0i, ai[c0]);
-            ar[c1] = pfma(nk, w1r, ar[c1]);
-            ai[c1] = pfma(nk, w1i, ai[c1]);
-            if constexpr (MU == 0) {
-                // lower = (i S w1, i S w0); i w = (-w_i, w_r)
-                if constexpr (S > 0) {
-                    ar[c2] = pfma(pk, w1i, ar[c2]);
-                    ai[c2] = pfma(nk, w1r, ai[c2]);
-                    ar[c3] = pfma(pk, w0i, ar[c3]);
-                    ai[c3] = pfma(nk, w0r, ai[c3]);
-                } else {
-                    ar[c2] = pfma(nk, w1i, ar[c2]);
-                    ai[c2] = pfma(pk, w1r, ai[c2]);
-                    ar[c3] = pfma(nk, w0i, ar[c3]);
-                    ai[c3] = pfma(pk, w0r, ai[c3]);
-                }
-            } else if constexpr (MU == 1) {
-                // lower = (S w1, -S w0)
-                if constexpr (S > 0) {
-                    ar[c2] = pfma(nk, w1r, ar[c2]);
-                    ai[c2] = pfma(nk, w1i, ai[c2]);
-                    ar[c3] = pfma(pk, w0r, ar[c3]);
-                    ai[c3] = pfma(pk, w0i, ai[c3]);
-                } else {
-                    ar[c2] = pfma(pk, w1r, ar[c2]);
-                    ai[c2] = pfma(pk, w1i, ai[c2]);
-                    ar[c3] = pfma(nk, w0r, ar[c3]);
-                    ai[c3] = pfma(nk, w0i, ai[c3]);
-                }
-            } else {
-                // MU == 2: lower = (i S w0, -i S w1)
-                if constexpr (S > 0) {
-                    ar[c2] = pfma(pk, w0i, ar[c2]);
-                    ai[c2] = pfma(nk, w0r, ai[c2]);
-                    ar[c3] = pfma(nk, w1i, ar[c3]);
-                    ai[c3] = pfma(pk, w1r, ai[c3]);
-                } else {
-                    ar[c2] = pfma(nk, w0i, ar[c2]);
-                    ai[c2] = pfma(pk, w0r, ai[c2]);
-                    ar[c3] = pfma(pk, w1i, ar[c3]);
-                    ai[c3] = pfma(nk, w1r, ai[c3]);
-                }
-            }
-        }
-    }
+    for (int a = 0; a < 3; ++a)
+        reconstruct_colour<MU, S>(a, w.r[a], w.i[a], w.r[3 + a], w.i[3 + a], nk, pk, ar, ai);
 }
 
 // w = U h (forward) or U^+ h (backward) for both half-spinor vectors.  Link
@@ -449,6 +454,269 @@ __global__ void __launch_bounds__(MAXT, MINB) k_dslash_pair(const __grid_constan
     store_pair<P>(a.y, n, p, ar, ai);
 }
 
+// Link product and reconstruction fused row by row: output colour i of both
+// half-spinor vectors is formed and added at once, so only one row of the
+// link and one colour of w are live.
+template <int MU, int S>
+__device__ __forceinline__ void link_mul_add(const float4* __restrict__ u4, const Hop& h, float2 nk, float2 pk,
+                                             float2 (&ar)[12], float2 (&ai)[12]) {
+    constexpr bool DAG = S > 0;
+    const float2* u2 = reinterpret_cast<const float2*>(u4);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float2 ur[3], ui[3], un[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int e = DAG ? 3 * j + i : 3 * i + j;
+            const float4 q = __ldg(u4 + e);
+            ur[j] = make_float2(q.x, q.y);
+            ui[j] = make_float2(q.z, q.w);
+            un[j] = __ldg(u2 + 18 + e);
+        }
+        float2 wr[2], wi[2];
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            wr[hh] = make_float2(0.f, 0.f);
+            wi[hh] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float2 hr = h.r[3 * hh + j], hi = h.i[3 * hh + j];
+                if constexpr (!DAG) {  // U_ij h_j
+                    wr[hh] = pfma(ur[j], hr, wr[hh]);
+                    wr[hh] = pfma(un[j], hi, wr[hh]);
+                    wi[hh] = pfma(ur[j], hi, wi[hh]);
+                    wi[hh] = pfma(ui[j], hr, wi[hh]);
+                } else {  // conj(U_ji) h_j
+                    wr[hh] = pfma(ur[j], hr, wr[hh]);
+                    wr[hh] = pfma(ui[j], hi, wr[hh]);
+                    wi[hh] = pfma(ur[j], hi, wi[hh]);
+                    wi[hh] = pfma(un[j], hr, wi[hh]);
+                }
+            }
+        }
+        reconstruct_colour<MU, S>(i, wr[0], wi[0], wr[1], wi[1], nk, pk, ar, ai);
+    }
+}
+
+// out = q - kappa C q with out holding q on entry; the two chiral blocks run
+// one after the other and add into out directly (fewer live registers than
+// clover_pair).
+__device__ __forceinline__ void clover_pair_inplace(const float4* __restrict__ c4, float2 nk, float2 (&ar)[12],
+                                                    float2 (&ai)[12]) {
+    const float2* c2 = reinterpret_cast<const float2*>(c4);
+    float2 vr[2][6], vi[2][6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        vr[0][k] = padd(ar[k], ar[k + 6]);
+        vi[0][k] = padd(ai[k], ai[k + 6]);
+        vr[1][k] = psub(ar[k], ar[k + 6]);
+        vi[1][k] = psub(ai[k], ai[k + 6]);
+    }
+    const float2 pk = make_float2(-nk.x, -nk.y);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        float2 yr[6], yi[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const float2 d = __ldg(c2 + 90 + 6 * b + i);
+            yr[i] = pmul(d, vr[b][i]);
+            yi[i] = pmul(d, vi[b][i]);
+        }
+        int q = 0;
+#pragma unroll
+        for (int i = 1; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j < i; ++j, ++q) {
+                const float4 A = __ldg(c4 + 15 * b + q);
+                const float2 AR = make_float2(A.x, A.y), AI = make_float2(A.z, A.w);
+                const float2 NAI = __ldg(c2 + 60 + 15 * b + q);
+                yr[i] = pfma(AR, vr[b][j], yr[i]);
+                yr[i] = pfma(NAI, vi[b][j], yr[i]);
+                yi[i] = pfma(AR, vi[b][j], yi[i]);
+                yi[i] = pfma(AI, vr[b][j], yi[i]);
+                yr[j] = pfma(AR, vr[b][i], yr[j]);
+                yr[j] = pfma(AI, vi[b][i], yr[j]);
+                yi[j] = pfma(AR, vi[b][i], yi[j]);
+                yi[j] = pfma(NAI, vr[b][i], yi[j]);
+            }
+        // upper half: -kappa y for both blocks; lower half: -kappa y (b = 0), +kappa y (b = 1)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            ar[k] = pfma(nk, yr[k], ar[k]);
+            ai[k] = pfma(nk, yi[k], ai[k]);
+            ar[k + 6] = pfma(b == 0 ? nk : pk, yr[k], ar[k + 6]);
+            ai[k + 6] = pfma(b == 0 ? nk : pk, yi[k], ai[k + 6]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- staged form (FP32)
+//
+// The same operator with the spinor rows staged through shared memory by
+// asynchronous copies (cp.async, 16 bytes each, L2 to shared memory).  A
+// thread's work is ten stages: its own row (clover term), the eight hops, and
+// the right-hand side of the residual form; each stage's rows go into one of
+// NSLOT slots of the thread's own ring, and while a stage computes, the next
+// NSLOT - 1 stages are already on their way.  The copies hold no registers,
+// so a thread keeps whole hops in flight at the register cost of the
+// synchronous kernel.  No thread reads another thread's slots, so no barrier
+// is needed: each thread waits for its own copy groups only.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int DA_STAGES = 10;  // own row, eight hops, right-hand side
+constexpr int DA_THREADS = 128;
+
+// rows of stage s at site `site` into the thread's slot (stride T float4)
+__device__ __forceinline__ void stage_issue(const DPairArgs& a, int s, int site, int p, float4* slot, int T) {
+    const Field& f = s == DA_STAGES - 1 ? a.b : a.x;
+    const float4* src = (const float4*)f.data + ((size_t)site * 12 * f.np + p);
+    const int k0 = s == 7 ? 6 : 0;   // forward t hop: spins 2, 3
+    const int k1 = s == 8 ? 6 : 12;  // backward t hop: spins 0, 1
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+        if (k >= k0 && k < k1) cp_async16(slot + k * T, src + (size_t)k * f.np);
+}
+
+template <int MU, int S>
+__device__ __forceinline__ void hop_staged(const float4* slot, int T, const float4* __restrict__ link, float2 nk,
+                                           float2 pk, float2 (&ar)[12], float2 (&ai)[12]) {
+    Hop h;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float2 qr[12], qi[12];
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) {
+            if (MU == 3 && ((S > 0) != (sp < 2))) continue;
+            const float4 q = slot[(3 * sp + c) * T];
+            qr[3 * sp + c] = make_float2(q.x, q.y);
+            qi[3 * sp + c] = make_float2(q.z, q.w);
+        }
+        Hop hc;
+        project_pair<MU, S>(qr, qi, hc, c);
+        h.r[c] = hc.r[c];
+        h.i[c] = hc.i[c];
+        h.r[3 + c] = hc.r[3 + c];
+        h.i[3 + c] = hc.i[3 + c];
+    }
+    link_mul_add<MU, S>(link, h, nk, pk, ar, ai);
+}
+
+// Stage S of the staged kernel: wait for its rows, compute, refill its slot
+// with stage S + NSLOT.  A template, so that every stage's hop, wait count
+// and slot are compile-time constants.
+template <int S, int NSLOT>
+__device__ __forceinline__ void run_stage(const DPairArgs& a, const int (&site)[DA_STAGES], int n, int p,
+                                          float4* ring, float2 nk, float2 pk, float2 (&ar)[12], float2 (&ai)[12]) {
+    constexpr int T = DA_THREADS;
+    // stage S complete; the later ones may still be in flight
+    constexpr int pending = (DA_STAGES - 1 - S) < (NSLOT - 1) ? (DA_STAGES - 1 - S) : (NSLOT - 1);
+    cp_async_wait<pending>();
+    const float4* slot = ring + (S % NSLOT) * 12 * T;
+    if constexpr (S == 0) {  // out = x - kappa C x
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const float4 q = slot[k * T];
+            ar[k] = make_float2(q.x, q.y);
+            ai[k] = make_float2(q.z, q.w);
+        }
+        clover_pair_inplace(a.C + (size_t)n * BK_CLOV32_F4, nk, ar, ai);
+    } else if constexpr (S < DA_STAGES - 1) {
+        constexpr int hop = S - 1, MU = hop >> 1, SG = (hop & 1) ? +1 : -1;
+        const float4* link = a.U + ((size_t)MU * a.V + ((hop & 1) ? site[S] : n)) * BK_LINK32_F4;
+        hop_staged<MU, SG>(slot, T, link, nk, pk, ar, ai);
+    } else {
+        if (a.residual) {  // b - D x
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                const float4 q = slot[k * T];
+                ar[k] = psub(make_float2(q.x, q.y), ar[k]);
+                ai[k] = psub(make_float2(q.z, q.w), ai[k]);
+            }
+        }
+    }
+    // refill the slot just read with stage S + NSLOT (its link lines prefetched)
+    constexpr int SN = S + NSLOT;
+    if constexpr (SN < DA_STAGES) {
+        if (SN < DA_STAGES - 1 || a.residual) stage_issue(a, SN, site[SN], p, ring + (SN % NSLOT) * 12 * T, T);
+        if constexpr (SN >= 1 && SN < DA_STAGES - 1) {
+            constexpr int hop = SN - 1;
+            const char* l =
+                (const char*)(a.U + ((size_t)(hop >> 1) * a.V + ((hop & 1) ? site[SN] : n)) * BK_LINK32_F4);
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(l));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(l + 128));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(l + 223));
+        }
+        cp_async_commit();
+    }
+}
+
+template <int NSLOT, int MINB>
+__global__ void __launch_bounds__(DA_THREADS, MINB) k_dslash_staged(const __grid_constant__ DPairArgs a) {
+    extern __shared__ float4 da_ring[];  // [NSLOT][12][DA_THREADS]
+    constexpr int T = DA_THREADS;
+    const int t = threadIdx.x;
+    const long long g = (long long)blockIdx.x * T + t;
+    if (g >= (long long)a.V * a.npl) return;  // no barriers below
+    const long long per_group = (long long)a.V * a.G;
+    const int grp = (int)(g / per_group);
+    const long long r = g - (long long)grp * per_group;
+    const int gw = min(a.G, a.npl - grp * a.G);
+    const int n = (int)(r / gw);
+    const int pl = grp * a.G + (int)(r - (long long)n * gw);
+    const int p = a.p0 + pl;
+    int site[DA_STAGES];
+    {
+        int co[4], rr = n;
+        co[0] = rr % a.L[0];
+        rr /= a.L[0];
+        co[1] = rr % a.L[1];
+        rr /= a.L[1];
+        co[2] = rr % a.L[2];
+        co[3] = rr / a.L[2];
+        site[0] = n;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const int Lm = a.L[mu], sm = a.st[mu];
+            site[1 + 2 * mu] = co[mu] == Lm - 1 ? n - (Lm - 1) * sm : n + sm;  // forward
+            site[2 + 2 * mu] = co[mu] == 0 ? n + (Lm - 1) * sm : n - sm;       // backward
+        }
+        site[DA_STAGES - 1] = n;
+    }
+    float4* ring = da_ring + t;
+    {   // the site's clover entries, needed first
+        const char* cl = (const char*)(a.C + (size_t)n * BK_CLOV32_F4);
+#pragma unroll
+        for (int l = 0; l < 7; ++l) asm volatile("prefetch.global.L1 [%0];" ::"l"(cl + 128 * l));
+    }
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) {
+        stage_issue(a, s, site[s], p, ring + s * 12 * T, T);
+        cp_async_commit();
+    }
+    const float2 nk = a.nk[pl];
+    const float2 pk = make_float2(-nk.x, -nk.y);
+    float2 ar[12], ai[12];
+    run_stage<0, NSLOT>(a, site, n, p, ring, nk, pk, ar, ai);
+    run_stage<1, NSLOT>(a, site, n, p, ring, nk, pk, ar, ai);
+    run_stage<2, NSLOT>(a, site, n, p, ring, nk, pk, ar, ai);
+    run_stage<3, NSLOT>(a, site, n, p, ring, nk, pk, ar, ai);
+    run_stage<4, NSLOT>(a, site, n, p, ring, nk, pk, ar, ai);
+    run_stage<5, NSLOT>(a, site, n, p, ring, nk, pk, ar, ai);
+    run_stage<6, NSLOT>(a, site, n, p, ring, nk, pk, ar, ai);
+    run_stage<7, NSLOT>(a, site, n, p, ring, nk, pk, ar, ai);
+    run_stage<8, NSLOT>(a, site, n, p, ring, nk, pk, ar, ai);
+    run_stage<9, NSLOT>(a, site, n, p, ring, nk, pk, ar, ai);
+    store_pair<BK_FP32>(a.y, n, p, ar, ai);
+}
+
 // ================================================================= FP64 / double-float: one column per thread
 
 template <int P>
@@ -678,7 +946,7 @@ bk_status dslash_pair_impl(const DslashOp& op, cudaStream_t st) {
             a.nk[j] = make_float2((float)-ka, (float)-kb);
         }
         // variants: register cap 255 (1: 1 block of 256), 170 (2: 3 blocks of
-        // 128), 128 (3: 4 blocks of 128)
+        // 128), 128 (3: 4 blocks of 128); FP32 staged form 4, 5 (k_dslash_staged)
         int threads = op.threads > 0 ? op.threads : 128;
         if (op.variant >= 2 && threads > 128) threads = 128;
         a.G = op.group > 0 ? std::min(op.group, npl) : npl;
@@ -690,7 +958,21 @@ bk_status dslash_pair_impl(const DslashOp& op, cudaStream_t st) {
     else if (op.prefetch == 2) k_dslash_pair<P, MT, MB, 2><<<blocks, threads, 0, st>>>(a); \
     else if (op.prefetch == 3) k_dslash_pair<P, MT, MB, 3><<<blocks, threads, 0, st>>>(a); \
     else k_dslash_pair<P, MT, MB, 0><<<blocks, threads, 0, st>>>(a);
-        if (op.variant == 1) {
+        if (P == BK_FP32 && (op.variant == 4 || op.variant == 5)) {
+            // staged form: 128 threads, ring of 2 (variant 4) or 3 (variant 5) slots
+            const unsigned sb = (unsigned)((items + DA_THREADS - 1) / DA_THREADS);
+            if (op.variant == 4) {
+                const size_t smem = (size_t)2 * 12 * DA_THREADS * sizeof(float4);
+                BK_CUDA_TRY(cudaFuncSetAttribute(k_dslash_staged<2, 4>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                k_dslash_staged<2, 4><<<sb, DA_THREADS, smem, st>>>(a);
+            } else {
+                const size_t smem = (size_t)3 * 12 * DA_THREADS * sizeof(float4);
+                BK_CUDA_TRY(cudaFuncSetAttribute(k_dslash_staged<3, 3>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                k_dslash_staged<3, 3><<<sb, DA_THREADS, smem, st>>>(a);
+            }
+        } else if (op.variant == 1) {
             BK_DP(256, 1)
         } else if (op.variant == 3) {
             BK_DP(128, 4)

@@ -174,14 +174,15 @@ def test_df64_operator_tracks_fp64_where_fp32_cannot():
     assert np.linalg.norm(r32 - r64) > 10 * np.linalg.norm(r64)
 
 
-@pytest.mark.parametrize("variant", ["1", "2", "3", "1:1", "2:2", "2:3", "3:3"])
+@pytest.mark.parametrize("variant", ["1", "2", "3", "1:1", "2:2", "2:3", "3:3", "4", "5"])
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
 @pytest.mark.parametrize("dims,L", [((4, 4, 4, 4), 12), ((2, 4, 2, 6), 5), ((3, 5, 4, 6), 1), ((8, 8, 8, 16), 13),
                                     ((4, 4, 4, 8), 21)])
 def test_dslash_every_launch_variant(monkeypatch, variant, prec, dims, L):
     """Each register-cap variant of the packed-pair operator the autotuner may
-    pick, with and without the L2 / L1 prefetch of its rows and in its looped
-    form (forced with
+    pick, with and without the L2 / L1 prefetch of its rows, in its looped
+    form and in the FP32 staged form (variants 4, 5; FP16 runs variant 2's
+    kernel for them) (forced with
     BK_DSLASH_VARIANT / BK_DSLASH_PREFETCH, pair groups of 8: L = 21 runs a full
     group of 8 pairs and a short one of 3) against the oracle; odd L leaves a
     padding column in the last pair.  On 4^4 the variant is also the inner operator of
