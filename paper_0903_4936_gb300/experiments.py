@@ -3,6 +3,7 @@ synthetic gauge fields: L dependence of block BiCGSTAB and block BiCGGR.
 
     python -m paper_0903_4936_gb300.experiments [--dims 16 16 16 32] [--seeds 1003 1013]
         [--kappas ...] [--scan] [--json out.json] [--markdown]
+    python -m paper_0903_4936_gb300.experiments --from-json result.json
 
 For every kappa, method and block size L, the 12 point sources at the origin
 are split into 12 / L blocks of L columns, each block a system of its own (the
@@ -118,6 +119,34 @@ def markdown(rows):
     return "\n".join(lines)
 
 
+def markdown_report(result):
+    """The scan and the grid of a result file as markdown (the tables of the
+    design notes are generated with --from-json)."""
+    out = []
+    for key, title in (("scan", "kappa scan, FP64 BiCGSTAB, one point source"),
+                       ("scan_fine", "refined between the last two kappas")):
+        if result.get(key):
+            out.append(f"{title} (seed {result['seeds'][0]}):\n")
+            out.append("| kappa | iterations | converged | true residual |")
+            out.append("|---|---|---|---|")
+            for r in result[key]:
+                out.append(f"| {r['kappa']:.5f} | {r['iterations']} | {r['converged']} | {r['true_res']:.2e} |")
+            out.append("")
+    out.append(markdown(result["grid"]))
+    h = result.get("histories", {})
+    if h.get("by_method_L"):
+        out.append("")
+        out.append(f"residual histories (seed {h['seed']}, kappa {h['kappa']}): iterations to 1e-4 / 1e-8 / 1e-12")
+        out.append("")
+        out.append("| method, L | 1e-4 | 1e-8 | 1e-12 | total |")
+        out.append("|---|---|---|---|---|")
+        for k, hist in h["by_method_L"].items():
+            def first(t):
+                return next((i for i, v in enumerate(hist) if v <= t), "-")
+            out.append(f"| {k} | {first(1e-4)} | {first(1e-8)} | {first(1e-12)} | {len(hist) - 1} |")
+    return "\n".join(out)
+
+
 def main(argv=None) -> None:
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--dims", type=int, nargs=4, default=[16, 16, 16, 32])
@@ -129,7 +158,12 @@ def main(argv=None) -> None:
     ap.add_argument("--scan", action="store_true")
     ap.add_argument("--json")
     ap.add_argument("--markdown", action="store_true")
+    ap.add_argument("--from-json", help="print the tables of an earlier --json result and exit")
     args = ap.parse_args(argv)
+    if args.from_json:
+        with open(args.from_json) as f:
+            print(markdown_report(json.load(f)))
+        return
     dims = tuple(args.dims)
     result = dict(dims=list(dims), eps=0.5, csw=1.0, tol=args.tol, seeds=args.seeds,
                   sources="the 12 point sources at the origin, split into 12/L blocks of L columns",
