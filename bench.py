@@ -1,25 +1,31 @@
 #!/usr/bin/env python
 """Benchmark: right-hand sides solved per second to FP64 true relative residual
-1e-10 on a synthetic clover Wilson-Dirac problem, plus the multi-RHS operator's
+1e-10 on a synthetic clover Wilson-Dirac problem, plus the inner operator's
 HBM roofline.
 
 Default workload (`--workload c4`): 24^3 x 48, random SU(3) links eps = 0.5,
 c_SW = 1, six systems kappa in {0.120, ..., 0.130} with L = {4, 12, 12, 24, 48,
 96} Z4 noise sources (196 right-hand sides).  One step = the whole workload
 solved once through the C ABI as one batched solve: every system split into
-block systems of at most 6 columns, block BiCGSTAB with FP32 inner iterations
-and FP64 residual replacement, each column to an FP64 true residual <= 1e-10
-(the run fails otherwise).  Prints ONE JSON line on rank 0.
+block systems of at most 6 columns, block BiCGSTAB on the even-odd Schur
+system (--no-eo: on the full system) with FP32 inner iterations and FP64
+residual replacement (delta 0.003), each column to an FP64 true residual
+<= 1e-10 of the full system (the run fails otherwise).  Prints ONE JSON line
+on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload c4|c3|c2|...] [--no-fp64] [--fp64-full] [--no-cpu-baseline]
+                  [--workload c4|c3|c2|c3-12] [--no-fp64] [--fp64-full] [--no-cpu-baseline]
+                  [--eo | --no-eo] [--delta D] [--update fp64|df64]
+                  [--oracle-solve] [--cpu-procs N]   (reference arm)
 
 Comparisons on the same GPU (after the timed steps): the plain FP64 method at
-the same 6-column split (isolates precision) and, with --fp64-full, the
-paper's FP64 block BiCGGR with every system as one block of all its columns.
+the same 6-column split and formulation (isolates precision) and, with
+--fp64-full, the paper's FP64 block BiCGGR with every system as one block of
+all its columns on the full system.
 
 --impl reference times the FP64 CPU oracle (test infrastructure, written from
-the paper) on bounded samples of the same workload on the host cores.
+the paper) on bounded samples of the same workload on the host cores
+(--oracle-solve: its full solve of the first block system, one core).
 """
 from __future__ import annotations
 
@@ -45,17 +51,19 @@ _C3_CASES = [(k, L, src) for k in (0.120, 0.125, 0.130) for (L, src) in ((12, "p
 # Workloads: (Lx, Ly, Lz, Lt), link spread eps, c_SW, cases (kappa, L, source kind).
 WORKLOADS = {
     "c4": dict(dims=(24, 24, 24, 48), eps=0.5, csw=1.0, gauge_seed=1004, prec="fp32", method="bicgstab",
-               block=6, delta=0.003, distinct_sources=True, cases=_C4_CASES,
+               block=6, delta=0.003, eo=True, distinct_sources=True, cases=_C4_CASES,
                desc="24^3x48 clover Wilson-Dirac, random SU(3) links eps=0.5, c_SW=1.0: 6 systems, kappa "
                     "{0.120,...,0.130} with L {4,12,12,24,48,96} Z4 noise = 196 right-hand sides; one batched "
-                    "block BiCGSTAB solve over 33 block systems of at most 6 columns, FP32 inner iterations, FP64 "
-                    "residual replacement (delta 0.003), FP64 true residual <= 1e-10 for every column"),
+                    "block BiCGSTAB solve over 33 block systems of at most 6 columns on the even-odd Schur "
+                    "system, FP32 inner iterations, FP64 residual replacement (delta 0.003), FP64 true residual "
+                    "of the full system <= 1e-10 for every column"),
     "c3": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp32", method="bicgstab",
-               block=6, delta=0.03, cases=_C3_CASES,
+               block=6, delta=0.003, eo=True, cases=_C3_CASES,
                desc="16^3x32 clover Wilson-Dirac, random SU(3) links eps=0.5, c_SW=1.0, kappa in "
                     "{0.120,0.125,0.130} x (L=12 point sources, L=48 complex-Z2 noise) = 180 right-hand sides; "
-                    "one batched block BiCGSTAB solve over 30 systems of 6 columns, FP32 inner iterations, FP64 "
-                    "residual replacement (delta 0.03), FP64 true residual <= 1e-10 for every column"),
+                    "one batched block BiCGSTAB solve over 30 systems of 6 columns on the even-odd Schur system, "
+                    "FP32 inner iterations, FP64 residual replacement (delta 0.003), FP64 true residual of the "
+                    "full system <= 1e-10 for every column"),
     "c2": dict(dims=(8, 8, 8, 16), eps=0.5, csw=1.0, gauge_seed=1002, prec="fp32", method="bicggr",
                cases=[(0.125, 12, "point")],
                desc="8^3x16, eps=0.5, c_SW=1.0, kappa=0.125, L=12 point sources; block BiCGGR with FP32 inner "
@@ -73,6 +81,16 @@ MAXITER = 5000
 def spinor_bytes(prec):
     # per site and column: read 24 reals, write 24 reals (+ one FP32 scale each way for FP16)
     return {"fp64": 2 * 24 * 8, "fp32": 2 * 24 * 4, "fp16": 2 * (24 * 2 + 4)}[prec]
+
+
+def schur_bytes(V, L, prec, applications=1):
+    """Algorithmic bytes of `applications` even-odd Schur operator
+    applications over L columns in total (two half-lattice launches each):
+    per application the links twice (4 per site) and the 72-real site
+    inverse once per site; per column the even input read twice, the odd
+    temporary written and read, the output written (5 half-lattice passes)."""
+    s = 8 if prec == "fp64" else 4
+    return applications * V * (2 * 4 * 18 * s + 72 * s) + (V // 2) * L * 5 * (spinor_bytes(prec) // 2)
 
 
 def dslash_bytes(V, L, prec, launches=1):
@@ -396,6 +414,7 @@ def gb300_arm(args, wl, rank, world, local_rank):
     sysl = systems(wl)
     kap_s, L_s, owner = [s[0] for s in sysl], [s[1] for s in sysl], [s[2] for s in sysl]
     update = args.update or wl.get("update", "fp64")
+    eo = wl.get("eo", False) if args.eo is None else args.eo
     delta = args.delta if args.delta is not None else wl.get("delta", 0.0)
     Xdev = torch.empty_like(Ball)
     Bh = Ball.cpu().pin_memory()
@@ -405,7 +424,7 @@ def gb300_arm(args, wl, rank, world, local_rank):
     def solve(B, X, record, prec=None, method=None):
         return lat.block_solve_batched(B, kap_s, L_s, method=method or wl["method"], prec=prec or wl["prec"],
                                        tol=TOL, maxiter=MAXITER, timing=record, delta=delta,
-                                       out=X, raise_on_fail=False, update=update)
+                                       out=X, raise_on_fail=False, update=update, eo=eo)
 
     def check(infos, what):
         for si, info in enumerate(infos):
@@ -418,7 +437,8 @@ def gb300_arm(args, wl, rank, world, local_rank):
         info = infos[0]
         return dict(launches=info["n_launches"], t_inner=info["time_dslash_inner_ms"],
                     n_inner=info["n_dslash_inner"],
-                    bytes_inner=dslash_bytes(V, info["cols_dslash_inner"], wl["prec"], info["n_dslash_inner"]),
+                    bytes_inner=(schur_bytes if eo else dslash_bytes)(V, info["cols_dslash_inner"], wl["prec"],
+                                                                      info["n_dslash_inner"]),
                     infos=infos)
 
     last = None
@@ -507,16 +527,17 @@ def gb300_arm(args, wl, rank, world, local_rank):
             Xc = Xdev[c["c0"]:c["c0"] + c["L"]]
             ks, ls = [kap_s[si] for si in idx], [L_s[si] for si in idx]
             lat.block_solve_batched(Bc, ks, ls, method="bicggr", prec="fp64", tol=TOL, maxiter=1, out=Xc,
-                                    raise_on_fail=False)
+                                    raise_on_fail=False, eo=eo)
             (X, inf64), ms = timed(lambda: lat.block_solve_batched(Bc, ks, ls, method="bicggr", prec="fp64",
                                                                    tol=TOL, maxiter=MAXITER, out=Xc,
-                                                                   raise_on_fail=False))
+                                                                   raise_on_fail=False, eo=eo))
             check(inf64, "FP64 solve at the same split")
             tot += ms
             its += [i["iterations"] for i in inf64]
             if first is None:
                 first = inf64[0]["iterations"]
-        fp64["same_split"] = dict(method="block BiCGGR, FP64, the same block systems (one batched solve per case)",
+        fp64["same_split"] = dict(method="block BiCGGR, FP64, the same block systems (one batched solve per case)"
+                                  + (", even-odd form" if eo else ""),
                                   rhs_per_s=Lt / (tot / 1e3), ms=round(tot, 1), iterations_first_system=first,
                                   iterations_max=max(its))
         if args.fp64_full:
@@ -536,7 +557,7 @@ def gb300_arm(args, wl, rank, world, local_rank):
             fp64["full_blocks"] = dict(method="block BiCGGR, FP64, each case one block (the paper's method)",
                                        rhs_per_s=Lt / (tot / 1e3), cases=per)
 
-    return dict(total_ms=total_ms, per_step_ms=per_step_ms, agg=agg, clocks=clk, e2e_ms=e2e_ms / n_e2e,
+    return dict(total_ms=total_ms, per_step_ms=per_step_ms, agg=agg, clocks=clk, e2e_ms=e2e_ms / n_e2e, eo=eo,
                 h2d=h2d, d2h=d2h, fp64=fp64, V=V, per_case=per_case,
                 batched=dict(systems=len(L_s), block=wl.get("block"), columns=Lt))
 
@@ -555,6 +576,9 @@ def main():
                     help="with --impl reference: time the oracle's full solve of the first block system")
     ap.add_argument("--cpu-procs", type=int, default=None,
                     help="with --impl reference: at most this many oracle processes")
+    ap.add_argument("--eo", dest="eo", action="store_true", default=None,
+                    help="solve through the even-odd Schur system (default: the workload's)")
+    ap.add_argument("--no-eo", dest="eo", action="store_false")
     ap.add_argument("--delta", type=float, default=None,
                     help="residual-replacement threshold (default: the workload's)")
     ap.add_argument("--update", choices=["fp64", "df64"], default=None,
@@ -629,7 +653,8 @@ def main():
     hbm, peak_kind = measured_peaks()
     achieved = (agg["bytes_inner"] / agg["n_inner"]) / ((agg["t_inner"] / agg["n_inner"]) / 1e3) / 1e9 \
         if agg["n_inner"] else None
-    traffic = ncu_traffic(wl["prec"], agg["bytes_inner"] / agg["n_inner"] if agg["n_inner"] else None)
+    traffic = ncu_traffic(wl["prec"] + ("_eo" if r["eo"] else ""),
+                          agg["bytes_inner"] / agg["n_inner"] if agg["n_inner"] else None)
     line = {
         "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -638,7 +663,10 @@ def main():
         "config": {"workload": wl["desc"], "lattice": "x".join(map(str, wl["dims"])),
                    "rhs_per_step": total_rhs_per_step, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 and a 256 MB L2 flush before every timed step"},
-        "roofline": {"bound": "hbm", "kernel": f"k_dslash_pair<{wl['prec'].upper()}> (inner operator, all columns)",
+        "roofline": {"bound": "hbm",
+                     "kernel": (f"k_eo_pair<{wl['prec'].upper()}> (inner Schur operator, both half-lattice launches)"
+                                if r["eo"] else f"k_dslash_staged / k_dslash_pair<{wl['prec'].upper()}> "
+                                                "(inner operator, all columns)"),
                      "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": (achieved / hbm) if achieved else None, "peak_kind": peak_kind,
                      "traffic": traffic, "launches": agg["n_inner"],

@@ -120,6 +120,18 @@ bk_status bk_unpack(bk_ctx* ctx, const void* Xd, double* X, int L, bk_prec prec,
 bk_status bk_dslash_dev(bk_ctx* ctx, const double* kappa, const void* Xd, void* Yd, int L,
                         bk_prec prec, void* stream);
 
+/* Even-odd Schur operator (not in the paper; see bk_solve_params.eo):
+ * Y_e = M X_e = X_e - kappa_j^2 A_ee^-1 H_eo A_oo^-1 H_oe X_e on the even
+ * sites, Y = 0 on the odd sites; the odd sites of X are ignored.  X, Y:
+ * canonical FP64 device blocks of L columns, computed in prec (BK_FP64,
+ * BK_DF64, BK_FP32, BK_FP16; library workspace).  kappa: host array of L
+ * values; in BK_FP32 / BK_FP16 columns 2p and 2p + 1 must share kappa (a
+ * packed pair takes one A^-1 table).  Needs an even Lx.  Errors: NO_GAUGE,
+ * INVALID_ARG (odd Lx; a pair with two kappas; a singular site term
+ * 1 - kappa C at some kappa), CUDA.                                       */
+bk_status bk_schur_dslash(bk_ctx* ctx, const double* kappa, const double* X, double* Y, int L,
+                          bk_prec prec, void* stream);
+
 /* Same operator on canonical FP64 device blocks X -> Y, computed in prec:
  * packs X, applies the operator, unpacks into Y (library workspace).
  * Both operator calls accept BK_DF64 (blocks in the BK_FP64 layout).      */
@@ -296,6 +308,26 @@ typedef struct bk_solve_params {
                               recurrences from an FP64 true residual (at most
                               20 times per system) instead of stopping.
                               0 = the plain method                            */
+    int eo;                /* even-odd (Schur complement) form (not in the
+                              paper; a reordering of the same system by site
+                              parity; needs an even Lx, deflate = 0 and
+                              rtilde_mode 0 or 1): 1 = iterate the method on
+                              M x_e = b^_e over the even sites, M = 1 -
+                              kappa^2 A_ee^-1 H_eo A_oo^-1 H_oe with A = 1 -
+                              kappa C the site term and H the hopping sum
+                              (A^-1 per kappa, FP64 Gauss-Jordan per site,
+                              cached per clover term), b^_e = A_ee^-1 (b_e +
+                              kappa H_eo A_oo^-1 b_o); then x_o = A_oo^-1 (b_o
+                              + kappa H_oe x_e).  Each system stops when its
+                              Schur residual is below tol ||b_j|| / a, a >=
+                              max_n ||A(n)||, which bounds the full residual
+                              (= A_ee times the Schur one) by tol ||b_j||; the
+                              reported true residual is that of the full
+                              system, in FP64, and a system whose full
+                              residual still exceeds tol is not converged.
+                              Only the even sites of an X_0 are used.  The
+                              iteration counts and residual histories are
+                              those of the Schur system.  0 = the full system */
 } bk_solve_params;
 
 typedef struct bk_solve_info {

@@ -22,7 +22,7 @@ METHOD = {"bicgstab": 0, "bicggr": 1}
 # Every symbol include/bkrylov.h declares.
 EXPORTED = [
     "bk_status_string", "bk_last_error", "bk_create", "bk_destroy", "bk_upload_gauge",
-    "bk_build_clover", "bk_field_bytes", "bk_pack", "bk_unpack", "bk_dslash_dev", "bk_dslash",
+    "bk_build_clover", "bk_field_bytes", "bk_pack", "bk_unpack", "bk_dslash_dev", "bk_dslash", "bk_schur_dslash",
     "bk_gamma5", "bk_block_gram", "bk_block_xmy", "bk_small_solve", "bk_block_solve",
     "bk_block_solve_batched", "bk_dot", "bk_gauge_force", "bk_block_gram_noalloc", "bk_dslash_multi",
     "bk_set_clover", "bk_probe_peak", "bk_kappa_grad",
@@ -36,7 +36,7 @@ class SolveParams(C.Structure):
         ("reliable_delta", C.c_double), ("x0_given", C.c_int), ("buffers_on_host", C.c_int),
         ("rtilde_mode", C.c_int), ("seed", C.c_uint64), ("rtilde", C.c_void_p), ("restart_on_update", C.c_int),
         ("orth_mode", C.c_int), ("record_history", C.c_int),
-        ("timing", C.c_int), ("update_prec", C.c_int), ("deflate", C.c_int),
+        ("timing", C.c_int), ("update_prec", C.c_int), ("deflate", C.c_int), ("eo", C.c_int),
     ]
 
 
@@ -85,6 +85,7 @@ def lib():
         "bk_unpack": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, vp]),
         "bk_dslash_dev": (C.c_int, [vp, dp, vp, vp, C.c_int, C.c_int, vp]),
         "bk_dslash": (C.c_int, [vp, dp, vp, vp, C.c_int, C.c_int, vp]),
+        "bk_schur_dslash": (C.c_int, [vp, dp, vp, vp, C.c_int, C.c_int, vp]),
         "bk_gamma5": (C.c_int, [vp, vp, vp, C.c_int, vp]),
         "bk_block_gram": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, vp, vp]),
         "bk_block_xmy": (C.c_int, [vp, vp, vp, dp, vp, vp, C.c_int, C.c_int, vp]),

@@ -16,6 +16,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <vector>
 
 #include "bk_common.cuh"
@@ -119,6 +120,20 @@ struct bk_ctx {
     int force_variant = 0;  // BK_DSLASH_VARIANT=1..5: FP32/FP16 operator variant (4, 5: FP32 staged form),
                             // 128 threads, pair groups of 8, no tuning (tests the variants the tuner may pick)
     int force_prefetch = 0; // BK_DSLASH_PREFETCH=0..3: its prefetch mode (with BK_DSLASH_VARIANT)
+    // even-odd form: A^-1 = (1 - kappa C)^-1 per kappa (FP64 and FP32 tables), built
+    // on first use and dropped when the gauge field or the clover term changes
+    struct CInv {
+        DevBuf c64, c32;
+        double bound = 1.0;  // >= the spectral norm of A(n) at every site
+        ~CInv() {
+            c64.release();
+            c32.release();
+        }
+    };
+    std::map<unsigned long long, std::unique_ptr<CInv>> cinv;
+    DevBuf cinv_bound;
+    // even-odd solve and operator workspace
+    DevBuf eoB, eoX, eoR, eoBo, eoT64, eoT, eoS;
 };
 
 static bool wide(int prec) { return prec == BK_FP64 || prec == BK_DF64; }
@@ -184,11 +199,16 @@ extern "C" bk_status bk_create(const int dims[4], int device, bk_ctx** out) {
 extern "C" bk_status bk_destroy(bk_ctx* c) {
     if (!c) return BK_OK;
     cudaSetDevice(c->device);
-    DevBuf* bufs[] = {&c->U64, &c->U32, &c->C64, &c->C32, &c->Utmp, &c->s1, &c->s2, &c->part, &c->scal,
-                      &c->B64, &c->X64, &c->R64, &c->Xlo, &c->small, &c->spart, &c->stage,
-                      &c->colmap, &c->fscratch, &c->ynorm};
+    DevBuf* bufs[] = {&c->U64,   &c->U32,   &c->C64,   &c->C32,        &c->Utmp, &c->s1,  &c->s2,
+                      &c->part,  &c->scal,  &c->B64,   &c->X64,        &c->R64,  &c->Xlo, &c->small,
+                      &c->spart, &c->stage, &c->colmap, &c->fscratch,  &c->ynorm, &c->cinv_bound,
+                      &c->eoB,   &c->eoX,   &c->eoR,   &c->eoBo,       &c->eoT64, &c->eoT, &c->eoS};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : c->blk) b.release();
+    for (auto& kv : c->cinv) {
+        kv.second->c64.release();
+        kv.second->c32.release();
+    }
     c->rb_host.release();
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     delete c;
@@ -209,6 +229,7 @@ extern "C" bk_status bk_upload_gauge(bk_ctx* c, const double* U, int on_device, 
     if (!on_device) BK_CUDA_TRY(cudaStreamSynchronize(st));
     c->has_gauge = true;
     c->has_clover = false;
+    c->cinv.clear();
     return BK_OK;
 }
 
@@ -223,6 +244,7 @@ extern "C" bk_status bk_build_clover(bk_ctx* c, double csw, void* stream) {
                                (cudaStream_t)stream));
     c->csw = csw;
     c->has_clover = true;
+    c->cinv.clear();
     return BK_OK;
 }
 
@@ -358,6 +380,206 @@ static bk_status dslash_fields(bk_ctx* c, int prec, const double* kappa, Field x
         op.prefetch = it->second.prefetch;
     }
     return launch_dslash(prec, op, st);
+}
+
+// ---------------------------------------------------------------- even-odd form
+//
+// The A^-1 tables of one kappa (built once per clover term).  A singular
+// site block is an error: the even-odd form does not exist at that kappa.
+static bk_status clover_inverse(bk_ctx* c, double kappa, cudaStream_t st, const bk_ctx::CInv** out) {
+    unsigned long long key;
+    memcpy(&key, &kappa, sizeof(key));
+    auto it = c->cinv.find(key);
+    if (it == c->cinv.end()) {
+        std::unique_ptr<bk_ctx::CInv> ci(new bk_ctx::CInv());
+        BK_TRY(ci->c64.ensure((size_t)36 * c->V * sizeof(double2)));
+        BK_TRY(ci->c32.ensure((size_t)c->V * BK_CLOV32_F4 * sizeof(float4)));
+        BK_TRY(c->cinv_bound.ensure(2 * sizeof(unsigned long long)));
+        BK_CUDA_TRY(cudaMemsetAsync(c->cinv_bound.p, 0, 2 * sizeof(unsigned long long), st));
+        BK_TRY(launch_clover_inverse(c->C64.as<double2>(), kappa, ci->c64.as<double2>(), ci->c32.as<float4>(), c->V,
+                                     c->cinv_bound.as<unsigned long long>(), st));
+        unsigned long long hb[2];
+        BK_CUDA_TRY(cudaMemcpyAsync(hb, c->cinv_bound.p, sizeof(hb), cudaMemcpyDeviceToHost, st));
+        BK_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hb[1] != 0) {
+            bk_set_error("even-odd form: the site term 1 - kappa C is singular at %llu blocks (kappa = %g)",
+                         (unsigned long long)hb[1], kappa);
+            return BK_ERR_INVALID_ARG;
+        }
+        double nb;
+        memcpy(&nb, &hb[0], sizeof(nb));
+        ci->bound = std::max(1.0, nb);
+        it = c->cinv.emplace(key, std::move(ci)).first;
+    }
+    *out = it->second.get();
+    return BK_OK;
+}
+
+// FP32 / FP16 even-odd launch shape, tuned once per (precision, column count)
+// on the caller's data (mode 1, the half of the Schur operator that writes
+// only the temporary): 256 or 128 threads, or (FP32) the staged form with 2
+// or 3 ring slots; pair groups of 16 or all pairs.
+static bk_status eo_shape(bk_ctx* c, int prec, EoOp op, cudaStream_t st) {
+    const long long key = (1LL << 44) | ((long long)prec << 40) | op.ncol;
+    auto it = c->shapes.find(key);
+    if (it == c->shapes.end()) {
+        bk_ctx::Shape best{0, 2, 0, 0};
+        if (c->autotune) {
+            cudaEvent_t e0, e1;
+            BK_CUDA_TRY(cudaEventCreate(&e0));
+            BK_CUDA_TRY(cudaEventCreate(&e1));
+            float best_ms = 1e30f;
+            const int npl = (op.ncol + 1) / 2;
+            for (int v : {1, 2, 4, 5})
+                for (int grp : {16, 0}) {
+                    if (grp > 0 && grp >= npl) continue;
+                    if (v >= 4 && prec != BK_FP32) continue;  // staged forms: FP32 only
+                    op.variant = v;
+                    op.group = grp;
+                    bk_status r = launch_eo(prec, op, st);
+                    if (r == BK_OK) r = (cudaEventRecord(e0, st) == cudaSuccess) ? BK_OK : BK_ERR_CUDA;
+                    if (r == BK_OK) r = launch_eo(prec, op, st);
+                    if (r == BK_OK) r = launch_eo(prec, op, st);
+                    if (r == BK_OK) r = (cudaEventRecord(e1, st) == cudaSuccess) ? BK_OK : BK_ERR_CUDA;
+                    float ms = 0.f;
+                    if (r == BK_OK && cudaEventSynchronize(e1) == cudaSuccess &&
+                        cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+                        best_ms = ms;
+                        best = {0, v, grp, 0};
+                    }
+                    if (r != BK_OK) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return r;
+                    }
+                }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (c->verbose)
+                fprintf(stderr, "[bkrylov] tuned even-odd operator prec=%d ncol=%d: variant=%d group=%d\n", prec,
+                        op.ncol, best.variant, best.group);
+        }
+        it = c->shapes.emplace(key, best).first;
+    }
+    return BK_OK;
+}
+
+// y_e = M x_e (residual: y_e = b_e - M x_e) on half-lattice blocks of one
+// storage precision, t an odd-parity temporary of the same layout; ci[j]
+// the A^-1 table (of prec) of column col0 + j.
+static bk_status schur_fields(bk_ctx* c, int prec, const double* kappa, const void* const* ci, Field x, Field y,
+                              Field b, Field t, int col0, int ncol, int residual, cudaStream_t st) {
+    EoOp op;
+    memset(&op, 0, sizeof(op));
+    op.U = gauge_ptr(c, prec);
+    op.Ci = ci;
+    for (int mu = 0; mu < 4; ++mu) op.dims[mu] = c->dims[mu];
+    op.V = c->V;
+    op.col0 = col0;
+    op.ncol = ncol;
+    op.kappa = kappa;
+    op.hop = 1;
+    // t_o = A_oo^-1 H_oe x_e
+    op.x = x;
+    op.xs = x;
+    op.y = t;
+    op.b = t;
+    op.par = 1;
+    op.mode = 1;
+    op.variant = 2;
+    if (!wide(prec) && c->force_variant) {  // BK_DSLASH_VARIANT: 1, 2 (3 -> 2), 4, 5 (FP32); groups of 8
+        op.variant = c->force_variant == 3 ? 2 : c->force_variant;
+        op.group = 8;
+    } else if (!wide(prec)) {
+        BK_TRY(eo_shape(c, prec, op, st));
+        const long long key = (1LL << 44) | ((long long)prec << 40) | ncol;
+        op.variant = c->shapes[key].variant;
+        op.group = c->shapes[key].group;
+    }
+    BK_TRY(launch_eo(prec, op, st));
+    // y_e = x_e - kappa^2 A_ee^-1 H_eo t_o   (or b_e minus that)
+    op.x = t;
+    op.xs = x;
+    op.y = y;
+    op.b = b;
+    op.par = 0;
+    op.mode = 2;
+    op.residual = residual;
+    return launch_eo(prec, op, st);
+}
+
+// one-column-per-thread even-odd step in FP64 (mode 3: y = A^-1 (xs + kappa H x))
+static bk_status eo_prep(bk_ctx* c, const double* kappa, const void* const* ci, Field x, Field xs, Field y, int par,
+                         int hop, int col0, int ncol, cudaStream_t st) {
+    EoOp op;
+    memset(&op, 0, sizeof(op));
+    op.U = gauge_ptr(c, BK_FP64);
+    op.Ci = ci;
+    for (int mu = 0; mu < 4; ++mu) op.dims[mu] = c->dims[mu];
+    op.V = c->V;
+    op.col0 = col0;
+    op.ncol = ncol;
+    op.kappa = kappa;
+    op.x = x;
+    op.xs = xs;
+    op.y = y;
+    op.b = y;
+    op.par = par;
+    op.mode = 3;
+    op.hop = hop;
+    return launch_eo(BK_FP64, op, st);
+}
+
+extern "C" bk_status bk_schur_dslash(bk_ctx* c, const double* kappa, const double* X, double* Y, int L, bk_prec prec,
+                                     void* stream) {
+    BK_CHECK_ARG(c && kappa && X && Y && L >= 1 && valid_op_prec(prec), "bad argument to bk_schur_dslash");
+    BK_CHECK_ARG((c->dims[0] & 1) == 0, "bk_schur_dslash: the even-odd form needs an even extent in x");
+    if (!c->has_gauge || !c->has_clover) {
+        bk_set_error("operator needs bk_upload_gauge and bk_build_clover first");
+        return BK_ERR_NO_GAUGE;
+    }
+    if (!wide(prec))  // packed pairs share one A^-1 table: the columns of a pair share kappa
+        for (int j = 0; j + 1 < L; j += 2)
+            BK_CHECK_ARG(kappa[j] == kappa[j + 1],
+                         "bk_schur_dslash in FP32 / FP16: columns 2p and 2p + 1 must share kappa");
+    BK_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int sp = storage_prec(prec);
+    const int Vh = c->V / 2;
+    const size_t full = field_bytes(L, c->V, BK_FP64), h64 = field_bytes(L, Vh, BK_FP64), hp = field_bytes(L, Vh, sp);
+    BK_TRY(c->s1.ensure(full));
+    BK_TRY(c->s2.ensure(full));
+    BK_TRY(c->eoS.ensure(3 * h64 + 3 * hp + 6 * 256));
+    auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    char* q = c->eoS.as<char>();
+    Field xe = make_field(q, L, Vh, BK_FP64), xo = make_field(q + al(h64), L, Vh, BK_FP64),
+          ye = make_field(q + 2 * al(h64), L, Vh, BK_FP64);
+    char* q2 = q + 3 * al(h64);
+    Field xp = make_field(q2, L, Vh, sp), tp = make_field(q2 + al(hp), L, Vh, sp),
+          yp = make_field(q2 + 2 * al(hp), L, Vh, sp);
+    Field xf = make_field(c->s1.p, L, c->V, BK_FP64), yf = make_field(c->s2.p, L, c->V, BK_FP64);
+    BK_TRY(pack_block(BK_FP64, X, xf, L, st));
+    BK_TRY(launch_eo_split(xf, xe, xo, c->dims, st));
+    const int Lp = L + (L & 1);
+    std::vector<double> k((size_t)Lp, 0.0);
+    std::vector<const void*> ci((size_t)Lp);
+    for (int j = 0; j < L; ++j) {
+        const bk_ctx::CInv* t;
+        BK_TRY(clover_inverse(c, kappa[j], st, &t));
+        k[j] = kappa[j];
+        ci[j] = wide(prec) ? t->c64.p : t->c32.p;
+    }
+    if (L & 1) ci[L] = ci[L - 1];
+    if (sp == BK_FP64) {
+        BK_TRY(schur_fields(c, prec, k.data(), ci.data(), xe, ye, xe, xo, 0, Lp, 0, st));
+    } else {
+        BK_TRY(launch_cast(BK_FP64, xe, sp, xp, npairs(L), st));
+        BK_TRY(schur_fields(c, prec, k.data(), ci.data(), xp, yp, xp, tp, 0, Lp, 0, st));
+        BK_TRY(launch_cast(sp, yp, BK_FP64, ye, npairs(L), st));
+    }
+    BK_CUDA_TRY(cudaMemsetAsync(xo.data, 0, h64, st));
+    BK_TRY(launch_eo_merge(ye, xo, yf, c->dims, st));
+    return launch_unpack(BK_FP64, yf, nullptr, 0, Y, L, st);
 }
 
 extern "C" bk_status bk_dslash_dev(bk_ctx* c, const double* kappa, const void* Xd, void* Yd, int L, bk_prec prec,
@@ -562,6 +784,15 @@ struct Solve {
     double* rfac = nullptr;           // R per system, complex FP64 (packed like the L x L matrices)
     const double* Bcaller = nullptr;  // the caller's B (re-read for the final true residual)
     Field B64, X64, R64, Xlo, R, Rt, Pb, Vb, Wb, Ub, Yb, Tb, Zb, Ptmp;
+    // even-odd form: the iteration blocks hold the even sites (V = Vf / 2) and
+    // solve M x_e = b^_e; Bf, Xf, Rf are full-lattice FP64 blocks (the caller's
+    // B, the solution, its true residual), Bo the odd sites of B, T64 / Tp
+    // odd-parity temporaries of the Schur operator; ci64 / cip the A^-1
+    // tables of each column's kappa (FP64 / inner precision)
+    bool eo = false;
+    int Vf = 0;
+    Field Bf, Xf, Rf, Bo, T64, Tp;
+    std::vector<const void*> ci64, cip;
     bool orth = false;
     int upd_prec = BK_FP64;  // arithmetic of the residual replacements
     double* ynorm = nullptr;  // per-block partial sums of ||R_j||^2 from the R update
@@ -614,7 +845,14 @@ struct Solve {
             BK_TRY(event_pair(ev));
             BK_CUDA_TRY(cudaEventRecord(c->events[ev], st));
         }
-        BK_TRY(dslash_fields(c, prec, kcol.data() + col0, x, y, b, col0, ncol, residual, st));
+        if (eo) {
+            const bool w = prec == BK_FP64 || prec == BK_DF64;
+            BK_TRY(schur_fields(c, prec, kcol.data() + col0, (w ? ci64 : cip).data() + col0, x, y, b, w ? T64 : Tp,
+                                col0, ncol, residual, st));
+            launches += 1;
+        } else {
+            BK_TRY(dslash_fields(c, prec, kcol.data() + col0, x, y, b, col0, ncol, residual, st));
+        }
         if (prm->timing) {
             BK_CUDA_TRY(cudaEventRecord(c->events[ev + 1], st));
             ev_pending.push_back({ev, prec == P});
@@ -762,6 +1000,25 @@ struct Solve {
 
     bk_status setup(const double* Bc, const double* Xc) {
         const size_t fb64 = field_bytes(Lt, V, BK_FP64), fbp = field_bytes(Lt, V, P);
+        if (eo) {
+            const size_t ff = field_bytes(Lt, Vf, BK_FP64);
+            BK_TRY(c->eoB.ensure(ff));
+            BK_TRY(c->eoX.ensure(ff));
+            BK_TRY(c->eoR.ensure(ff));
+            BK_TRY(c->eoBo.ensure(fb64));
+            BK_TRY(c->eoT64.ensure(fb64));
+            Bf = make_field(c->eoB.p, Lt, Vf, BK_FP64);
+            Xf = make_field(c->eoX.p, Lt, Vf, BK_FP64);
+            Rf = make_field(c->eoR.p, Lt, Vf, BK_FP64);
+            Bo = make_field(c->eoBo.p, Lt, V, BK_FP64);
+            T64 = make_field(c->eoT64.p, Lt, V, BK_FP64);
+            if (P == BK_FP64) {
+                Tp = T64;
+            } else {
+                BK_TRY(c->eoT.ensure(fbp));
+                Tp = make_field(c->eoT.p, Lt, V, P);
+            }
+        }
         BK_TRY(c->B64.ensure(fb64));
         BK_TRY(c->X64.ensure(fb64));
         BK_TRY(c->R64.ensure(fb64));
@@ -845,7 +1102,7 @@ struct Solve {
         info_g_h = info_a_h + nsys;
         zbad_h = info_a_h + 2 * nsys;
         BK_CUDA_TRY(cudaMemsetAsync(info_a, 0, 3 * nsys * sizeof(int), st));
-        const size_t pb = std::max(gram_partial_bytes(part, V), coldot_partial_bytes(Lt, 3, V));
+        const size_t pb = std::max(gram_partial_bytes(part, V), coldot_partial_bytes(Lt, 3, std::max(V, Vf)));
         BK_TRY(c->spart.ensure(pb));
         partial = c->spart.as<double>();
         if (method == BK_BICGSTAB) {  // residual norms fused into the R update
@@ -857,10 +1114,15 @@ struct Solve {
 
         // B, X0 into the FP64 device layout (padding columns zero)
         Bcaller = Bc;
-        BK_TRY(put_caller_block(Bc, B64));
+        BK_TRY(put_caller_block(Bc, eo ? Bf : B64));
         {
-            Field a[1] = {B64}, b[1] = {B64};
-            BK_TRY(coldot(BK_FP64, 1, a, b, rn, 0, Lt));
+            Field a[1] = {eo ? Bf : B64}, b[1] = {eo ? Bf : B64};
+            if (eo) {  // the norms of the full right-hand side
+                launches += 2;
+                BK_TRY(launch_coldot(BK_FP64, 1, a, b, 0, Lt, rn, Lt, partial, Vf, st));
+            } else {
+                BK_TRY(coldot(BK_FP64, 1, a, b, rn, 0, Lt));
+            }
             BK_TRY(readback());
             for (int s = 0; s < nsys; ++s)
                 for (int j = part.col0[s]; j < part.col0[s] + part.L[s]; ++j) {
@@ -878,6 +1140,13 @@ struct Solve {
                 }
             bnorm_orig = bnorm;
         }
+        if (eo) {
+            // b^_e = A_ee^-1 (b_e + kappa H_eo A_oo^-1 b_o)  (X64 holds b_e for a moment)
+            BK_TRY(launch_eo_split(Bf, X64, Bo, c->dims, st));
+            BK_TRY(eo_prep(c, kcol.data(), ci64.data(), Bo, Bo, T64, 1, 0, 0, Lt, st));
+            BK_TRY(eo_prep(c, kcol.data(), ci64.data(), T64, X64, B64, 0, 1, 0, Lt, st));
+            launches += 3;
+        }
         if (deflate) {
             // B = Q R: the systems now solve D Y = Q, whose columns have unit norm
             BK_TRY(orthonormalise());
@@ -892,7 +1161,13 @@ struct Solve {
             launches++;
         }
         if (prm->x0_given) {
-            BK_TRY(put_caller_block(Xc, X64));
+            if (eo) {  // the even sites of X_0 (the odd ones follow from them)
+                BK_TRY(put_caller_block(Xc, Xf));
+                BK_TRY(launch_eo_split(Xf, X64, T64, c->dims, st));
+                launches++;
+            } else {
+                BK_TRY(put_caller_block(Xc, X64));
+            }
             Field a[1] = {X64}, b[1] = {X64};
             BK_TRY(coldot(BK_FP64, 1, a, b, rn, 0, Lt));
             BK_TRY(readback());
@@ -1029,7 +1304,7 @@ struct Solve {
     // dcol_h[j]; padding columns are zeroed.  Host blocks are staged through
     // a bounded device buffer, a chunk of columns at a time.
     bk_status put_caller_block(const double* src, Field dst) {
-        const size_t colb = (size_t)V * 12 * sizeof(double2);
+        const size_t colb = (size_t)Vf * 12 * sizeof(double2);
         if (!prm->buffers_on_host) {
             BK_TRY(launch_pack(BK_FP64, src, Lu, dcol, 0, dst, st));
             launches++;
@@ -1053,7 +1328,7 @@ struct Solve {
     }
     // The solution into the caller's canonical block (device or host).
     bk_status get_caller_block(Field src, double* dst) {
-        const size_t colb = (size_t)V * 12 * sizeof(double2);
+        const size_t colb = (size_t)Vf * 12 * sizeof(double2);
         if (!prm->buffers_on_host) {
             launches++;
             return launch_unpack(BK_FP64, src, dcol, 0, dst, Lu, st);
@@ -1071,7 +1346,7 @@ struct Solve {
     }
     // staging chunk: columns of at most 1 GiB in all
     int stage_cols() const {
-        const size_t colb = (size_t)V * 12 * sizeof(double2);
+        const size_t colb = (size_t)Vf * 12 * sizeof(double2);
         return (int)std::max<size_t>(1, std::min<size_t>((size_t)Lu, ((size_t)1 << 30) / colb));
     }
 
@@ -1406,7 +1681,7 @@ struct Solve {
         // that converged on an FP64 residual replacement (mixed precision)
         sysmask need = 0;
         for (int s = 0; s < nsys; ++s)
-            if (!res_known[s] || deflate) {
+            if (!res_known[s] || deflate || eo) {
                 need |= 1ull << s;
                 mv64[s]++;
             }
@@ -1434,13 +1709,33 @@ struct Solve {
             bnorm = bnorm_orig;
             launches += 2;
         }
-        for (const auto& cr : col_runs(need)) BK_TRY(dslash(BK_FP64, X64, R64, B64, cr.first, cr.second, 1));
-        BK_TRY(norms_runs(BK_FP64, R64, need));
-        BK_TRY(get_caller_block(X64, Xc));
+        if (eo) {
+            // x_o = A_oo^-1 (b_o + kappa H_oe x_e); the full solution and the FP64
+            // true residual of the original (full-lattice) system
+            BK_TRY(eo_prep(c, kcol.data(), ci64.data(), X64, Bo, T64, 1, 1, 0, Lt, st));
+            BK_TRY(launch_eo_merge(X64, T64, Xf, c->dims, st));
+            launches += 2;
+            for (const auto& cr : col_runs(need)) {
+                BK_TRY(dslash_fields(c, BK_FP64, kcol.data() + cr.first, Xf, Rf, Bf, cr.first, cr.second, 1, st));
+                Field a[1] = {Rf};
+                BK_TRY(launch_coldot(BK_FP64, 1, a, a, cr.first, cr.second, rn, Lt, partial, Vf, st));
+                launches += 3;
+                n_dslash++;
+            }
+            BK_TRY(get_caller_block(Xf, Xc));
+        } else {
+            for (const auto& cr : col_runs(need)) BK_TRY(dslash(BK_FP64, X64, R64, B64, cr.first, cr.second, 1));
+            BK_TRY(norms_runs(BK_FP64, R64, need));
+            BK_TRY(get_caller_block(X64, Xc));
+        }
         BK_TRY(readback());
         for (int s = 0; s < nsys; ++s)
             if ((need >> s) & 1u)
                 for (int j = part.col0[s]; j < part.col0[s] + part.L[s]; ++j) true_res[j] = rel(j);
+        if (eo)  // the Schur residual bounds the full one; a system is converged only if the full one holds
+            for (int s = 0; s < nsys; ++s)
+                for (int j = part.col0[s]; j < part.col0[s] + part.L[s]; ++j)
+                    if (done[s] == 1 && !(true_res[j] <= prm->tol)) done[s] = 3;
         return BK_OK;
     }
 };
@@ -1458,6 +1753,9 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
     BK_CHECK_ARG(prm->rtilde_mode >= 0 && prm->rtilde_mode <= 2, "rtilde_mode must be 0, 1 or 2");
     BK_CHECK_ARG(prm->rtilde_mode != 2 || prm->rtilde, "rtilde_mode 2 needs the rtilde block");
     BK_CHECK_ARG(!prm->deflate || !prm->x0_given, "deflate needs X_0 = 0 (x0_given = 0)");
+    BK_CHECK_ARG(!prm->eo || !prm->deflate, "eo and deflate cannot be combined");
+    BK_CHECK_ARG(!prm->eo || prm->rtilde_mode != 2, "eo needs rtilde_mode 0 or 1");
+    BK_CHECK_ARG(!prm->eo || (c && (c->dims[0] & 1) == 0), "eo needs an even extent in x");
     int Lu = 0;
     for (int s = 0; s < nsys; ++s) {
         BK_CHECK_ARG(Ls[s] >= 1 && Ls[s] <= 128, "every system needs 1 <= L <= 128");
@@ -1475,7 +1773,9 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
     S.prm = prm;
     S.st = st;
     S.nsys = nsys;
-    S.V = c->V;
+    S.eo = prm->eo != 0;
+    S.Vf = c->V;
+    S.V = S.eo ? c->V / 2 : c->V;
     S.P = prm->prec;
     S.method = prm->method;
     S.mixed = prm->prec != BK_FP64;
@@ -1509,6 +1809,22 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
     S.deflate = prm->deflate != 0;
     S.tol_s.assign(nsys, prm->tol);
     S.ndefl.assign(nsys, 0);
+    if (S.eo) {
+        // A^-1 tables per system kappa (padding columns take their system's);
+        // the Schur residual is at most ||A_ee|| times smaller than the full
+        // one, so each system stops at tol / (a bound on ||A_ee||)
+        S.ci64.assign(Lt, nullptr);
+        S.cip.assign(Lt, nullptr);
+        for (int s = 0; s < nsys; ++s) {
+            const bk_ctx::CInv* t;
+            BK_TRY(clover_inverse(c, kappa[s], st, &t));
+            for (int j = S.part.col0[s]; j < S.part.col0[s + 1]; ++j) {
+                S.ci64[j] = t->c64.p;
+                S.cip[j] = S.P == BK_FP64 ? t->c64.p : t->c32.p;
+            }
+            S.tol_s[s] = prm->tol / t->bound;
+        }
+    }
 
     // host buffers (buffers_on_host) are copied in and out a chunk of
     // columns at a time inside setup() and finish()

@@ -10,6 +10,11 @@
 bk_status launch_gauge_convert(const double* Uin_dev, double2* U64, float4* U32, int V, cudaStream_t st);
 bk_status launch_clover_build(const double2* U64, double2* C64, float4* C32, const int dims[4], double csw,
                               cudaStream_t st);
+// Even-odd form: A(n)^-1 = (1 - kappa C(n))^-1 for one kappa, stored like the
+// clover (FP64 [36][V], FP32 packed pairs); bound[0] = the largest infinity
+// norm of A's chiral blocks (as double bits), bound[1] += singular blocks.
+bk_status launch_clover_inverse(const double2* C64, double kappa, double2* Ci64, float4* Ci32, int V,
+                                unsigned long long* bound, cudaStream_t st);
 
 // ---------------------------------------------------------------- dslash.cu
 struct DslashOp {
@@ -31,6 +36,28 @@ struct DslashOp {
                            // a loop, each prefetching the next hop's rows into L1
 };
 bk_status launch_dslash(int prec, const DslashOp& op, cudaStream_t st);
+
+// Even-odd operators on half-lattice blocks (site n at index n >> 1; Lx even).
+// Output sites have parity par; x holds the other parity.
+//   mode 1: y = A^-1 H x;   mode 2: y = xs - kappa^2 A^-1 H x (residual: b - that);
+//   mode 3 (FP64 / DF64 only): y = A^-1 (xs + kappa H x), or A^-1 xs with hop = 0.
+// Ci[j]: the A^-1 table (precision of the op) of column col0 + j's kappa.
+struct EoOp {
+    Field x, xs, y, b;
+    const void* U;
+    const void* const* Ci;
+    int dims[4];
+    int V;  // full-lattice sites
+    int col0, ncol;
+    int par, mode, hop, residual;
+    const double* kappa;  // kappa of column col0 + j
+    int variant, group;   // FP32 / FP16: 1 = 256 threads (255 registers), 2 = 128 (170); FP32 4 / 5 =
+                          // staged, 2 / 3 ring slots; pair groups of `group` pairs (0: all)
+};
+bk_status launch_eo(int prec, const EoOp& op, cudaStream_t st);
+// FP64 full-lattice block <-> its even and odd half-lattice blocks (same columns)
+bk_status launch_eo_split(Field full, Field ev, Field od, const int dims[4], cudaStream_t st);
+bk_status launch_eo_merge(Field ev, Field od, Field full, const int dims[4], cudaStream_t st);
 
 // canonical FP64 columns <-> device layout.  Canonical column j of the chunk
 // (ncan columns starting at canon) is device column dcol[j] (dcol a device

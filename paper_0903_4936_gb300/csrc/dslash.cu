@@ -224,7 +224,7 @@ __device__ __forceinline__ void link_mul(const float4* __restrict__ u4, const Ho
 }
 
 template <int P, int MU, int S>
-__device__ __forceinline__ void hop_pair(const DPairArgs& a, int nb, int p, const float4* __restrict__ link,
+__device__ __forceinline__ void hop_pair(const Field& x, int nb, int p, const float4* __restrict__ link,
                                          float2 nk, float2 pk, float2 (&ar)[12], float2 (&ai)[12]) {
     Hop h, w;
 #pragma unroll
@@ -234,7 +234,7 @@ __device__ __forceinline__ void hop_pair(const DPairArgs& a, int nb, int p, cons
         for (int sp = 0; sp < 4; ++sp) {
             // the t projector reads only two of the four spins
             if (MU == 3 && ((S > 0) != (sp < 2))) continue;
-            load_elem<P>(a.x, nb, 3 * sp + c, p, qr[3 * sp + c], qi[3 * sp + c]);
+            load_elem<P>(x, nb, 3 * sp + c, p, qr[3 * sp + c], qi[3 * sp + c]);
         }
         Hop hc;
         project_pair<MU, S>(qr, qi, hc, c);
@@ -244,7 +244,7 @@ __device__ __forceinline__ void hop_pair(const DPairArgs& a, int nb, int p, cons
         h.i[3 + c] = hc.i[3 + c];
     }
     if constexpr (P == BK_FP16) {  // the projection is linear: scale the 12 projected pairs
-        const float2 sc = pair_scale<P>(a.x, nb, p);
+        const float2 sc = pair_scale<P>(x, nb, p);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             h.r[k] = pmul(h.r[k], sc);
@@ -262,9 +262,9 @@ __device__ __forceinline__ void hop_dir_pair(const DPairArgs& a, const int (&co)
     const int nf = co[MU] == Lm - 1 ? n - (Lm - 1) * sm : n + sm;
     const int nb = co[MU] == 0 ? n + (Lm - 1) * sm : n - sm;
     // forward: (1 - gamma_mu) U_mu(n) x(n + mu)
-    hop_pair<P, MU, -1>(a, nf, p, a.U + ((size_t)MU * a.V + n) * BK_LINK32_F4, nk, pk, ar, ai);
+    hop_pair<P, MU, -1>(a.x, nf, p, a.U + ((size_t)MU * a.V + n) * BK_LINK32_F4, nk, pk, ar, ai);
     // backward: (1 + gamma_mu) U_mu(n - mu)^+ x(n - mu)
-    hop_pair<P, MU, +1>(a, nb, p, a.U + ((size_t)MU * a.V + nb) * BK_LINK32_F4, nk, pk, ar, ai);
+    hop_pair<P, MU, +1>(a.x, nb, p, a.U + ((size_t)MU * a.V + nb) * BK_LINK32_F4, nk, pk, ar, ai);
 }
 
 // out = q - kappa C q for one chiral 6x6 Hermitian block pair (see gauge.cu
@@ -388,14 +388,14 @@ __device__ __forceinline__ void hops_looped(const DPairArgs& a, const int (&co)[
         }
         const float4* link = a.U + ((size_t)mu * a.V + ((h & 1) ? nb : n)) * BK_LINK32_F4;
         switch (h) {
-            case 0: hop_pair<P, 0, -1>(a, nb, p, link, nk, pk, ar, ai); break;
-            case 1: hop_pair<P, 0, +1>(a, nb, p, link, nk, pk, ar, ai); break;
-            case 2: hop_pair<P, 1, -1>(a, nb, p, link, nk, pk, ar, ai); break;
-            case 3: hop_pair<P, 1, +1>(a, nb, p, link, nk, pk, ar, ai); break;
-            case 4: hop_pair<P, 2, -1>(a, nb, p, link, nk, pk, ar, ai); break;
-            case 5: hop_pair<P, 2, +1>(a, nb, p, link, nk, pk, ar, ai); break;
-            case 6: hop_pair<P, 3, -1>(a, nb, p, link, nk, pk, ar, ai); break;
-            default: hop_pair<P, 3, +1>(a, nb, p, link, nk, pk, ar, ai); break;
+            case 0: hop_pair<P, 0, -1>(a.x, nb, p, link, nk, pk, ar, ai); break;
+            case 1: hop_pair<P, 0, +1>(a.x, nb, p, link, nk, pk, ar, ai); break;
+            case 2: hop_pair<P, 1, -1>(a.x, nb, p, link, nk, pk, ar, ai); break;
+            case 3: hop_pair<P, 1, +1>(a.x, nb, p, link, nk, pk, ar, ai); break;
+            case 4: hop_pair<P, 2, -1>(a.x, nb, p, link, nk, pk, ar, ai); break;
+            case 5: hop_pair<P, 2, +1>(a.x, nb, p, link, nk, pk, ar, ai); break;
+            case 6: hop_pair<P, 3, -1>(a.x, nb, p, link, nk, pk, ar, ai); break;
+            default: hop_pair<P, 3, +1>(a.x, nb, p, link, nk, pk, ar, ai); break;
         }
     }
 }
@@ -792,17 +792,19 @@ __device__ __forceinline__ void load_link(const L* __restrict__ U, int mu, int s
     }
 }
 
-template <int P, int MU>
-__device__ __forceinline__ void hop_dir_col(const DColArgs<P>& a, const int (&co)[4], int n, int c,
+// HALF: the input x is a half-lattice (one parity) block, site n at index n >> 1
+template <int P, int MU, bool HALF = false, typename Args>
+__device__ __forceinline__ void hop_dir_col(const Args& a, const int (&co)[4], int n, int c,
                                             cx<typename Prec<P>::real> (&acc)[12]) {
     using R = typename Prec<P>::real;
     const int Lm = a.L[MU], sm = a.st[MU];
     const int nf = co[MU] == Lm - 1 ? n - (Lm - 1) * sm : n + sm;
     const int nb = co[MU] == 0 ? n + (Lm - 1) * sm : n - sm;
+    const int xf = HALF ? nf >> 1 : nf, xb = HALF ? nb >> 1 : nb;
     {   // forward: (1 - gamma_mu) U_mu(n) x(n + mu)
         cx<R> u[9], q[12], h[6], w[6];
         load_link(a.U, MU, n, a.V, u);
-        load_col<P>(a.x, nf, c, q);
+        load_col<P>(a.x, xf, c, q);
         project<MU, -1>(q, h);
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh)
@@ -818,7 +820,7 @@ __device__ __forceinline__ void hop_dir_col(const DColArgs<P>& a, const int (&co
     {   // backward: (1 + gamma_mu) U_mu(n - mu)^+ x(n - mu)
         cx<R> u[9], q[12], h[6], w[6];
         load_link(a.U, MU, nb, a.V, u);
-        load_col<P>(a.x, nb, c, q);
+        load_col<P>(a.x, xb, c, q);
         project<MU, +1>(q, h);
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh)
@@ -1142,6 +1144,450 @@ __global__ void k_gamma5(const double2* __restrict__ X, double2* __restrict__ Y,
     }
 }
 
+// ================================================================= even-odd (Schur complement) form
+//
+// Not in the paper: the same system reordered by site parity p(n) = (x + y +
+// z + t) mod 2.  With D = A - kappa H (A the site term of Eq. (wd-op), H the
+// hopping sum, which only joins sites of opposite parity), the even sites
+// solve M x_e = b^_e, M = 1 - kappa^2 A_ee^-1 H_eo A_oo^-1 H_oe.  A
+// half-lattice block holds the sites of one parity, site n at index n >> 1
+// (with Lx even, n and n + 1 have opposite parities and share n >> 1).  The
+// clover-inverse tables (A^-1 per kappa, see k_clover_inverse) and the links
+// stay indexed by the full site.
+
+__device__ __forceinline__ int eo_site(int h, int par, const int (&L)[4], int (&co)[4]) {
+    int n = 2 * h, r = n;
+    co[0] = r % L[0];
+    r /= L[0];
+    co[1] = r % L[1];
+    r /= L[1];
+    co[2] = r % L[2];
+    co[3] = r / L[2];
+    if (((co[0] + co[1] + co[2] + co[3]) & 1) != par) {  // co[0] is even, so co[0] + 1 < Lx
+        ++n;
+        ++co[0];
+    }
+    return n;
+}
+
+// out = A^-1 in for one column pair, in place: the table's blocks act on
+// v0 = u + l and v1 = u - l; u = y0 + y1, l = y0 - y1 (same packing as the clover)
+__device__ __forceinline__ void herm_pair_inplace(const float4* __restrict__ c4, float2 (&ar)[12], float2 (&ai)[12]) {
+    const float2* c2 = reinterpret_cast<const float2*>(c4);
+    float2 vr[2][6], vi[2][6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        vr[0][k] = padd(ar[k], ar[k + 6]);
+        vi[0][k] = padd(ai[k], ai[k + 6]);
+        vr[1][k] = psub(ar[k], ar[k + 6]);
+        vi[1][k] = psub(ai[k], ai[k + 6]);
+    }
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        float2 yr[6], yi[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const float2 d = __ldg(c2 + 90 + 6 * b + i);
+            yr[i] = pmul(d, vr[b][i]);
+            yi[i] = pmul(d, vi[b][i]);
+        }
+        int q = 0;
+#pragma unroll
+        for (int i = 1; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j < i; ++j, ++q) {
+                const float4 A = __ldg(c4 + 15 * b + q);
+                const float2 AR = make_float2(A.x, A.y), AI = make_float2(A.z, A.w);
+                const float2 NAI = __ldg(c2 + 60 + 15 * b + q);
+                yr[i] = pfma(AR, vr[b][j], yr[i]);
+                yr[i] = pfma(NAI, vi[b][j], yr[i]);
+                yi[i] = pfma(AR, vi[b][j], yi[i]);
+                yi[i] = pfma(AI, vr[b][j], yi[i]);
+                yr[j] = pfma(AR, vr[b][i], yr[j]);
+                yr[j] = pfma(AI, vi[b][i], yr[j]);
+                yi[j] = pfma(AR, vi[b][i], yi[j]);
+                yi[j] = pfma(NAI, vr[b][i], yi[j]);
+            }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            if (b == 0) {
+                ar[k] = yr[k];
+                ai[k] = yi[k];
+                ar[k + 6] = yr[k];
+                ai[k + 6] = yi[k];
+            } else {
+                ar[k] = padd(ar[k], yr[k]);
+                ai[k] = padd(ai[k], yi[k]);
+                ar[k + 6] = psub(ar[k + 6], yr[k]);
+                ai[k + 6] = psub(ai[k + 6], yi[k]);
+            }
+        }
+    }
+}
+
+struct EOPairArgs {
+    Field in, xs, y;  // in: the other parity; xs: this parity (mode 2); y: the output (this parity)
+    const float4* __restrict__ U;      // packed-pair links, full-site index
+    const float4* Ci[BK_MAX_COLS / 2];  // packed-pair A^-1 table of launch pair p - p0 (its kappa)
+    int L[4], st[4];
+    int V, Vh, p0, npl, par, mode, G;
+    float2 mk2[BK_MAX_COLS / 2];  // mode 2: {-kappa^2} of the pair's columns
+};
+
+// mode 1: y = A^-1 H in;  mode 2: y = xs - kappa^2 A^-1 H in  (FP32 / FP16 storage)
+template <int P, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_eo_pair(const __grid_constant__ EOPairArgs a) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long long)a.Vh * a.npl) return;
+    const long long per_group = (long long)a.Vh * a.G;
+    const int grp = (int)(g / per_group);
+    const long long r = g - (long long)grp * per_group;
+    const int gw = min(a.G, a.npl - grp * a.G);
+    const int h = (int)(r / gw);
+    const int pl = grp * a.G + (int)(r - (long long)h * gw);
+    const int p = a.p0 + pl;
+    int co[4];
+    const int n = eo_site(h, a.par, a.L, co);
+    const float2 one = make_float2(1.f, 1.f), mone = make_float2(-1.f, -1.f);
+    float2 ar[12], ai[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) ar[k] = ai[k] = make_float2(0.f, 0.f);
+#define BK_EO_DIR(MU)                                                                                          \
+    {                                                                                                          \
+        const int Lm = a.L[MU], sm = a.st[MU];                                                                 \
+        const int nf = co[MU] == Lm - 1 ? n - (Lm - 1) * sm : n + sm;                                          \
+        const int nb = co[MU] == 0 ? n + (Lm - 1) * sm : n - sm;                                               \
+        hop_pair<P, MU, -1>(a.in, nf >> 1, p, a.U + ((size_t)MU * a.V + n) * BK_LINK32_F4, one, mone, ar, ai); \
+        hop_pair<P, MU, +1>(a.in, nb >> 1, p, a.U + ((size_t)MU * a.V + nb) * BK_LINK32_F4, one, mone, ar, ai); \
+    }
+    BK_EO_DIR(0)
+    BK_EO_DIR(1)
+    BK_EO_DIR(2)
+    BK_EO_DIR(3)
+#undef BK_EO_DIR
+    herm_pair_inplace(a.Ci[pl] + (size_t)n * BK_CLOV32_F4, ar, ai);
+    if (a.mode == 2) {
+        float2 xr[12], xi[12];
+        load_pair<P>(a.xs, h, p, xr, xi);
+        const float2 m = a.mk2[pl];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            ar[k] = pfma(m, ar[k], xr[k]);
+            ai[k] = pfma(m, ai[k], xi[k]);
+        }
+    }
+    store_pair<P>(a.y, h, p, ar, ai);
+}
+
+// Staged form of k_eo_pair (FP32): the eight hops' rows of the other parity
+// and, in mode 2, the thread's own row of xs go through the same per-thread
+// cp.async ring as k_dslash_staged (stages: eight hops, then xs).
+constexpr int EA_STAGES = 9;
+
+__device__ __forceinline__ void eo_stage_issue(const EOPairArgs& a, int s, int hsite, int p, float4* slot, int T) {
+    const Field& f = s == EA_STAGES - 1 ? a.xs : a.in;
+    const float4* src = (const float4*)f.data + ((size_t)hsite * 12 * f.np + p);
+    const int k0 = s == 6 ? 6 : 0;   // forward t hop: spins 2, 3
+    const int k1 = s == 7 ? 6 : 12;  // backward t hop: spins 0, 1
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+        if (k >= k0 && k < k1) cp_async16(slot + k * T, src + (size_t)k * f.np);
+}
+
+template <int S, int NSLOT>
+__device__ __forceinline__ void eo_run_stage(const EOPairArgs& a, const int (&hs)[EA_STAGES], const int (&ls)[8],
+                                             int n, int p, int pl, float4* ring, float2 (&ar)[12], float2 (&ai)[12]) {
+    constexpr int T = DA_THREADS;
+    constexpr int pending = (EA_STAGES - 1 - S) < (NSLOT - 1) ? (EA_STAGES - 1 - S) : (NSLOT - 1);
+    cp_async_wait<pending>();
+    const float4* slot = ring + (S % NSLOT) * 12 * T;
+    if constexpr (S < EA_STAGES - 1) {
+        constexpr int MU = S >> 1, SG = (S & 1) ? +1 : -1;
+        const float4* link = a.U + ((size_t)MU * a.V + ls[S]) * BK_LINK32_F4;
+        hop_staged<MU, SG>(slot, T, link, make_float2(1.f, 1.f), make_float2(-1.f, -1.f), ar, ai);
+        if constexpr (S == EA_STAGES - 2) herm_pair_inplace(a.Ci[pl] + (size_t)n * BK_CLOV32_F4, ar, ai);
+    } else {
+        if (a.mode == 2) {  // xs - kappa^2 A^-1 H in
+            const float2 m = a.mk2[pl];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                const float4 q = slot[k * T];
+                ar[k] = pfma(m, ar[k], make_float2(q.x, q.y));
+                ai[k] = pfma(m, ai[k], make_float2(q.z, q.w));
+            }
+        }
+    }
+    constexpr int SN = S + NSLOT;
+    if constexpr (SN < EA_STAGES) {
+        if (SN < EA_STAGES - 1 || a.mode == 2) eo_stage_issue(a, SN, hs[SN], p, ring + (SN % NSLOT) * 12 * T, T);
+        if constexpr (SN < EA_STAGES - 1) {
+            const char* l = (const char*)(a.U + ((size_t)(SN >> 1) * a.V + ls[SN]) * BK_LINK32_F4);
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(l));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(l + 128));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(l + 223));
+        }
+        cp_async_commit();
+    }
+}
+
+template <int NSLOT, int MINB>
+__global__ void __launch_bounds__(DA_THREADS, MINB) k_eo_staged(const __grid_constant__ EOPairArgs a) {
+    extern __shared__ float4 ea_ring[];  // [NSLOT][12][DA_THREADS]
+    constexpr int T = DA_THREADS;
+    const int t = threadIdx.x;
+    const long long g = (long long)blockIdx.x * T + t;
+    if (g >= (long long)a.Vh * a.npl) return;  // no barriers below
+    const long long per_group = (long long)a.Vh * a.G;
+    const int grp = (int)(g / per_group);
+    const long long r = g - (long long)grp * per_group;
+    const int gw = min(a.G, a.npl - grp * a.G);
+    const int h = (int)(r / gw);
+    const int pl = grp * a.G + (int)(r - (long long)h * gw);
+    const int p = a.p0 + pl;
+    int co[4];
+    const int n = eo_site(h, a.par, a.L, co);
+    int hs[EA_STAGES], ls[8];  // half-lattice row of each stage; link site of each hop
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        const int Lm = a.L[mu], sm = a.st[mu];
+        const int nf = co[mu] == Lm - 1 ? n - (Lm - 1) * sm : n + sm;
+        const int nb = co[mu] == 0 ? n + (Lm - 1) * sm : n - sm;
+        hs[2 * mu] = nf >> 1;
+        hs[2 * mu + 1] = nb >> 1;
+        ls[2 * mu] = n;
+        ls[2 * mu + 1] = nb;
+    }
+    hs[EA_STAGES - 1] = h;
+    float4* ring = ea_ring + t;
+    {   // the site's A^-1 entries, needed after the hops
+        const char* cl = (const char*)(a.Ci[pl] + (size_t)n * BK_CLOV32_F4);
+#pragma unroll
+        for (int l = 0; l < 7; ++l) asm volatile("prefetch.global.L2 [%0];" ::"l"(cl + 128 * l));
+    }
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) {
+        eo_stage_issue(a, s, hs[s], p, ring + s * 12 * T, T);
+        cp_async_commit();
+    }
+    float2 ar[12], ai[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) ar[k] = ai[k] = make_float2(0.f, 0.f);
+    eo_run_stage<0, NSLOT>(a, hs, ls, n, p, pl, ring, ar, ai);
+    eo_run_stage<1, NSLOT>(a, hs, ls, n, p, pl, ring, ar, ai);
+    eo_run_stage<2, NSLOT>(a, hs, ls, n, p, pl, ring, ar, ai);
+    eo_run_stage<3, NSLOT>(a, hs, ls, n, p, pl, ring, ar, ai);
+    eo_run_stage<4, NSLOT>(a, hs, ls, n, p, pl, ring, ar, ai);
+    eo_run_stage<5, NSLOT>(a, hs, ls, n, p, pl, ring, ar, ai);
+    eo_run_stage<6, NSLOT>(a, hs, ls, n, p, pl, ring, ar, ai);
+    eo_run_stage<7, NSLOT>(a, hs, ls, n, p, pl, ring, ar, ai);
+    eo_run_stage<8, NSLOT>(a, hs, ls, n, p, pl, ring, ar, ai);
+    store_pair<BK_FP32>(a.y, h, p, ar, ai);
+}
+
+template <int P>
+struct EOColArgs {
+    Field x, xs, y, b;  // x: the other parity (hop input); xs: this parity; y: output; b: residual mode
+    const typename Prec<P>::link* __restrict__ U;  // [mu][9][V] double2, full-site index
+    const typename Prec<P>::clov* Ci[BK_MAX_COLS];  // [36][V] A^-1 table of launch column c - c0
+    int L[4], st[4];
+    int V, Vh, c0, ncl, par, mode, hop, residual;
+    double kappa[BK_MAX_COLS];
+};
+
+// FP64 / double-float, one column per thread:
+//   mode 1: y = A^-1 H x
+//   mode 2: y = xs - kappa^2 A^-1 H x        (residual: y = b - that)
+//   mode 3: y = A^-1 (xs + kappa H x)       (hop = 0: y = A^-1 xs)
+template <int P>
+__global__ void __launch_bounds__(128) k_eo_col(const __grid_constant__ EOColArgs<P> a) {
+    using R = typename Prec<P>::real;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long long)a.Vh * a.ncl) return;
+    const int h = (int)(g / a.ncl);
+    const int cl = (int)(g - (long long)h * a.ncl);
+    const int c = a.c0 + cl;
+    int co[4];
+    const int n = eo_site(h, a.par, a.L, co);
+    cx<R> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = mk(R(0), R(0));
+    if (a.hop) {
+        hop_dir_col<P, 0, true>(a, co, n, c, acc);
+        hop_dir_col<P, 1, true>(a, co, n, c, acc);
+        hop_dir_col<P, 2, true>(a, co, n, c, acc);
+        hop_dir_col<P, 3, true>(a, co, n, c, acc);
+    }
+    const R kap = (R)a.kappa[cl];
+    cx<R> xs[12];
+    if (a.mode != 1) load_col<P>(a.xs, h, c, xs);
+    if (a.mode == 3) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = xs[k] + kap * acc[k];
+    }
+    cx<R> w[12];
+#pragma unroll
+    for (int blk = 0; blk < 2; ++blk) {
+        R m[36];
+#pragma unroll
+        for (int e = 0; e < 18; ++e) {
+            const double2 v = __ldg(a.Ci[cl] + (size_t)(18 * blk + e) * a.V + n);
+            m[2 * e] = (R)v.x;
+            m[2 * e + 1] = (R)v.y;
+        }
+        cx<R> v[6], yv[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = blk == 0 ? acc[k] + acc[k + 6] : acc[k] - acc[k + 6];
+        herm6(m, v, yv);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            if (blk == 0) {
+                w[k] = yv[k];
+                w[k + 6] = yv[k];
+            } else {
+                w[k] = w[k] + yv[k];
+                w[k + 6] = w[k + 6] - yv[k];
+            }
+        }
+    }
+    cx<R> out[12];
+    if (a.mode == 2) {
+        const R k2 = kap * kap;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) out[k] = xs[k] - k2 * w[k];
+        if (a.residual) {
+            cx<R> bb[12];
+            load_col<P>(a.b, h, c, bb);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) out[k] = bb[k] - out[k];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) out[k] = w[k];
+    }
+    store_col<P>(a.y, h, c, out);
+}
+
+// full-lattice FP64 block <-> its two half-lattice blocks (same columns)
+__device__ __forceinline__ int site_parity(int n, const int (&L)[4]) {
+    int r = n, s = r % L[0];
+    r /= L[0];
+    s += r % L[1];
+    r /= L[1];
+    s += r % L[2];
+    s += r / L[2];
+    return s & 1;
+}
+
+struct EOGeo {
+    int L[4];
+};
+
+template <bool MERGE>
+__global__ void k_eo_split_merge(Field full, Field ev, Field od, EOGeo geo) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long row = 12LL * full.np;
+    if (g >= (long long)full.V * row) return;
+    const int n = (int)(g / row);
+    const long long e = g - (long long)n * row;
+    const Field& half = site_parity(n, geo.L) ? od : ev;
+    double2* f = (double2*)full.data + 2 * g;  // an FP64 element: two double2
+    double2* hp = (double2*)half.data + 2 * ((long long)(n >> 1) * row + e);
+    if (MERGE) {
+        f[0] = hp[0];
+        f[1] = hp[1];
+    } else {
+        hp[0] = f[0];
+        hp[1] = f[1];
+    }
+}
+
+template <int P>
+bk_status eo_pair_impl(const EoOp& op, cudaStream_t st) {
+    const int p0 = op.col0 / 2, p1 = (op.col0 + op.ncol + 1) / 2;
+    const int maxp = BK_MAX_COLS / 2;
+    for (int q0 = p0; q0 < p1; q0 += maxp) {
+        const int npl = std::min(maxp, p1 - q0);
+        EOPairArgs a;
+        a.in = op.x;
+        a.xs = op.xs;
+        a.y = op.y;
+        a.U = (const float4*)op.U;
+        int st4[4];
+        geometry(op.dims, a.L, st4);
+        for (int mu = 0; mu < 4; ++mu) a.st[mu] = st4[mu];
+        a.V = op.V;
+        a.Vh = op.V / 2;
+        a.p0 = q0;
+        a.npl = npl;
+        a.par = op.par;
+        a.mode = op.mode;
+        for (int j = 0; j < npl; ++j) {
+            // the pair's columns share one kappa (systems have even widths); a
+            // column outside [col0, col0 + ncol) is padding: kappa 0
+            const int ca = 2 * (q0 + j) - op.col0, cb = ca + 1;
+            const bool ina = ca >= 0 && ca < op.ncol, inb = cb >= 0 && cb < op.ncol;
+            const double ka = ina ? op.kappa[ca] : 0.0, kb = inb ? op.kappa[cb] : 0.0;
+            a.Ci[j] = (const float4*)op.Ci[ina ? ca : cb];
+            a.mk2[j] = make_float2((float)(-ka * ka), (float)(-kb * kb));
+        }
+        const int threads = op.variant == 1 ? 256 : 128;
+        a.G = op.group > 0 ? std::min(op.group, npl) : npl;
+        const long long items = (long long)a.Vh * npl;
+        const unsigned blocks = (unsigned)((items + threads - 1) / threads);
+        if (P == BK_FP32 && (op.variant == 4 || op.variant == 5)) {
+            // staged form: ring of 2 (variant 4) or 3 (variant 5) slots per thread
+            const unsigned sb = (unsigned)((items + DA_THREADS - 1) / DA_THREADS);
+            if (op.variant == 4) {
+                const size_t smem = (size_t)2 * 12 * DA_THREADS * sizeof(float4);
+                BK_CUDA_TRY(cudaFuncSetAttribute(k_eo_staged<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+                k_eo_staged<2, 4><<<sb, DA_THREADS, smem, st>>>(a);
+            } else {
+                const size_t smem = (size_t)3 * 12 * DA_THREADS * sizeof(float4);
+                BK_CUDA_TRY(cudaFuncSetAttribute(k_eo_staged<3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+                k_eo_staged<3, 3><<<sb, DA_THREADS, smem, st>>>(a);
+            }
+        } else if (op.variant == 1) {
+            k_eo_pair<P, 256, 1><<<blocks, threads, 0, st>>>(a);
+        } else {
+            k_eo_pair<P, 128, 3><<<blocks, threads, 0, st>>>(a);
+        }
+        BK_CUDA_TRY(cudaGetLastError());
+    }
+    return BK_OK;
+}
+
+template <int P>
+bk_status eo_col_impl(const EoOp& op, cudaStream_t st) {
+    for (int c0 = 0; c0 < op.ncol; c0 += BK_MAX_COLS) {
+        const int n = std::min(BK_MAX_COLS, op.ncol - c0);
+        EOColArgs<P> a;
+        a.x = op.x;
+        a.xs = op.xs;
+        a.y = op.y;
+        a.b = op.b;
+        a.U = (const typename Prec<P>::link*)op.U;
+        geometry(op.dims, a.L, a.st);
+        a.V = op.V;
+        a.Vh = op.V / 2;
+        a.c0 = op.col0 + c0;
+        a.ncl = n;
+        a.par = op.par;
+        a.mode = op.mode;
+        a.hop = op.hop;
+        a.residual = op.residual;
+        for (int j = 0; j < n; ++j) {
+            a.kappa[j] = op.kappa[c0 + j];
+            a.Ci[j] = (const typename Prec<P>::clov*)op.Ci[c0 + j];
+        }
+        const long long items = (long long)a.Vh * n;
+        k_eo_col<P><<<(unsigned)((items + 127) / 128), 128, 0, st>>>(a);
+        BK_CUDA_TRY(cudaGetLastError());
+    }
+    return BK_OK;
+}
+
 }  // namespace
 
 bk_status launch_dslash(int prec, const DslashOp& op, cudaStream_t st) {
@@ -1226,4 +1672,46 @@ bk_status launch_gamma5_canon(const double* X, double* Y, long long n, cudaStrea
     k_gamma5<<<(unsigned)((n + 127) / 128), 128, 0, st>>>((const double2*)X, (double2*)Y, n);
     BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
+}
+
+bk_status launch_eo(int prec, const EoOp& op, cudaStream_t st) {
+    if (op.ncol <= 0) return BK_OK;
+    if ((op.dims[0] & 1) || (op.V & 1)) {
+        bk_set_error("the even-odd form needs an even extent in x");
+        return BK_ERR_INVALID_ARG;
+    }
+    if (op.mode < 1 || op.mode > 3 || ((prec == BK_FP32 || prec == BK_FP16) && op.mode == 3)) {
+        bk_set_error("bad even-odd operator mode");
+        return BK_ERR_INVALID_ARG;
+    }
+    switch (prec) {
+        case BK_FP64: return eo_col_impl<BK_FP64>(op, st);
+        case BK_DF64: return eo_col_impl<BK_DF64>(op, st);
+        case BK_FP32: return eo_pair_impl<BK_FP32>(op, st);
+        case BK_FP16: return eo_pair_impl<BK_FP16>(op, st);
+    }
+    return BK_ERR_INVALID_ARG;
+}
+
+static bk_status eo_split_merge(bool merge, Field full, Field ev, Field od, const int dims[4], cudaStream_t st) {
+    if (ev.np != full.np || od.np != full.np || 2 * ev.V != full.V || 2 * od.V != full.V) {
+        bk_set_error("even-odd split: half blocks must have the full block's columns and half its sites");
+        return BK_ERR_INVALID_ARG;
+    }
+    EOGeo geo;
+    for (int mu = 0; mu < 4; ++mu) geo.L[mu] = dims[mu];
+    const long long items = (long long)full.V * 12 * full.np;
+    const unsigned blocks = (unsigned)((items + 255) / 256);
+    if (merge) k_eo_split_merge<true><<<blocks, 256, 0, st>>>(full, ev, od, geo);
+    else k_eo_split_merge<false><<<blocks, 256, 0, st>>>(full, ev, od, geo);
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}
+
+bk_status launch_eo_split(Field full, Field ev, Field od, const int dims[4], cudaStream_t st) {
+    return eo_split_merge(false, full, ev, od, dims, st);
+}
+
+bk_status launch_eo_merge(Field ev, Field od, Field full, const int dims[4], cudaStream_t st) {
+    return eo_split_merge(true, full, ev, od, dims, st);
 }

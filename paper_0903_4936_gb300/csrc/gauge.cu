@@ -274,6 +274,125 @@ __global__ void k_clover_build(const double2* __restrict__ U, double2* __restric
     }
 }
 
+// ---------------------------------------------------------------- clover inverse
+//
+// Even-odd form: the site term of D_W is A(n) = 1 - kappa C(n).  In the
+// chiral basis a = u + l, b = u - l it acts as a' = (1 - 2 kappa A') a,
+// b' = (1 - 2 kappa B') b (A', B' the stored blocks), so with Pa, Pb the
+// inverses of those two 6x6 matrices,
+//     (A^-1 q)_u = (Pa/2) a + (Pb/2) b,   (A^-1 q)_l = (Pa/2) a - (Pb/2) b,
+// the same form as C q: Pa/2 and Pb/2 are stored exactly like A' and B'
+// (FP64 [36][site] and FP32 packed pairs).  Each block is inverted in FP64 by
+// Gauss-Jordan elimination with partial pivoting.  bound[0] receives the
+// largest infinity norm of (1 - 2 kappa A'), (1 - 2 kappa B') over the sites
+// (>= the spectral norm of A(n), used to scale the Schur system's stopping
+// rule); bound[1] counts blocks whose pivot fell below 1e-12 (singular A).
+__global__ void k_clover_inverse(const double2* __restrict__ C64, double kappa, double2* __restrict__ Ci64,
+                                 float4* __restrict__ Ci32, int V, unsigned long long* __restrict__ bound) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    double out[72];
+    double nmax = 0.0;
+    int singular = 0;
+#pragma unroll 1
+    for (int b = 0; b < 2; ++b) {
+        double h[36];
+#pragma unroll
+        for (int e = 0; e < 18; ++e) {
+            const double2 v = C64[(size_t)(18 * b + e) * V + s];
+            h[2 * e] = v.x;
+            h[2 * e + 1] = v.y;
+        }
+        // M = 1 - 2 kappa H, augmented with the identity
+        cx<double> m[6][12];
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j < 12; ++j) m[i][j] = mk(j == i + 6 ? 1.0 : 0.0, 0.0);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) m[i][i] = mk(1.0 - 2.0 * kappa * h[i], 0.0);
+        {
+            int q = 0;
+#pragma unroll
+            for (int i = 1; i < 6; ++i)
+#pragma unroll
+                for (int j = 0; j < i; ++j, ++q) {
+                    const cx<double> a = mk(h[6 + 2 * q], h[7 + 2 * q]);
+                    m[i][j] = mk(-2.0 * kappa * a.r, -2.0 * kappa * a.i);
+                    m[j][i] = mk(-2.0 * kappa * a.r, 2.0 * kappa * a.i);
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            double r = 0.0;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) r += hypot(m[i][j].r, m[i][j].i);
+            nmax = fmax(nmax, r);
+        }
+#pragma unroll 1
+        for (int k = 0; k < 6; ++k) {
+            int piv = k;
+            double best = hypot(m[k][k].r, m[k][k].i);
+            for (int i = k + 1; i < 6; ++i) {
+                const double v = hypot(m[i][k].r, m[i][k].i);
+                if (v > best) {
+                    best = v;
+                    piv = i;
+                }
+            }
+            if (best < 1e-12) singular = 1;
+            if (piv != k)
+                for (int j = 0; j < 12; ++j) {
+                    const cx<double> t = m[k][j];
+                    m[k][j] = m[piv][j];
+                    m[piv][j] = t;
+                }
+            // row k /= pivot
+            const cx<double> p = m[k][k];
+            const double den = p.r * p.r + p.i * p.i;
+            const cx<double> ip = den > 0.0 ? mk(p.r / den, -p.i / den) : mk(0.0, 0.0);
+            for (int j = 0; j < 12; ++j) m[k][j] = m[k][j] * ip;
+            for (int i = 0; i < 6; ++i) {
+                if (i == k) continue;
+                const cx<double> f = m[i][k];
+                for (int j = 0; j < 12; ++j) m[i][j] = m[i][j] - f * m[k][j];
+            }
+        }
+        // the inverse (Hermitian): diagonal real part and lower triangle, halved
+        double* o = out + 36 * b;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) o[i] = 0.5 * m[i][i + 6].r;
+        int q = 0;
+#pragma unroll
+        for (int i = 1; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j < i; ++j, ++q) {
+                // average the two triangles (they agree to rounding)
+                o[6 + 2 * q] = 0.25 * (m[i][j + 6].r + m[j][i + 6].r);
+                o[7 + 2 * q] = 0.25 * (m[i][j + 6].i - m[j][i + 6].i);
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < 36; ++q) Ci64[(size_t)q * V + s] = make_double2(out[2 * q], out[2 * q + 1]);
+    float2* c2 = reinterpret_cast<float2*>(Ci32 + (size_t)s * BK_CLOV32_F4);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const double* o = out + 36 * b;
+#pragma unroll
+        for (int q = 0; q < 15; ++q) {
+            const float ar = (float)o[6 + 2 * q], ai = (float)o[7 + 2 * q];
+            c2[2 * (15 * b + q)] = make_float2(ar, ar);
+            c2[2 * (15 * b + q) + 1] = make_float2(ai, ai);
+            c2[60 + 15 * b + q] = make_float2(-ai, -ai);
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) c2[90 + 6 * b + i] = make_float2((float)o[i], (float)o[i]);
+    }
+    // non-negative doubles order like their bit patterns
+    atomicMax(bound, (unsigned long long)__double_as_longlong(nmax));
+    if (singular) atomicAdd(bound + 1, 1ull);
+}
+
 }  // namespace
 
 bk_status launch_gauge_convert(const double* Uin_dev, double2* U64, float4* U32, int V, cudaStream_t st) {
@@ -294,6 +413,13 @@ bk_status launch_clover_build(const double2* U64, double2* C64, float4* C32, con
     }
     const int V = stride;
     k_clover_build<<<(V + 63) / 64, 64, 0, st>>>(U64, C64, C32, g, V, csw);
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}
+
+bk_status launch_clover_inverse(const double2* C64, double kappa, double2* Ci64, float4* Ci32, int V,
+                                unsigned long long* bound, cudaStream_t st) {
+    k_clover_inverse<<<(V + 63) / 64, 64, 0, st>>>(C64, kappa, Ci64, Ci32, V, bound);
     BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
 }

@@ -92,8 +92,9 @@ def test_fp64_cholesky_basis_keeps_the_papers_iterates(c1):
     assert n >= 10
     # equal in exact arithmetic only: the basis change rounds differently from
     # the plain recursion, so the histories drift apart at the 1e-5 level as the
-    # residual falls (a wrong transformation differs at O(1))
-    assert np.allclose(np.array(info["history"][:n]), ho[:n], rtol=1e-3)
+    # residual falls (a wrong transformation differs at O(1)); 1e-4 leaves a
+    # factor of ten over that drift
+    assert np.allclose(np.array(info["history"][:n]), ho[:n], rtol=1e-4)
     assert _dev(X.cpu().numpy(), dense.from_columns(Xo, dims)) < 1e-9
 
 
