@@ -68,6 +68,11 @@ WORKLOADS = {
                cases=[(0.125, 12, "point")],
                desc="8^3x16, eps=0.5, c_SW=1.0, kappa=0.125, L=12 point sources; block BiCGGR with FP32 inner "
                     "iterations (Cholesky basis of P) and FP64 residual replacement, tol 1e-10"),
+    "c3-24": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp32", method="bicgstab",
+                  block=6, delta=0.003, eo=True, cases=[(0.125, 24, "z2")],
+                  desc="16^3x32, eps=0.5, c_SW=1.0, kappa=0.125, 24 complex-Z2 sources as 4 systems of 6 columns "
+                       "on the even-odd Schur system, FP32 inner iterations, FP64 residual replacement (delta "
+                       "0.003), tol 1e-10 (the small case for ncu captures: every block above L2, a few GB)"),
     "c3-12": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp32", method="bicgstab",
                   cases=[(0.125, 12, "point")],
                   desc="16^3x32, eps=0.5, c_SW=1.0, kappa=0.125, L=12 point sources; block BiCGSTAB, "
@@ -356,10 +361,10 @@ def oracle_rhs_per_s(secs, procs, L, iters):
 
 
 # Iteration count of the FP64 block BiCGGR on the first block system of each
-# workload (kappa 0.120, L <= 6), as measured by this benchmark's FP64
-# comparison on a GB300; the reference arm, which has no GPU, uses it to turn
-# the oracle's seconds per application into RHS/s.
-FP64_ITERS_FIRST_SYSTEM = {"c4": 45, "c3": 45, "c2": 50, "c3-12": 54}
+# workload on the full system (the oracle's form), as measured by this
+# benchmark's FP64 comparison on a GB300 (--no-eo); the reference arm, which
+# has no GPU, uses it to turn the oracle's seconds per application into RHS/s.
+FP64_ITERS_FIRST_SYSTEM = {"c4": 42, "c3": 45, "c2": 50, "c3-12": 54}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -613,9 +618,11 @@ def main():
                 "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                 "host": {"nproc": _host_cores()}}))
             return
+        iters = FP64_ITERS_FIRST_SYSTEM.get(args.workload)
+        if iters is None:
+            raise SystemExit(f"no measured FP64 iteration count for workload {args.workload}; use --oracle-solve")
         secs, procs, (kappa, L) = oracle_samples(wl, args.warmup + args.steps, max_procs=args.cpu_procs)
         timed = secs[args.warmup:] if len(secs) > args.warmup else secs
-        iters = FP64_ITERS_FIRST_SYSTEM[args.workload]
         value, mean = oracle_rhs_per_s(timed, procs, L, iters)
         sample = (f"one FP64 numpy-oracle application of D_W to the first block system's {L} columns (kappa={kappa}) "
                   f"per step ({mean:.1f} s), {procs} processes on the host cores at once; RHS/s = processes x L / "
@@ -684,15 +691,17 @@ def main():
         line["fp64_comparison"] = r["fp64"]
     if cpu is not None:
         secs, procs, (kappa, L) = cpu
-        iters = (r["fp64"] or {}).get("same_split", {}).get("iterations_first_system") or \
-            FP64_ITERS_FIRST_SYSTEM[args.workload]
+        # the oracle solves the full system: its iteration count, not the even-odd one
+        iters = FP64_ITERS_FIRST_SYSTEM.get(args.workload) if r["eo"] else \
+            ((r["fp64"] or {}).get("same_split", {}).get("iterations_first_system") or
+             FP64_ITERS_FIRST_SYSTEM.get(args.workload))
         cv, mean = oracle_rhs_per_s(secs, procs, L, iters)
         line["cpu_baseline"] = {
             "value": cv, "unit": "RHS/s", "cores": procs, "kind": "oracle",
             "sample": f"one FP64 numpy-oracle application of D_W to the first block system's {L} columns "
                       f"(kappa={kappa}, {mean:.1f} s) on each of {procs} host processes at once; RHS/s = processes x "
-                      f"L / (s x (2 x {iters} + 2)), {iters} = this run's FP64 block BiCGGR iteration count for that "
-                      f"system; the oracle's block algebra is left out"}
+                      f"L / (s x (2 x {iters} + 2)), {iters} = the FP64 block BiCGGR iteration count of that system "
+                      f"on the full system (GB300); the oracle's block algebra is left out"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
