@@ -546,7 +546,15 @@ def gb300_arm(args, wl, rank, world, local_rank):
                                   rhs_per_s=Lt / (tot / 1e3), ms=round(tot, 1), iterations_first_system=first,
                                   iterations_max=max(its))
         if args.fp64_full:
-            # the paper's method as printed: every case one block of all its columns
+            # the paper's method as printed: every case one block of all its
+            # columns, on the full system.  A fresh context, so that the
+            # workspace of the solves above (even-odd blocks) is released.
+            lat.close()
+            U = synth.random_su3_field(dims, wl["eps"], wl["gauge_seed"])
+            lat = bk.Lattice(dims, local_rank)
+            lat.upload_gauge(U)
+            lat.build_clover(wl["csw"])
+            del U
             tot, per = 0.0, {}
             for c in cases:
                 Bc = Ball[c["c0"]:c["c0"] + c["L"]].contiguous()
