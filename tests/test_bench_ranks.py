@@ -82,8 +82,11 @@ def test_roofline_traffic_scales_the_capture(tmp_path, monkeypatch):
     import json
     b = _bench()
     d = json.load(open(os.path.join(ROOT, "profiles", "dslash_traffic.json")))
-    c = d["captures"]["fp32"]
-    if d["source_hash"] == b.source_hash():
-        assert b.ncu_traffic("fp32", 2e9) == pytest.approx(c["dram_bytes"] / c["alg_bytes"] * 2e9)
+    assert d["captures"]
+    for kind, c in d["captures"].items():
+        if d["source_hash"] == b.source_hash():
+            assert b.ncu_traffic(kind, 2e9) == pytest.approx(c["dram_bytes"] / c["alg_bytes"] * 2e9)
     monkeypatch.setattr(b, "source_hash", lambda: "0000")
-    assert b.ncu_traffic("fp32", 2e9) is None
+    for kind in d["captures"]:
+        assert b.ncu_traffic(kind, 2e9) is None
+    assert b.ncu_traffic("no such capture", 2e9) is None
