@@ -8,14 +8,16 @@ c_SW = 1, six systems kappa in {0.120, ..., 0.130} with L = {4, 12, 12, 24, 48,
 96} Z4 noise sources (196 right-hand sides).  One step = the whole workload
 solved once through the C ABI as one batched solve: every system split into
 block systems of at most 6 columns, block BiCGSTAB on the even-odd Schur
-system (--no-eo: on the full system) with FP32 inner iterations and FP64
-residual replacement (delta 0.003), each column to an FP64 true residual
-<= 1e-10 of the full system (the run fails otherwise).  Prints ONE JSON line
+system (--no-eo: on the full system) with FP32 inner iterations and residual
+replacement at delta 0.003 (an FP64 true residual after every 1e-4 of
+reduction and for every convergence decision, FP32 updates r -= A dx between;
+--anchor 0: always FP64), each column to an FP64 true residual <= 1e-10 of
+the full system (the run fails otherwise).  Prints ONE JSON line
 on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
                   [--workload c4|c3|c2|c3-12] [--no-fp64] [--fp64-full] [--no-cpu-baseline]
-                  [--eo | --no-eo] [--delta D] [--update fp64|df64]
+                  [--eo | --no-eo] [--delta D] [--anchor A] [--update fp64|df64]
                   [--oracle-solve] [--cpu-procs N]   (reference arm)
 
 Comparisons on the same GPU (after the timed steps): the plain FP64 method at
@@ -51,19 +53,20 @@ _C3_CASES = [(k, L, src) for k in (0.120, 0.125, 0.130) for (L, src) in ((12, "p
 # Workloads: (Lx, Ly, Lz, Lt), link spread eps, c_SW, cases (kappa, L, source kind).
 WORKLOADS = {
     "c4": dict(dims=(24, 24, 24, 48), eps=0.5, csw=1.0, gauge_seed=1004, prec="fp32", method="bicgstab",
-               block=6, delta=0.003, eo=True, distinct_sources=True, cases=_C4_CASES,
+               block=6, delta=0.003, anchor=1e-4, eo=True, distinct_sources=True, cases=_C4_CASES,
                desc="24^3x48 clover Wilson-Dirac, random SU(3) links eps=0.5, c_SW=1.0: 6 systems, kappa "
                     "{0.120,...,0.130} with L {4,12,12,24,48,96} Z4 noise = 196 right-hand sides; one batched "
                     "block BiCGSTAB solve over 33 block systems of at most 6 columns on the even-odd Schur "
-                    "system, FP32 inner iterations, FP64 residual replacement (delta 0.003), FP64 true residual "
-                    "of the full system <= 1e-10 for every column"),
+                    "system, FP32 inner iterations, residual replacement at delta 0.003 (FP64 after every 1e-4 "
+                    "of reduction, FP32 between), FP64 true residual of the full system <= 1e-10 for every "
+                    "column"),
     "c3": dict(dims=(16, 16, 16, 32), eps=0.5, csw=1.0, gauge_seed=1003, prec="fp32", method="bicgstab",
-               block=6, delta=0.003, eo=True, cases=_C3_CASES,
+               block=6, delta=0.003, anchor=1e-4, eo=True, cases=_C3_CASES,
                desc="16^3x32 clover Wilson-Dirac, random SU(3) links eps=0.5, c_SW=1.0, kappa in "
                     "{0.120,0.125,0.130} x (L=12 point sources, L=48 complex-Z2 noise) = 180 right-hand sides; "
                     "one batched block BiCGSTAB solve over 30 systems of 6 columns on the even-odd Schur system, "
-                    "FP32 inner iterations, FP64 residual replacement (delta 0.003), FP64 true residual of the "
-                    "full system <= 1e-10 for every column"),
+                    "FP32 inner iterations, residual replacement at delta 0.003 (FP64 after every 1e-4 of "
+                    "reduction, FP32 between), FP64 true residual of the full system <= 1e-10 for every column"),
     "c2": dict(dims=(8, 8, 8, 16), eps=0.5, csw=1.0, gauge_seed=1002, prec="fp32", method="bicggr",
                cases=[(0.125, 12, "point")],
                desc="8^3x16, eps=0.5, c_SW=1.0, kappa=0.125, L=12 point sources; block BiCGGR with FP32 inner "
@@ -420,6 +423,7 @@ def gb300_arm(args, wl, rank, world, local_rank):
     kap_s, L_s, owner = [s[0] for s in sysl], [s[1] for s in sysl], [s[2] for s in sysl]
     update = args.update or wl.get("update", "fp64")
     eo = wl.get("eo", False) if args.eo is None else args.eo
+    anchor = wl.get("anchor", 0.0) if args.anchor is None else args.anchor
     delta = args.delta if args.delta is not None else wl.get("delta", 0.0)
     Xdev = torch.empty_like(Ball)
     Bh = Ball.cpu().pin_memory()
@@ -429,7 +433,7 @@ def gb300_arm(args, wl, rank, world, local_rank):
     def solve(B, X, record, prec=None, method=None):
         return lat.block_solve_batched(B, kap_s, L_s, method=method or wl["method"], prec=prec or wl["prec"],
                                        tol=TOL, maxiter=MAXITER, timing=record, delta=delta,
-                                       out=X, raise_on_fail=False, update=update, eo=eo)
+                                       out=X, raise_on_fail=False, update=update, eo=eo, anchor=anchor)
 
     def check(infos, what):
         for si, info in enumerate(infos):
@@ -571,6 +575,7 @@ def gb300_arm(args, wl, rank, world, local_rank):
                                        rhs_per_s=Lt / (tot / 1e3), cases=per)
 
     return dict(total_ms=total_ms, per_step_ms=per_step_ms, agg=agg, clocks=clk, e2e_ms=e2e_ms / n_e2e, eo=eo,
+                anchor=anchor,
                 h2d=h2d, d2h=d2h, fp64=fp64, V=V, per_case=per_case,
                 batched=dict(systems=len(L_s), block=wl.get("block"), columns=Lt))
 
@@ -592,6 +597,8 @@ def main():
     ap.add_argument("--eo", dest="eo", action="store_true", default=None,
                     help="solve through the even-odd Schur system (default: the workload's)")
     ap.add_argument("--no-eo", dest="eo", action="store_false")
+    ap.add_argument("--anchor", type=float, default=None,
+                    help="fp64_anchor: replacements between FP64 ones in FP32 (default: the workload's)")
     ap.add_argument("--delta", type=float, default=None,
                     help="residual-replacement threshold (default: the workload's)")
     ap.add_argument("--update", choices=["fp64", "df64"], default=None,
@@ -674,7 +681,10 @@ def main():
         "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": wl["prec"], "data": "synthetic",
-        "mixed_precision": "inner iterations in FP32, FP64 residual replacement and true residual",
+        "mixed_precision": ("inner iterations in FP32; residual replacement " +
+                            (f"in FP64 after every {r['anchor']:g} of reduction and in FP32 between"
+                             if r["anchor"] else "in FP64") + "; FP64 true residual"),
+        "formulation": "even-odd Schur system" if r["eo"] else "full system",
         "config": {"workload": wl["desc"], "lattice": "x".join(map(str, wl["dims"])),
                    "rhs_per_step": total_rhs_per_step, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 and a 256 MB L2 flush before every timed step"},

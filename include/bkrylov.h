@@ -328,6 +328,17 @@ typedef struct bk_solve_params {
                               Only the even sites of an X_0 are used.  The
                               iteration counts and residual histories are
                               those of the Schur system.  0 = the full system */
+    double fp64_anchor;    /* mixed precision with FP32 inner iterations and
+                              FP64 replacements (not in the paper): a residual
+                              replacement of a system whose residual has not
+                              fallen by this factor since its last FP64 one
+                              is done in the inner precision, R64 <- R64 -
+                              A X_lo and X64 += X_lo, with A X_lo from the
+                              FP32 operator (its rounding is relative to the
+                              residual at the previous replacement); the
+                              others, and every convergence decision, take
+                              the FP64 true residual B - A X64.  0 (default):
+                              every replacement in FP64.  Must be in [0, 1). */
 } bk_solve_params;
 
 typedef struct bk_solve_info {

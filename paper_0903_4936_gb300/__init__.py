@@ -232,11 +232,12 @@ class Lattice:
 
     # ------------------------------------------------------------ solves
     def _params(self, method, prec, tol, maxiter, delta, x0_given, on_host, rtilde, seed, history, timing,
-                restart=False, orth=None, update="fp64", deflate=False, eo=False):
+                restart=False, orth=None, update="fp64", deflate=False, eo=False, anchor=0.0):
         """rtilde: None -> seeded Gaussian R~_0 (library default), "r0" -> R~_0 = R_0,
         tensor -> the caller's block (canonical layout, where B lives).  update:
         arithmetic of the mixed-precision residual replacements, "df64" or "fp64".
-        eo: iterate on the even-odd Schur system (bk_solve_params.eo)."""
+        eo: iterate on the even-odd Schur system (bk_solve_params.eo).  anchor:
+        bk_solve_params.fp64_anchor (replacements between FP64 ones in FP32)."""
         if update not in ("df64", "fp64"):
             raise ValueError("update must be 'df64' or 'fp64'")
         mode, ptr = 0, None
@@ -249,7 +250,8 @@ class Lattice:
         return SolveParams(METHOD[method] if isinstance(method, str) else int(method), _prec(prec), float(tol),
                            int(maxiter), float(delta), int(x0_given), int(on_host), mode, int(seed), ptr,
                            int(bool(restart)), 0 if orth is None else (1 if orth else 2), int(history),
-                           int(timing), 1 if update == "df64" else 0, int(bool(deflate)), int(bool(eo)))
+                           int(timing), 1 if update == "df64" else 0, int(bool(deflate)), int(bool(eo)),
+                           float(anchor))
 
     @staticmethod
     def _info_dict(info: SolveInfo, hist_buf, res_buf):
@@ -261,7 +263,7 @@ class Lattice:
     def block_solve(self, B: torch.Tensor, kappa: float, method="bicggr", prec="fp64", tol=1e-10, maxiter=2000,
                     X0: torch.Tensor | None = None, delta=0.0, rtilde=None, seed=0, history=False,
                     timing=False, out: torch.Tensor | None = None, raise_on_fail=True, restart=False,
-                    orth=None, update="fp64", deflate=False, eo=False):
+                    orth=None, update="fp64", deflate=False, eo=False, anchor=0.0):
         """Solve D_W X = B (Eq. (linear_mrhs)).  B on the GPU, or on the host
         (then pinned memory is best): X is returned where B lives."""
         self._check_block(B, "B")
@@ -275,7 +277,7 @@ class Lattice:
             if rtilde.shape != B.shape or rtilde.is_cuda != B.is_cuda:
                 raise ValueError("rtilde must have B's shape and location")
         prm = self._params(method, prec, tol, maxiter, delta, X0 is not None, on_host, rtilde, seed, history,
-                           timing, restart, orth, update, deflate, eo)
+                           timing, restart, orth, update, deflate, eo, anchor)
         info = SolveInfo()
         res_buf = (C.c_double * L)()
         info.true_res = C.cast(res_buf, C.POINTER(C.c_double))
@@ -293,7 +295,7 @@ class Lattice:
     def block_solve_batched(self, B: torch.Tensor, kappas: Sequence[float], Ls: Sequence[int], method="bicggr",
                             prec="fp64", tol=1e-10, maxiter=2000, delta=0.0, rtilde=None, seed=0, history=False,
                             timing=False, raise_on_fail=True, restart=False, orth=None, update="fp64",
-                            out: torch.Tensor | None = None, deflate=False, eo=False):
+                            out: torch.Tensor | None = None, deflate=False, eo=False, anchor=0.0):
         """Several systems (kappa_s, L_s columns each, concatenated in B).  X is
         returned where B lives, in `out` if given (same shape and location as
         B; pinned host memory for host blocks)."""
@@ -310,7 +312,7 @@ class Lattice:
         else:
             X = torch.empty_like(B, pin_memory=on_host) if on_host else torch.empty_like(B)
         prm = self._params(method, prec, tol, maxiter, delta, False, on_host, rtilde, seed, history, timing,
-                           restart, orth, update, deflate, eo)
+                           restart, orth, update, deflate, eo, anchor)
         infos = (SolveInfo * nsys)()
         res_bufs, hist_bufs = [], []
         for s in range(nsys):

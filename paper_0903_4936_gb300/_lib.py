@@ -37,6 +37,7 @@ class SolveParams(C.Structure):
         ("rtilde_mode", C.c_int), ("seed", C.c_uint64), ("rtilde", C.c_void_p), ("restart_on_update", C.c_int),
         ("orth_mode", C.c_int), ("record_history", C.c_int),
         ("timing", C.c_int), ("update_prec", C.c_int), ("deflate", C.c_int), ("eo", C.c_int),
+        ("fp64_anchor", C.c_double),
     ]
 
 

@@ -134,6 +134,7 @@ struct bk_ctx {
     DevBuf cinv_bound;
     // even-odd solve and operator workspace
     DevBuf eoB, eoX, eoR, eoBo, eoT64, eoT, eoS;
+    DevBuf Ylo;  // inner-precision A Xlo of the fp64_anchor replacements
 };
 
 static bool wide(int prec) { return prec == BK_FP64 || prec == BK_DF64; }
@@ -202,7 +203,8 @@ extern "C" bk_status bk_destroy(bk_ctx* c) {
     DevBuf* bufs[] = {&c->U64,   &c->U32,   &c->C64,   &c->C32,        &c->Utmp, &c->s1,  &c->s2,
                       &c->part,  &c->scal,  &c->B64,   &c->X64,        &c->R64,  &c->Xlo, &c->small,
                       &c->spart, &c->stage, &c->colmap, &c->fscratch,  &c->ynorm, &c->cinv_bound,
-                      &c->eoB,   &c->eoX,   &c->eoR,   &c->eoBo,       &c->eoT64, &c->eoT, &c->eoS};
+                      &c->eoB,   &c->eoX,   &c->eoR,   &c->eoBo,       &c->eoT64, &c->eoT, &c->eoS,
+                      &c->Ylo};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : c->blk) b.release();
     for (auto& kv : c->cinv) {
@@ -773,6 +775,12 @@ struct Solve {
     // that update, restarts, and systems whose recurrences restart this iteration
     std::vector<int> since, nrestart, restart_now;
     std::vector<double> m_upd;
+    // fp64_anchor (FP32 inner iterations): replacements between FP64 anchors
+    // in the inner precision; m_anchor = residual at the last FP64 one; Ylo
+    // the inner-precision image A Xlo
+    bool low_updates = false;
+    std::vector<double> m_anchor;
+    Field Ylo;
     std::vector<std::vector<double>> hist;
     std::vector<double> true_res, rec_res;
     std::vector<char> res_known;     // per system: true_res already holds the final FP64 residual
@@ -977,15 +985,27 @@ struct Solve {
     // Leaves the FP64 residual norms of s in rn_h after a readback.
     // rprec: BK_FP64 or BK_DF64 arithmetic for B - A X; accum = false recomputes
     // the residual of the current X64 (Xlo already folded in).
+    // rprec == P (fp64_anchor): R64 -= A Xlo with A Xlo in the inner precision,
+    // X64 += Xlo; no FP64 operator (exact to the inner precision's rounding
+    // of A Xlo, relative to the residual at the previous replacement)
     bk_status reliable_update(const std::vector<int>& sys, int rprec, bool accum) {
         sysmask mask = 0;
         for (int s : sys) {
             mask |= 1ull << s;
-            mv64[s]++;
+            if (rprec == P) mv[s]++;
+            else mv64[s]++;
             if (accum) nrel[s]++;
         }
         for (const auto& cr : col_runs(mask)) {
             const int c0 = cr.first, n = cr.second;
+            if (rprec == P) {
+                BK_TRY(dslash(P, Xlo, Ylo, Ylo, c0, n, 0));
+                BK_TRY(launch_accum(X64, Xlo, c0 / 2, n / 2, st));
+                BK_TRY(launch_sub_lo(R64, Ylo, c0 / 2, n / 2, st));
+                BK_TRY(cast_cols(R64, BK_FP64, R, P, c0, n));
+                launches += 3;
+                continue;
+            }
             if (mixed && accum) {
                 BK_TRY(launch_accum(X64, Xlo, c0 / 2, n / 2, st));
                 launches++;
@@ -1051,6 +1071,11 @@ struct Solve {
         if (mixed) {
             BK_TRY(c->Xlo.ensure(field_bytes(Lt, V, BK_FP32)));
             Xlo = make_field(c->Xlo.p, Lt, V, BK_FP32);
+        }
+        low_updates = mixed && P == BK_FP32 && upd_prec == BK_FP64 && prm->fp64_anchor > 0.0;
+        if (low_updates) {
+            BK_TRY(c->Ylo.ensure(field_bytes(Lt, V, BK_FP32)));
+            Ylo = make_field(c->Ylo.p, Lt, V, BK_FP32);
         }
         // caller column -> device column
         BK_TRY(c->colmap.ensure((size_t)Lu * sizeof(int)));
@@ -1201,6 +1226,7 @@ struct Solve {
             const double m = sys_max(s);
             hist[s].push_back(m);
             rmax_since[s] = m;
+            m_anchor[s] = m;
             if (m <= tol_s[s]) done[s] = 1;
         }
         update_active();
@@ -1436,17 +1462,32 @@ struct Solve {
             }
         }
         if (!upd.empty()) {
-            BK_TRY(reliable_update(upd, upd_prec, true));
-            std::vector<int> conf;
+            // fp64_anchor: a replacement in the inner precision (r <- r - A dx)
+            // unless the residual fell by the anchor factor since the last FP64
+            // one, or meets tol
+            std::vector<int> hi, lo;
             for (int s : upd) {
-                const double m = sys_max(s);  // true residual (FP64 or double-float)
-                hist[s].back() = m;
-                rmax_since[s] = m;
-                m_upd[s] = m;
-                since[s] = 0;
-                if (m <= tol_s[s] && upd_prec != BK_FP64) conf.push_back(s);
-                else if (m <= tol_s[s]) converged_fp64(s);
-                else if (prm->restart_on_update) restart_now[s] = 1;
+                const double m = sys_max(s);
+                if (low_updates && m > tol_s[s] && m >= prm->fp64_anchor * m_anchor[s]) lo.push_back(s);
+                else hi.push_back(s);
+            }
+            std::vector<int> conf;
+            for (int pass = 0; pass < 2; ++pass) {
+                const std::vector<int>& set = pass == 0 ? hi : lo;
+                if (set.empty()) continue;
+                const int rp = pass == 0 ? upd_prec : P;
+                BK_TRY(reliable_update(set, rp, true));
+                for (int s : set) {
+                    const double m = sys_max(s);  // FP64 / double-float true residual, or the updated one
+                    hist[s].back() = m;
+                    rmax_since[s] = m;
+                    m_upd[s] = m;
+                    since[s] = 0;
+                    if (rp == BK_FP64) m_anchor[s] = m;
+                    if (m <= tol_s[s] && rp != BK_FP64) conf.push_back(s);
+                    else if (m <= tol_s[s]) converged_fp64(s);
+                    else if (prm->restart_on_update) restart_now[s] = 1;
+                }
             }
             if (!conf.empty()) {
                 // convergence is decided on an FP64 true residual of the same X
@@ -1456,6 +1497,7 @@ struct Solve {
                     hist[s].back() = m;
                     rmax_since[s] = m;
                     m_upd[s] = m;
+                    m_anchor[s] = m;
                     if (m <= tol_s[s]) converged_fp64(s);
                     else if (prm->restart_on_update) restart_now[s] = 1;
                 }
@@ -1755,6 +1797,7 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
     BK_CHECK_ARG(!prm->deflate || !prm->x0_given, "deflate needs X_0 = 0 (x0_given = 0)");
     BK_CHECK_ARG(!prm->eo || !prm->deflate, "eo and deflate cannot be combined");
     BK_CHECK_ARG(!prm->eo || prm->rtilde_mode != 2, "eo needs rtilde_mode 0 or 1");
+    BK_CHECK_ARG(prm->fp64_anchor >= 0.0 && prm->fp64_anchor < 1.0, "fp64_anchor must be in [0, 1)");
     BK_CHECK_ARG(!prm->eo || (c && (c->dims[0] & 1) == 0), "eo needs an even extent in x");
     int Lu = 0;
     for (int s = 0; s < nsys; ++s) {
@@ -1803,6 +1846,7 @@ static bk_status solve_impl(bk_ctx* c, const bk_solve_params* prm, int nsys, con
     S.nrestart.assign(nsys, 0);
     S.restart_now.assign(nsys, 0);
     S.m_upd.assign(nsys, 1.0);
+    S.m_anchor.assign(nsys, 1.0);
     S.hist.resize(nsys);
     S.true_res.assign(Lt, 0.0);
     S.res_known.assign(nsys, 0);

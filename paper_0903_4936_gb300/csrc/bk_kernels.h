@@ -161,6 +161,8 @@ int genop_norm_rows(int V);
 bk_status launch_norm_finish(const double* ynorm, int ncols, int c0, int n, double* out, int V, cudaStream_t st);
 // X64[cols] += Xlo[cols], Xlo[cols] = 0 over pairs [p0, p0 + np)
 bk_status launch_accum(Field X64, Field Xlo, int p0, int np, cudaStream_t st);
+// X64[cols] -= Ylo[cols] over pairs [p0, p0 + np) (Ylo unchanged)
+bk_status launch_sub_lo(Field X64, Field Ylo, int p0, int np, cudaStream_t st);
 // seeded complex Gaussian block (counter-based, independent of the layout)
 bk_status launch_random(int prec, Field f, int L, uint64_t seed, cudaStream_t st);
 

@@ -987,7 +987,8 @@ __global__ void k_norm_finish(const double* __restrict__ part, int nrows, int nc
 }
 
 // X64 += Xlo; Xlo = 0 over pairs [p0, p0 + np)
-__global__ void k_accum(Field x64, Field xlo, int p0, int np) {
+// X64 += sign * Xlo over pairs [p0, p0 + np); zero_lo: then Xlo = 0
+__global__ void k_accum(Field x64, Field xlo, int p0, int np, double sign, int zero_lo) {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= (long long)x64.V * np) return;
     const int n = (int)(g / np), q = p0 + (int)(g - (long long)(g / np) * np);
@@ -997,13 +998,13 @@ __global__ void k_accum(Field x64, Field xlo, int p0, int np) {
     load_pair<BK_FP32>(xlo, n, q, lr, li);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-        xr[k] = make_double2(xr[k].x + (double)lr[k].x, xr[k].y + (double)lr[k].y);
-        xi[k] = make_double2(xi[k].x + (double)li[k].x, xi[k].y + (double)li[k].y);
+        xr[k] = make_double2(fma(sign, (double)lr[k].x, xr[k].x), fma(sign, (double)lr[k].y, xr[k].y));
+        xi[k] = make_double2(fma(sign, (double)li[k].x, xi[k].x), fma(sign, (double)li[k].y, xi[k].y));
         lr[k] = make_float2(0.f, 0.f);
         li[k] = make_float2(0.f, 0.f);
     }
     store_pair<BK_FP64>(x64, n, q, xr, xi);
-    store_pair<BK_FP32>(xlo, n, q, lr, li);
+    if (zero_lo) store_pair<BK_FP32>(xlo, n, q, lr, li);
 }
 
 // Seeded Gaussian block: SplitMix64 of (seed, canonical index), Box-Muller.
@@ -1597,7 +1598,15 @@ bk_status launch_xmy(int prec, Field X, const double* M, const double* c_dev, Fi
 bk_status launch_accum(Field X64, Field Xlo, int p0, int np, cudaStream_t st) {
     if (np <= 0) return BK_OK;
     const long long items = (long long)X64.V * np;
-    k_accum<<<(unsigned)((items + 127) / 128), 128, 0, st>>>(X64, Xlo, p0, np);
+    k_accum<<<(unsigned)((items + 127) / 128), 128, 0, st>>>(X64, Xlo, p0, np, 1.0, 1);
+    BK_CUDA_TRY(cudaGetLastError());
+    return BK_OK;
+}
+
+bk_status launch_sub_lo(Field X64, Field Ylo, int p0, int np, cudaStream_t st) {
+    if (np <= 0) return BK_OK;
+    const long long items = (long long)X64.V * np;
+    k_accum<<<(unsigned)((items + 127) / 128), 128, 0, st>>>(X64, Ylo, p0, np, -1.0, 0);
     BK_CUDA_TRY(cudaGetLastError());
     return BK_OK;
 }

@@ -3,6 +3,7 @@ synthetic gauge fields: L dependence of block BiCGSTAB and block BiCGGR.
 
     python -m paper_0903_4936_gb300.experiments [--dims 16 16 16 32] [--seeds 1003 1013]
         [--kappas ...] [--scan] [--json out.json] [--markdown]
+    python -m paper_0903_4936_gb300.experiments --kappas 0.1425 --L 4 12 --deflate --json out.json
     python -m paper_0903_4936_gb300.experiments --from-json result.json
 
 For every kappa, method and block size L, the 12 point sources at the origin
@@ -68,7 +69,7 @@ def kappa_scan(dims, seed, kappas, eps=0.5, csw=1.0, target=1000, maxiter=4000):
 
 
 def block_size_scan(dims, kappas, Ls, methods, seeds, tol=1e-14, eps=0.5, csw=1.0, maxiter=6000,
-                    history_seed=None, history_kappa=None):
+                    history_seed=None, history_kappa=None, deflate=False):
     """Rows of (kappa, method, L, mean iterations, mean seconds, seconds per
     source, max true residual, min true residual, failed blocks), and the
     residual histories (first block) of history_seed at history_kappa."""
@@ -85,12 +86,12 @@ def block_size_scan(dims, kappas, Ls, methods, seeds, tol=1e-14, eps=0.5, csw=1.
                     want_hist = seed == history_seed and kappa == history_kappa
                     # warm-up of the operator's launch shapes for this column count
                     lat.block_solve_batched(B, [kappa] * len(Ls_sys), Ls_sys, method=method, prec="fp64",
-                                            tol=1e-4, maxiter=50, raise_on_fail=False)
+                                            tol=1e-4, maxiter=50, raise_on_fail=False, deflate=deflate)
                     torch.cuda.synchronize()
                     t0 = time.perf_counter()
                     X, infos = lat.block_solve_batched(B, [kappa] * len(Ls_sys), Ls_sys, method=method,
                                                        prec="fp64", tol=tol, maxiter=maxiter,
-                                                       raise_on_fail=False, history=want_hist)
+                                                       raise_on_fail=False, history=want_hist, deflate=deflate)
                     torch.cuda.synchronize()
                     dt = time.perf_counter() - t0
                     a = acc.setdefault((kappa, method, L), dict(it=[], t=[], tr=[], fail=0))
@@ -158,6 +159,8 @@ def main(argv=None) -> None:
     ap.add_argument("--scan", action="store_true")
     ap.add_argument("--json")
     ap.add_argument("--markdown", action="store_true")
+    ap.add_argument("--deflate", action="store_true",
+                    help="breakdown-robust form: orthonormalised sources, restarts on L x L breakdown")
     ap.add_argument("--from-json", help="print the tables of an earlier --json result and exit")
     args = ap.parse_args(argv)
     if args.from_json:
@@ -187,7 +190,8 @@ def main(argv=None) -> None:
         light = [s["kappa"] for s in pts if s["iterations"] <= 3000][-3:]
         kappas = light
     rows, hist = block_size_scan(dims, kappas, args.L, args.methods, args.seeds, args.tol,
-                                 history_seed=args.seeds[0], history_kappa=max(kappas))
+                                 history_seed=args.seeds[0], history_kappa=max(kappas), deflate=args.deflate)
+    result["deflate"] = bool(args.deflate)
     result["kappas"] = kappas
     result["grid"] = rows
     result["histories"] = dict(kappa=max(kappas), seed=args.seeds[0], by_method_L=hist)

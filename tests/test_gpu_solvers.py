@@ -408,3 +408,21 @@ def test_deflation_keeps_independent_solves(c1):
         assert infos[s]["deflated"] == 0
         assert _dev(X[c0:c0 + L], ref) <= 1e-8
         c0 += L
+
+
+@pytest.mark.parametrize("eo", [False, True])
+@pytest.mark.parametrize("method", ["bicgstab", "bicggr"])
+def test_fp64_anchor_replacements(c1, method, eo):
+    """fp64_anchor: replacements between FP64 anchors update the residual in
+    FP32 (R64 -= A X_lo); every convergence decision still takes the FP64 true
+    residual, so the solve meets tol and the dense-LU solution with fewer FP64
+    operator applications than with every replacement in FP64."""
+    dims, lat, U, B, Xd, A = c1
+    Bt = torch.from_numpy(B).cuda()
+    kw = dict(method=method, prec="fp32", tol=1e-10, maxiter=1000, delta=0.003, eo=eo)
+    X, info = lat.block_solve(Bt, 0.12, anchor=1e-4, **kw)
+    _, ref = lat.block_solve(Bt, 0.12, **kw)
+    assert info["converged"] == 1 and info["true_res_max"] <= 1e-10
+    assert _dev(X.cpu().numpy(), Xd) <= 1e-8
+    assert info["matvecs_fp64"] < ref["matvecs_fp64"], (info["matvecs_fp64"], ref["matvecs_fp64"])
+    assert info["iterations"] <= 1.5 * ref["iterations"] + 5
