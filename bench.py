@@ -16,7 +16,7 @@ the full system (the run fails otherwise).  Prints ONE JSON line
 on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload c4|c3|c2|c3-12] [--no-fp64] [--fp64-full] [--no-cpu-baseline]
+                  [--workload c4|c3|c2|c3-12|c3-24] [--no-fp64] [--fp64-full] [--no-cpu-baseline]
                   [--eo | --no-eo] [--delta D] [--anchor A] [--update fp64|df64]
                   [--oracle-solve] [--cpu-procs N]   (reference arm)
 
