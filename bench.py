@@ -597,6 +597,8 @@ def main():
     ap.add_argument("--eo", dest="eo", action="store_true", default=None,
                     help="solve through the even-odd Schur system (default: the workload's)")
     ap.add_argument("--no-eo", dest="eo", action="store_false")
+    ap.add_argument("--prec", choices=["fp32", "fp16"], default=None,
+                    help="storage of the inner iterations (default: the workload's, fp32)")
     ap.add_argument("--anchor", type=float, default=None,
                     help="fp64_anchor: replacements between FP64 ones in FP32 (default: the workload's)")
     ap.add_argument("--delta", type=float, default=None,
@@ -605,6 +607,8 @@ def main():
                     help="arithmetic of the residual replacements (default: the workload's)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
+    if args.prec:
+        wl = dict(wl, prec=args.prec)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
