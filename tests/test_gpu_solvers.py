@@ -307,14 +307,16 @@ def test_bicggr_residual_gap_vs_bicgstab(c2):
     assert res["bicgstab"] > 2 * res["bicggr"], res
 
 
-@pytest.mark.parametrize("split", [None, 6])
-def test_batched_uneven_systems_c4_structure(split):
+@pytest.mark.parametrize("split,bench_path", [(None, False), (6, False), (6, True)])
+def test_batched_uneven_systems_c4_structure(split, bench_path):
     """The batched configuration's structure on a 4^4 lattice: six systems,
     kappa 0.120 ... 0.130, L = 4, 12, 12, 24, 48, 96 (196 columns of Z4 noise)
     in one batched mixed-precision solve, as given (L = 96 exercises the
     global-memory L x L solve) and split into systems of at most 6 columns
-    as the benchmark solves them.  Every system is compared with the dense LU
-    solution of its own kappa (oracle) and must reach its FP64 true residual."""
+    as the benchmark solves them, also with the benchmark's settings (even-odd
+    form, delta 0.003, FP64 anchors every 1e-4).  Every system is compared
+    with the dense LU solution of its own kappa (oracle) and must reach its
+    FP64 true residual."""
     dims = (4, 4, 4, 4)
     lat, U = _setup(dims, 0.5, 1004)
     kappas = [0.120, 0.122, 0.124, 0.126, 0.128, 0.130]
@@ -327,8 +329,9 @@ def test_batched_uneven_systems_c4_structure(split):
             ks.append(k)
             ls.append(min(step, L - j0))
             owner.append(s)
+    extra = dict(eo=True, delta=0.003, anchor=1e-4) if bench_path else {}
     X, infos = lat.block_solve_batched(torch.from_numpy(B).cuda(), ks, ls, method="bicgstab", prec="fp32",
-                                       tol=1e-10, maxiter=3000)
+                                       tol=1e-10, maxiter=3000, **extra)
     X = X.cpu().numpy()
     for si, info in enumerate(infos):
         assert info["converged"] == 1 and info["true_res_max"] <= 1e-10, (si, info)
