@@ -180,3 +180,24 @@ def test_eo_initial_guess_and_host_buffers(c1):
                                 maxiter=1000, X0=X0, eo=True)
     assert info1["converged"] == 1 and _dev(X1.cpu().numpy(), Xd) <= 1e-8
     assert info1["iterations"] < info["iterations"]
+
+
+def test_eo_fp16_storage_matches_dense_lu(c1):
+    """FP16-stored inner iterations on the Schur system (FP64 replacements and
+    true residual): the full solution to dense LU accuracy."""
+    dims, lat, U, B, Xd = c1
+    X, infos = lat.block_solve_batched(torch.from_numpy(B).cuda(), [0.12, 0.12], [6, 6], method="bicgstab",
+                                       prec="fp16", tol=1e-10, maxiter=2000, eo=True)
+    for info in infos:
+        assert info["converged"] == 1 and info["true_res_max"] <= 1e-10, info
+    assert _dev(X.cpu().numpy(), Xd) <= 1e-8
+
+
+def test_eo_rejects_deflate_and_caller_rtilde(c1):
+    import paper_0903_4936_gb300 as bk
+    dims, lat, U, B, Xd = c1
+    Bt = torch.from_numpy(B).cuda()
+    with pytest.raises(bk.BKError):
+        lat.block_solve(Bt, 0.12, method="bicgstab", prec="fp64", eo=True, deflate=True)
+    with pytest.raises(bk.BKError):
+        lat.block_solve(Bt, 0.12, method="bicgstab", prec="fp64", eo=True, rtilde=Bt.clone())
